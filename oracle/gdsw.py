@@ -1,0 +1,353 @@
+"""Monolithic multilevel GDSW overlapping Schwarz preconditioner, FP64.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Paper passages followed (Section 2.1 and 2.2):
+  * first level: N nonoverlapping subdomains Omega_i, each enlarged by k layers of
+    elements to Omega_i'; block restriction R_i = diag(R_iu, R_ip) and local saddle-point
+    matrices A_i = R_i A R_i^T with homogeneous Dirichlet data on the artificial boundary;
+  * interface Gamma = union of subdomain boundaries minus the Dirichlet boundary, split
+    into entities (vertices, edges, faces); one coarse column per entity and null-space
+    mode (velocity translations, pressure constant); interface part block-diagonal;
+  * coarse basis by discrete saddle-point extension Phi_I = -A_II^{-1} A_IGamma Phi_Gamma;
+  * coarse operator A_0 = Phi^T A Phi; two-level B = Phi A_0^{-1} Phi^T + sum R_i^T A_i^{-1} R_i;
+  * multilevel: A_0^(l) = Phi^(l)T A_0^(l-1) Phi^(l); the inverse of A_0^(l) is replaced by
+    the two-level method on a coarser decomposition, recursively; only the coarsest
+    A_0^(L) is solved directly (four-level equation of Section 2.2).
+
+Readings where the paper is silent (the same list is in the design notes):
+  * overlap: Omega_i' = Omega_i plus every fluid element sharing a node with it (k = 1);
+    R_i keeps the free dofs of the nodes whose every fluid element lies in Omega_i'
+    (dropping the artificial rim gives the homogeneous Dirichlet condition);
+  * sharing set of a node = subdomains owning a fluid element that contains it; interface
+    nodes have >= 2; entity = connected component (nodes sharing an element) of interface
+    nodes with free dofs and equal sharing sets, ordered by (sorted sharing set, smallest
+    node id); columns (ux, uy, uz) if it has a free velocity node, p if it has a Q1 node;
+  * coarse levels: a coarse node is an entity of the finer level; its part set is the set
+    of coarser groups of its sharing set; two coarse nodes couple iff their sharing sets
+    intersect; Omega_J' = nodes whose part set contains J plus every node coupled to one of
+    them; entities and interiors as on level 1, with coarse null space = indicator of each
+    mode's dofs on the entity;
+  * weighting: "plain" (the paper's additive sum) or "pou" (prolongation weighted by the
+    inverse multiplicity of each dof among the overlapping subdomains).
+
+Parity status: pinned (partition of unity, constant reproduction, extension property,
+brute-force dense preconditioner, one-subdomain reduction, level collapse, symmetry).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+from scipy.sparse.csgraph import connected_components
+
+MODES = 4   # ux, uy, uz, p
+
+
+class LocalSolver:
+    """Exact local solve with a sparse LU (SciPy SuperLU) or a dense LU (NumPy)."""
+
+    def __init__(self, M):
+        if sp.issparse(M):
+            self.lu = spla.splu(sp.csc_matrix(M))
+            self.dense = None
+        else:
+            self.lu = None
+            self.dense = np.asarray(M)
+        self.n = M.shape[0]
+
+    def solve(self, b):
+        if self.n == 0:
+            return np.zeros_like(b)
+        if self.lu is not None:
+            return self.lu.solve(b)
+        return np.linalg.solve(self.dense, b)
+
+
+def _components(nodes_adj, members):
+    """Connected components of the subgraph induced by `members` (sorted ids)."""
+    if members.size == 1:
+        return [members]
+    sub = nodes_adj[members][:, members]
+    ncomp, lab = connected_components(sub, directed=False)
+    return [members[lab == c] for c in range(ncomp)]
+
+
+class SchwarzLevel:
+    """One Schwarz level: overlapping restrictions, local factors, weights, and the GDSW
+    coarse basis Phi towards the next level."""
+
+    # filled by the builders
+    n: int
+    dofs: list            # per overlapping subdomain: sorted global dofs
+    solvers: list
+    weights: list
+    Phi: object           # (n, n0) sparse or dense
+    n0: int
+    coarse_nodes: list    # per coarse node: (sharing-set tuple, dof list, mode list)
+
+    def apply_local(self, r, weighting):
+        z = np.zeros_like(r)
+        for d, s, w in zip(self.dofs, self.solvers, self.weights):
+            zi = s.solve(r[d])
+            z[d] += (w * zi) if weighting == "pou" else zi
+        return z
+
+
+def _multiplicity_weights(dofs, n):
+    mult = np.zeros(n)
+    for d in dofs:
+        mult[d] += 1.0
+    return [1.0 / mult[d] for d in dofs], mult
+
+
+def _coarse_columns(entity_modes):
+    """Number the coarse dofs: entities in order, modes in (ux, uy, uz, p) order."""
+    col = {}
+    nodes = []
+    c = 0
+    for e, modes in enumerate(entity_modes):
+        dl, ml = [], []
+        for m in range(MODES):
+            if modes[m]:
+                col[(e, m)] = c
+                dl.append(c); ml.append(m)
+                c += 1
+        nodes.append((dl, ml))
+    return col, c, nodes
+
+
+def build_level1(sys_, prob, overlap=1, dense_local=False):
+    """First level from the mesh and the element partition (Section 2.1)."""
+    mesh = sys_["mesh"]
+    A = sys_["A"]
+    n = A.shape[0]
+    ne = mesh.elems.size
+    sub = prob.part[mesh.elems].astype(np.int64)
+    if (sub < 0).any():
+        raise ValueError("every fluid element needs a subdomain")
+    N = int(sub.max()) + 1
+    nn = prob.n_nodes
+    # node-element and node-subdomain incidence
+    NE = sp.csr_matrix((np.ones(27 * ne), (mesh.enodes.ravel(), np.repeat(np.arange(ne), 27))),
+                       shape=(nn, ne))
+    NE.data[:] = 1.0
+    ES = sp.csr_matrix((np.ones(ne), (np.arange(ne), sub)), shape=(ne, N))
+    NS = (NE @ ES).tocsr()
+    NS.data[:] = 1.0
+    deg = np.asarray(NE.sum(axis=1)).ravel()
+    # overlap: add `overlap` layers of elements sharing a node
+    EO = ES.copy()
+    for _ in range(overlap):
+        EO = (NE.T @ (NE @ EO)).tocsr()
+        EO.data[:] = 1.0
+    cnt = (NE @ EO).tocsr()          # (node, subdomain): fluid elements of the node inside Omega_i'
+    # dofs of a node
+    vnode_dof = np.where(mesh.vindex >= 0, 3 * mesh.vindex, -1)
+    pnode_dof = np.where(mesh.pindex >= 0, mesh.nu + mesh.pindex, -1)
+
+    def node_dofs(nodes):
+        nodes = np.asarray(nodes)
+        out = []
+        v = vnode_dof[nodes]
+        vv = v[v >= 0]
+        out.append((vv[:, None] + np.arange(3)[None, :]).ravel())
+        pp = pnode_dof[nodes]
+        out.append(pp[pp >= 0])
+        return np.sort(np.concatenate(out))
+
+    cntc = cnt.tocsc()
+    lev = SchwarzLevel()
+    lev.n = n
+    lev.dofs = []
+    for i in range(N):
+        col = cntc[:, i]
+        nodes = col.indices[col.data == deg[col.indices]]
+        lev.dofs.append(node_dofs(nodes))
+    lev.solvers = []
+    for d in lev.dofs:
+        Ai = A[d][:, d]
+        lev.solvers.append(LocalSolver(Ai.toarray() if dense_local else Ai))
+    lev.weights, lev.mult = _multiplicity_weights(lev.dofs, n)
+    lev.N = N
+
+    # --- interface and entities (Section 2.1) ---
+    has_free = (mesh.vindex >= 0) | (mesh.pindex >= 0)
+    nsh = np.diff(NS.indptr)
+    iface = np.nonzero((nsh >= 2) & has_free)[0]
+    key = {}
+    for v in iface:
+        s = tuple(NS.indices[NS.indptr[v]:NS.indptr[v + 1]].tolist())
+        key.setdefault(s, []).append(v)
+    node_adj = (NE @ NE.T).tocsr()
+    entities = []
+    for s in key:
+        members = np.array(sorted(key[s]))
+        for comp in _components(node_adj, members):
+            entities.append((s, np.sort(comp)))
+    entities.sort(key=lambda t: (t[0], int(t[1][0])))
+    ent_modes = []
+    for s, nodes in entities:
+        hv = (mesh.vindex[nodes] >= 0).any()
+        hp = (mesh.pindex[nodes] >= 0).any()
+        ent_modes.append([hv, hv, hv, hp])
+    col, n0, cnodes = _coarse_columns(ent_modes)
+    # Phi_Gamma: Gamma dof -> coarse column
+    g_rows, g_cols = [], []
+    for e, (s, nodes) in enumerate(entities):
+        v = vnode_dof[nodes]
+        v = v[v >= 0]
+        for c in range(3):
+            g_rows.append(v + c); g_cols.append(np.full(v.size, col[(e, c)]) if v.size else np.zeros(0, int))
+        pdofs = pnode_dof[nodes]
+        pdofs = pdofs[pdofs >= 0]
+        if pdofs.size:
+            g_rows.append(pdofs); g_cols.append(np.full(pdofs.size, col[(e, 3)]))
+    g_rows = np.concatenate(g_rows) if g_rows else np.zeros(0, int)
+    g_cols = np.concatenate(g_cols) if g_cols else np.zeros(0, int)
+    PhiG = sp.csr_matrix((np.ones(g_rows.size), (g_rows, g_cols)), shape=(n, n0))
+    gamma = np.zeros(n, dtype=bool)
+    gamma[g_rows] = True
+    # interior dofs of each subdomain: free dofs of nodes with sharing set {i}
+    inter_nodes = np.nonzero((nsh == 1) & has_free)[0]
+    owner = NS.indices[NS.indptr[inter_nodes]]
+    lev.interior = []
+    Phi_rows, Phi_cols, Phi_vals = [g_rows], [g_cols], [np.ones(g_rows.size)]
+    AG = A[:, gamma.nonzero()[0]] @ PhiG[gamma.nonzero()[0]]       # A_{:,Gamma} Phi_Gamma
+    AG = AG.tocsr()
+    for i in range(N):
+        I = node_dofs(inter_nodes[owner == i])
+        lev.interior.append(I)
+        if I.size == 0 or n0 == 0:
+            continue
+        rhs = -AG[I]
+        cols = np.unique(rhs.indices)
+        if cols.size == 0:
+            continue
+        X = LocalSolver(A[I][:, I]).solve(rhs[:, cols].toarray())
+        rr, cc = np.meshgrid(I, cols, indexing="ij")
+        Phi_rows.append(rr.ravel()); Phi_cols.append(cc.ravel()); Phi_vals.append(X.ravel())
+    lev.Phi = sp.csr_matrix((np.concatenate(Phi_vals), (np.concatenate(Phi_rows), np.concatenate(Phi_cols))),
+                            shape=(n, n0))
+    lev.PhiGamma = PhiG
+    lev.gamma = gamma
+    lev.n0 = n0
+    lev.coarse_nodes = [(entities[e][0], cnodes[e][0], cnodes[e][1]) for e in range(len(entities))]
+    lev.entities = entities
+    A0 = (lev.Phi.T @ (A @ lev.Phi)).toarray() if n0 else np.zeros((0, 0))
+    return lev, A0
+
+
+def build_coarse_level(A, cnodes, group, dense_local=True):
+    """A Schwarz level on a coarse operator (Section 2.2 recursion).
+
+    A: dense coarse operator of the finer level; cnodes: list of (sharing set, dofs, modes)
+    per coarse node; group: maps each finer-level part to its part on this level."""
+    n = A.shape[0]
+    nn = len(cnodes)
+    parts = [tuple(sorted({int(group[i]) for i in s})) for (s, d, m) in cnodes]
+    N = int(np.max(group)) + 1 if len(group) else 1
+    # structural coupling: sharing sets intersect
+    inc_r, inc_c = [], []
+    for v, (s, d, m) in enumerate(cnodes):
+        inc_r += [v] * len(s); inc_c += list(s)
+    NS = sp.csr_matrix((np.ones(len(inc_r)), (inc_r, inc_c)), shape=(nn, max(inc_c) + 1 if inc_c else 1))
+    adj = (NS @ NS.T).tocsr()
+    adj.data[:] = 1.0
+    lev = SchwarzLevel()
+    lev.n = n
+    lev.N = N
+    lev.dofs = []
+    for J in range(N):
+        closure = np.array([v for v in range(nn) if J in parts[v]], dtype=int)
+        if closure.size:
+            ext = np.unique(adj[closure].indices)
+        else:
+            ext = closure
+        d = np.sort(np.concatenate([np.array(cnodes[v][1], dtype=int) for v in ext])) if ext.size else np.zeros(0, int)
+        lev.dofs.append(d)
+    lev.solvers = [LocalSolver(A[np.ix_(d, d)]) for d in lev.dofs]
+    lev.weights, lev.mult = _multiplicity_weights(lev.dofs, n)
+    # entities of this level
+    key = {}
+    for v in range(nn):
+        if len(parts[v]) >= 2:
+            key.setdefault(parts[v], []).append(v)
+    entities = []
+    for s in key:
+        members = np.array(sorted(key[s]))
+        for comp in _components(adj, members):
+            entities.append((s, np.sort(comp)))
+    entities.sort(key=lambda t: (t[0], int(t[1][0])))
+    ent_modes = []
+    for s, nodes in entities:
+        present = [False] * MODES
+        for v in nodes:
+            for mm in cnodes[v][2]:
+                present[mm] = True
+        ent_modes.append(present)
+    col, n0, cn = _coarse_columns(ent_modes)
+    PhiG = np.zeros((n, n0))
+    gamma = np.zeros(n, dtype=bool)
+    for e, (s, nodes) in enumerate(entities):
+        for v in nodes:
+            for dof, mm in zip(cnodes[v][1], cnodes[v][2]):
+                PhiG[dof, col[(e, mm)]] = 1.0
+                gamma[dof] = True
+    Phi = PhiG.copy()
+    lev.interior = []
+    for J in range(N):
+        inodes = [v for v in range(nn) if parts[v] == (J,)]
+        I = np.sort(np.array([dd for v in inodes for dd in cnodes[v][1]], dtype=int))
+        lev.interior.append(I)
+        if I.size == 0 or n0 == 0:
+            continue
+        G = gamma.nonzero()[0]
+        rhs = -A[np.ix_(I, G)] @ PhiG[G]
+        Phi[I] = LocalSolver(A[np.ix_(I, I)]).solve(rhs)
+    lev.Phi = Phi
+    lev.PhiGamma = PhiG
+    lev.gamma = gamma
+    lev.n0 = n0
+    lev.coarse_nodes = [(entities[e][0], cn[e][0], cn[e][1]) for e in range(len(entities))]
+    lev.entities = entities
+    A0 = Phi.T @ A @ Phi
+    return lev, A0
+
+
+class GDSW:
+    """Multilevel monolithic GDSW preconditioner (Section 2.2 four-level equation, for
+    L = 2, 3, 4 levels)."""
+
+    def __init__(self, sys_, prob, levels=None, weighting="pou", overlap=1, dense_local=False):
+        L = prob.levels if levels is None else levels
+        self.L = L
+        self.weighting = weighting
+        self.levels = []
+        lev, A0 = build_level1(sys_, prob, overlap=overlap, dense_local=dense_local)
+        self.levels.append(lev)
+        self.A0 = [sys_["A"], A0]
+        for l in range(2, L):
+            cn = self.levels[-1].coarse_nodes
+            lev, A0 = build_coarse_level(A0, cn, prob.groups[l - 2])
+            self.levels.append(lev)
+            self.A0.append(A0)
+        self.coarsest = LocalSolver(A0)
+
+    def apply(self, r, level=0):
+        """z = B r, recursively: local sum on this level plus Phi (next level) Phi^T."""
+        lev = self.levels[level]
+        z = lev.apply_local(r, self.weighting)
+        if lev.n0 == 0:
+            return z
+        r0 = lev.Phi.T @ r
+        if level + 1 == len(self.levels):
+            x0 = self.coarsest.solve(r0)
+        else:
+            x0 = self.apply(r0, level + 1)
+        return z + lev.Phi @ x0
+
+    def dense(self):
+        """The preconditioner as a dense matrix (for small tests)."""
+        n = self.levels[0].n
+        return np.column_stack([self.apply(e) for e in np.eye(n)])
