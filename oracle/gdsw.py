@@ -177,7 +177,7 @@ def build_level1(sys_, prob, overlap=1, dense_local=False):
     iface = np.nonzero((nsh >= 2) & has_free)[0]
     key = {}
     for v in iface:
-        s = tuple(NS.indices[NS.indptr[v]:NS.indptr[v + 1]].tolist())
+        s = tuple(sorted(NS.indices[NS.indptr[v]:NS.indptr[v + 1]].tolist()))
         key.setdefault(s, []).append(v)
     node_adj = (NE @ NE.T).tocsr()
     entities = []
