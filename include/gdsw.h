@@ -1,0 +1,219 @@
+/*
+ * gdsw.h -- C ABI of libgdsw.so: monolithic multilevel GDSW overlapping Schwarz
+ * preconditioner and flexible GMRES for Q2/Q1 Carreau Stokes saddle-point systems,
+ * computed on one GB300 (sm_103a) GPU.
+ *
+ * Method (arXiv 2606.01433):
+ *   - Section 2, saddle-point equation: A_cal = [[A, B^T], [B, 0]] from the weak form
+ *     mu int grad u : grad v - int div v p (gradient form) or, Section 3,
+ *     int 2 nu(u_k) D(u):D(v) - int div v p (symmetric form, Carreau nu).
+ *   - Section 2.1: overlapping restrictions R_i, local saddle-point matrices
+ *     A_i = R_i A R_i^T, interface entities, coarse basis Phi by saddle-point extension,
+ *     A_0 = Phi^T A Phi, B = Phi A_0^{-1} Phi^T + sum_i R_i^T A_i^{-1} R_i.
+ *   - Section 2.2: multilevel recursion and the four-level preconditioner equation; only
+ *     the coarsest A_0^(L) is solved directly.
+ *   - Section 3: restarted FGMRES preconditioned by the multilevel operator.
+ *
+ * Conventions shared by every call:
+ *   - Mesh: nx*ny*nz axis-aligned cubes of edge h; element (ex,ey,ez) has index
+ *     ex + nx*(ey + ny*ez); Q2 node (i,j,k), 0 <= i <= 2nx, at origin + (h/2)(i,j,k), has
+ *     index i + (2nx+1)*(j + (2ny+1)*k).  Q1 (pressure) nodes are the Q2 nodes with all
+ *     indices even that belong to a fluid element.
+ *   - Free-dof vector order: free velocity nodes (fluid nodes whose tag is not
+ *     GDSW_TAG_WALL / GDSW_TAG_INFLOW) in increasing node index, three interleaved
+ *     components each, then the pressure nodes in increasing node index.  n = 3 n_vnodes +
+ *     n_pnodes.
+ *   - Vectors passed to gdsw_apply / gdsw_spmv / gdsw_solve / gdsw_rhs_lift are DEVICE
+ *     pointers to contiguous float64 arrays of length n, owned by the caller.  Calls are
+ *     ordered on the context's stream; apply/spmv/rhs_lift return without synchronising;
+ *     gdsw_solve returns after the final status is known.
+ *   - Host arrays passed to gdsw_setup are read during the call only.
+ *   - The context owns every factor, basis and workspace; gdsw_destroy frees them.
+ *   - Every call returns GDSW_OK or an error code; gdsw_last_error gives the message.
+ *     No exception crosses the ABI.  A context whose call returned GDSW_ERR_CUDA should be
+ *     destroyed.
+ */
+#ifndef GDSW_H
+#define GDSW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum gdsw_status {
+  GDSW_OK = 0,
+  GDSW_ERR_INVALID_ARG = 1,
+  GDSW_ERR_OOM = 2,
+  GDSW_ERR_SINGULAR = 3,      /* a pivot of a local / coarse factorisation vanished */
+  GDSW_ERR_NOT_CONVERGED = 4, /* FGMRES hit max_it; x holds the last iterate */
+  GDSW_ERR_NAN = 5,           /* non-finite residual */
+  GDSW_ERR_TIMEOUT = 6,       /* a bounded device wait expired */
+  GDSW_ERR_CUDA = 7
+};
+
+enum gdsw_tag { GDSW_TAG_INTERIOR = 0, GDSW_TAG_WALL = 1, GDSW_TAG_INFLOW = 2, GDSW_TAG_OUTFLOW = 3 };
+enum gdsw_form { GDSW_FORM_GRADIENT = 0, GDSW_FORM_SYMMETRIC = 1 };
+enum gdsw_precision { GDSW_FP64 = 0, GDSW_FP32 = 1, GDSW_BF16 = 2 };
+enum gdsw_weighting { GDSW_WEIGHT_POU = 0, GDSW_WEIGHT_PLAIN = 1 };
+
+typedef struct gdsw_ctx gdsw_ctx;
+
+/* Voxel mesh and boundary data (Section 3 model problem: inflow, outflow, no-slip). */
+typedef struct {
+  int32_t nx, ny, nz;
+  double h;
+  double origin[3];
+  const uint8_t* mask;   /* host, nx*ny*nz; 1 = fluid element */
+  const uint8_t* tags;   /* host, (2nx+1)(2ny+1)(2nz+1) node tags (enum gdsw_tag) */
+  const double* g;       /* host, 3 per node: Dirichlet datum (read where tag is WALL/INFLOW) */
+} gdsw_mesh;
+
+/* Viscosity (Section 2: constant mu; Section 3: Carreau law
+ * nu = nu_inf + (nu0 - nu_inf)(1 + (lambda gamma_dot)^2)^((n-1)/2),
+ * gamma_dot = sqrt(2 D(u_k):D(u_k)) at every Gauss point of the frozen velocity u_k). */
+typedef struct {
+  int32_t form;          /* enum gdsw_form */
+  double nu0, nu_inf, lambda, n;
+  const double* uk;      /* host, 3 per node, or NULL: constant nu0 */
+} gdsw_viscosity;
+
+/* Partition (Section 2.1 nonoverlapping subdomains; Section 2.2 coarser parts). */
+typedef struct {
+  const int32_t* elem_part;   /* host, nx*ny*nz: subdomain of each fluid element (>= 0) */
+  int32_t n_groups;           /* levels - 2 grouping arrays */
+  const int32_t* groups[2];   /* groups[l][p] = level-(l+2) part of level-(l+1) part p */
+  int32_t group_len[2];       /* entries in groups[l] (= number of level-(l+1) parts) */
+} gdsw_partition;
+
+typedef struct {
+  int32_t levels;        /* L in {2,3,4}: L-1 Schwarz levels, direct solve of A_0^(L) */
+  int32_t overlap;       /* element layers of overlap on level 1 (the paper uses 1) */
+} gdsw_levels;
+
+typedef struct {
+  int32_t weighting;        /* enum gdsw_weighting */
+  int32_t precision[3];     /* storage precision of the local factors on Schwarz levels 1..3 */
+  int32_t phi_precision;    /* storage precision of the level-1 coarse basis */
+  int32_t restart;          /* FGMRES restart length m */
+  int32_t max_it;
+  double tol;               /* relative residual ||b - A x|| / ||b|| */
+  int32_t slab_elems;       /* level-1 factor slab thickness in elements; 0 = one dense block */
+  int32_t use_graph;        /* capture the preconditioner apply in a CUDA graph */
+  void* stream;             /* cudaStream_t for all work of this context (NULL = default) */
+} gdsw_options;
+
+typedef struct {
+  int32_t iterations;
+  int32_t status;           /* enum gdsw_status of the solve */
+  double relres;            /* true ||b - A x|| / ||b|| in FP64 */
+  double est_relres;        /* the Krylov estimate at exit */
+  double time_ms;           /* device time of the whole solve */
+  double apply_ms;          /* summed device time of preconditioner applies */
+  double spmv_ms;
+  double arnoldi_ms;
+} gdsw_solve_info;
+
+typedef struct {
+  int64_t n, n_u, n_p, n_elems, n_nodes;
+  int32_t levels;
+  int64_t n_coarse[4];      /* n_coarse[l] = size of A_0^(l+2) (l = 0..L-2) */
+  int32_t n_parts[3];       /* parts on Schwarz levels 1..L-1 */
+  int64_t local_dofs[3];    /* sum of overlapping local sizes per Schwarz level */
+  int64_t factor_entries[3];/* stored factor entries per Schwarz level */
+  int64_t max_local[3];     /* largest local problem per Schwarz level */
+  int32_t max_slabs;        /* level-1 block-tridiagonal depth */
+  int64_t nnzb_A, nnz_B;    /* 3x3 velocity blocks; pressure-velocity 1x3 entries */
+  int64_t phi_entries;      /* stored level-1 Phi_I entries */
+  int64_t device_bytes;     /* bytes the context holds on the device */
+  double setup_ms[6];       /* host symbolic, viscosity+assembly, level-1 factors, Phi+A0,
+                               coarse levels, total */
+} gdsw_sizes_info;
+
+/* Per-call kernel timing (CUDA events on the context stream) and algorithmic bytes. */
+typedef struct {
+  int32_t enabled;
+  int64_t calls[12];
+  double ms[12];
+  double bytes[12];         /* algorithmic bytes moved per call, summed */
+} gdsw_profile;
+
+enum gdsw_kernel_group {
+  GDSW_K_SPMV = 0, GDSW_K_GATHER = 1, GDSW_K_LOCAL = 2, GDSW_K_SCATTER = 3,
+  GDSW_K_RESTRICT = 4, GDSW_K_COARSE = 5, GDSW_K_PROLONG = 6, GDSW_K_ARNOLDI = 7,
+  GDSW_K_APPLY = 8, GDSW_K_ASSEMBLY = 9, GDSW_K_VISCOSITY = 10, GDSW_K_OTHER = 11
+};
+
+/* Build everything: host symbolic setup (dofs, patterns, overlap, entities, orderings),
+ * then on the device the Carreau viscosity, the assembly of A_cal, the local factors of
+ * every Schwarz level, the coarse bases and coarse operators, and the direct inverse of
+ * the coarsest operator.  Returns GDSW_ERR_SINGULAR if a factorisation pivot vanishes. */
+int gdsw_setup(const gdsw_mesh* mesh, const gdsw_viscosity* visc, const gdsw_partition* part,
+               const gdsw_levels* levels, const gdsw_options* opt, gdsw_ctx** out);
+
+/* Host-only analysis with the same arguments: dof numbering, overlapping subdomains,
+ * entities and coarse sizes of every level (Section 2.1 / 2.2 index sets), plus an
+ * estimate of the device memory gdsw_setup would take (gdsw_sizes_info.device_bytes).
+ * Touches no GPU.  The returned context answers gdsw_sizes, gdsw_level_dofs and
+ * gdsw_level_entities; every device call on it returns GDSW_ERR_INVALID_ARG. */
+int gdsw_analyze(const gdsw_mesh* mesh, const gdsw_viscosity* visc, const gdsw_partition* part,
+                 const gdsw_levels* levels, const gdsw_options* opt, gdsw_ctx** out);
+
+void gdsw_destroy(gdsw_ctx* ctx);
+const char* gdsw_last_error(const gdsw_ctx* ctx);
+int gdsw_sizes(const gdsw_ctx* ctx, gdsw_sizes_info* info);
+
+/* b = -A_(free, Dirichlet) g (Section 2: inhomogeneous Dirichlet datum moved to the right
+ * side); b is a device vector of length n. */
+int gdsw_rhs_lift(gdsw_ctx* ctx, double* b);
+
+/* y = A_cal x (Section 2 saddle-point equation), FP64. */
+int gdsw_spmv(gdsw_ctx* ctx, const double* x, double* y);
+
+/* z = B r: the multilevel GDSW preconditioner (Section 2.2 four-level equation and its
+ * two/three-level forms), with the precisions chosen at setup. */
+int gdsw_apply(gdsw_ctx* ctx, const double* r, double* z);
+
+/* Restarted FGMRES (Section 3) for A_cal x = b; x holds the initial guess on entry. */
+int gdsw_solve(gdsw_ctx* ctx, const double* b, double* x, gdsw_solve_info* info);
+
+/* The same solve with HOST buffers: the copies to and from the device are part of the call. */
+int gdsw_solve_host(gdsw_ctx* ctx, const double* b_host, double* x_host, gdsw_solve_info* info);
+
+/* Re-evaluate the Carreau viscosity from a new frozen velocity u_k (host array, 3 per node,
+ * or NULL to keep the current one) and re-assemble A_cal in place (a Picard step with a
+ * frozen preconditioner). */
+int gdsw_reassemble(gdsw_ctx* ctx, const double* uk_host);
+
+/* ---- component access for tests and profiling (same arithmetic as the apply) ---- */
+
+/* Level l (0-based Schwarz level) local branch only: z = sum_i R_i^T D_i A_i^{-1} R_i r
+ * (D_i = I for plain weighting).  r, z: device FP64 vectors of that level's size. */
+int gdsw_apply_local(gdsw_ctx* ctx, int32_t level, const double* r, double* z);
+/* r0 = Phi^T r towards level l+1 (device vectors). */
+int gdsw_restrict(gdsw_ctx* ctx, int32_t level, const double* r, double* r0);
+/* z += Phi x0 (device vectors). */
+int gdsw_prolong(gdsw_ctx* ctx, int32_t level, const double* x0, double* z);
+/* Copy the coarse operator A_0^(l+2) (dense, row-major FP64, n_coarse[l]^2) to host. */
+int gdsw_coarse_matrix(gdsw_ctx* ctx, int32_t l, double* host);
+/* Copy the assembled operator to host as CSR on free dofs: row_ptr (n+1), col (nnz),
+ * val (nnz); pass NULL pointers to query nnz through *nnz. */
+int gdsw_matrix_csr(gdsw_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val, int64_t* nnz);
+/* Copy the Gauss-point viscosity nu[e][27] (fluid elements in increasing index) to host. */
+int gdsw_viscosity_values(gdsw_ctx* ctx, double* host);
+/* Level-l overlapping sets: dof lists of every subdomain concatenated (global numbering of
+ * that level, sorted per subdomain) and their offsets (n_parts + 1). */
+int gdsw_level_dofs(gdsw_ctx* ctx, int32_t level, int64_t* offsets, int32_t* dofs);
+/* Coarse-space columns: for level l, the number of entities and their modes. */
+int gdsw_level_entities(gdsw_ctx* ctx, int32_t level, int32_t* n_entities);
+
+int gdsw_profile_enable(gdsw_ctx* ctx, int32_t on);
+int gdsw_profile_read(gdsw_ctx* ctx, gdsw_profile* prof);
+int gdsw_profile_reset(gdsw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GDSW_H */

@@ -1,0 +1,1385 @@
+// C ABI of libgdsw.so and the orchestration of set-up and apply
+// (arXiv 2606.01433: Section 2.1 two-level monolithic GDSW, Section 2.2 multilevel
+// recursion and four-level preconditioner, Section 3 FGMRES).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "common.h"
+#include "kernels.h"
+#include "setup.h"
+
+namespace gdsw {
+
+void fgmres_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info);
+
+static thread_local std::string g_setup_error;
+
+static double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------------ profiling helpers
+struct ProfScope {
+  gdsw_ctx* c;
+  int group;
+  double bytes;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(gdsw_ctx* c_, int g, double by, cudaStream_t st) : c(c_), group(g), bytes(by), s(st) {
+    if (!c->prof.enabled) return;
+    a = take();
+    b = take();
+    cudaEventRecord(a, s);
+  }
+  cudaEvent_t take() {
+    if (!c->ev_pool.empty()) {
+      cudaEvent_t e = c->ev_pool.back();
+      c->ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  ~ProfScope() {
+    if (!c->prof.enabled) return;
+    cudaEventRecord(b, s);
+    c->pending.push_back({group, a, b, bytes});
+  }
+};
+
+static void prof_collect(gdsw_ctx* c) {
+  for (auto& p : c->pending) {
+    cudaEventSynchronize(p.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    c->prof.calls[p.group] += 1;
+    c->prof.ms[p.group] += ms;
+    c->prof.bytes[p.group] += p.bytes;
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+// ------------------------------------------------------------------ device views
+struct SlabDevice {
+  SlabView v{};
+  std::vector<int32_t> owner;
+  std::vector<int32_t> part_of_row;
+};
+
+static SlabView upload_slabview(DevArena& A, const SlabSet& S, cudaStream_t s, std::vector<int32_t>* owner_out) {
+  std::vector<int32_t> owner(S.nvec), pslab(S.nvec), pidx(S.nvec), slab_base(S.nsub + 1);
+  std::vector<int64_t> fS, fG, fW;
+  std::vector<int32_t> ldS, ldG, ldW, m;
+  int sb = 0;
+  for (int i = 0; i < S.nsub; ++i) {
+    slab_base[i] = sb;
+    for (int k = 0; k < S.K[i]; ++k) {
+      fS.push_back(S.fS[i][k]); fG.push_back(S.fG[i][k]); fW.push_back(S.fW[i][k]);
+      ldS.push_back(S.ldS[i][k]); ldG.push_back(S.ldG[i][k]); ldW.push_back(S.ldW[i][k]);
+      m.push_back(S.m[i][k]);
+      int64_t p0 = S.voff[i] + S.soff[i][k];
+      for (int r = 0; r < S.s[i][k]; ++r) {
+        owner[p0 + r] = i;
+        pslab[p0 + r] = k;
+        pidx[p0 + r] = r;
+      }
+    }
+    sb += S.K[i];
+  }
+  slab_base[S.nsub] = sb;
+  SlabView v;
+  v.nvec = S.nvec;
+  v.gdof = A.upload(S.gdof, s);
+  v.owner = A.upload(owner, s);
+  v.pslab = A.upload(pslab, s);
+  v.pidx = A.upload(pidx, s);
+  v.voff = A.upload(S.voff, s);
+  v.slab_base = A.upload(slab_base, s);
+  v.fS = A.upload(fS, s); v.fG = A.upload(fG, s); v.fW = A.upload(fW, s);
+  v.ldS = A.upload(ldS, s); v.ldG = A.upload(ldG, s); v.ldW = A.upload(ldW, s);
+  v.m = A.upload(m, s);
+  if (owner_out) *owner_out = owner;
+  return v;
+}
+
+static MatView matview(const gdsw_ctx* c) {
+  MatView v;
+  v.n = c->mesh.n;
+  v.nu = c->mesh.nu;
+  v.a_ptr = c->d_a_ptr; v.a_col = c->d_a_col;
+  v.bt_ptr = c->d_bt_ptr; v.bt_col = c->d_bt_col;
+  v.b_ptr = c->d_b_ptr; v.b_col = c->d_b_col;
+  v.aval = c->d_val;
+  v.btval = c->d_val + 9 * c->nnzb;
+  v.bval = v.btval + 3 * c->nbt;
+  return v;
+}
+
+template <typename T>
+static T* ptr_at(void* base, int64_t off) {
+  return static_cast<T*>(base) + off;
+}
+
+// ------------------------------------------------------------------ block-tridiagonal LDU factorisation
+// For slab blocks A_kk (diagonal), B_k (rows of slab k coupled to slab k-1) and C_k
+// (columns of slab k+1 coupled to slab k), compute in place
+//   S_0 = A_00, S_k = A_kk - B_k S_{k-1}^{-1} C_{k-1},  Sinv_k = S_k^{-1},
+//   G_k = B_k S_{k-1}^{-1},  W_k = S_k^{-1} C_k,
+// so that A = L D U with L_{k,k-1} = G_k, D = diag(S_k), U_{k,k+1} = W_k.
+template <typename T>
+static void factor_slabs(const SlabSet& S, T* fac, double& minpiv, cudaStream_t s) {
+  DevArena tmp;
+  int64_t maxB = 1, maxC = 1;
+  for (int k = 0; k < S.Kmax; ++k) {
+    int64_t sb = 0, sc = 0;
+    for (int i = 0; i < S.nsub; ++i) {
+      if (k >= 1 && k < S.K[i]) sb += int64_t(S.m[i][k]) * S.ldG[i][k];
+      if (k + 1 < S.K[i]) sc += int64_t(S.s[i][k]) * S.ldW[i][k];
+    }
+    maxB = std::max(maxB, sb);
+    maxC = std::max(maxC, sc);
+  }
+  T* scrB = tmp.alloc<T>(maxB);
+  T* scrC = tmp.alloc<T>(maxC);
+  minpiv = 1e300;
+  try {
+    for (int k = 0; k < S.Kmax; ++k) {
+      if (k >= 1) {
+        std::vector<GemmTaskP> tasks;
+        int64_t off = 0;
+        for (int i = 0; i < S.nsub; ++i) {
+          if (k >= S.K[i] || S.m[i][k] == 0) continue;
+          int m = S.m[i][k], sp = S.s[i][k - 1];
+          int64_t cnt = int64_t(m) * S.ldG[i][k];
+          GDSW_CUDA(cudaMemcpyAsync(scrB + off, fac + S.fG[i][k], cnt * sizeof(T), cudaMemcpyDeviceToDevice, s));
+          GemmTaskP u{scrB + off, fac + S.fW[i][k - 1], fac + S.fS[i][k], m, m, sp, S.ldG[i][k], S.ldW[i][k - 1],
+                      S.ldS[i][k], 0, 0, -1.0, 1.0};
+          GemmTaskP g{scrB + off, fac + S.fS[i][k - 1], fac + S.fG[i][k], m, sp, sp, S.ldG[i][k], S.ldS[i][k - 1],
+                      S.ldG[i][k], 0, 0, 1.0, 0.0};
+          tasks.push_back(u);
+          tasks.push_back(g);
+          off += cnt;
+        }
+        run_gemm<T>(tmp, tasks, s);
+      }
+      std::vector<InvTaskP> inv;
+      for (int i = 0; i < S.nsub; ++i)
+        if (k < S.K[i]) inv.push_back({fac + S.fS[i][k], S.s[i][k], S.ldS[i][k], 0});
+      std::vector<double> mp;
+      run_inverse<T>(tmp, inv, mp, s);
+      for (double v : mp) minpiv = std::min(minpiv, v);
+      std::vector<GemmTaskP> wt;
+      int64_t off = 0;
+      for (int i = 0; i < S.nsub; ++i) {
+        if (k + 1 >= S.K[i] || S.m[i][k + 1] == 0) continue;
+        int sk = S.s[i][k], m1 = S.m[i][k + 1];
+        int64_t cnt = int64_t(sk) * S.ldW[i][k];
+        GDSW_CUDA(cudaMemcpyAsync(scrC + off, fac + S.fW[i][k], cnt * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        wt.push_back({fac + S.fS[i][k], scrC + off, fac + S.fW[i][k], sk, m1, sk, S.ldS[i][k], S.ldW[i][k],
+                      S.ldW[i][k], 0, 0, 1.0, 0.0});
+        off += cnt;
+      }
+      run_gemm<T>(tmp, wt, s);
+    }
+    GDSW_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    tmp.free_all();
+    throw;
+  }
+  tmp.free_all();
+}
+
+// multi right-hand-side solve with the LDU factors: R (rows in slab order, ld ldt per
+// part) holds the right-hand sides and is overwritten by the forward sweep; W receives the
+// solution.
+template <typename T>
+static void sweep_multi(const SlabSet& S, const T* fac, T* R, T* W, const std::vector<int64_t>& toff,
+                        const std::vector<int>& ldt, const std::vector<int>& nc, cudaStream_t s) {
+  DevArena tmp;
+  try {
+    for (int k = 0; k < S.Kmax; ++k) {
+      std::vector<GemmTaskP> g, d;
+      for (int i = 0; i < S.nsub; ++i) {
+        if (k >= S.K[i] || nc[i] == 0) continue;
+        T* Rk = R + toff[i] + S.soff[i][k] * ldt[i];
+        if (k >= 1 && S.m[i][k] > 0)
+          g.push_back({fac + S.fG[i][k], R + toff[i] + S.soff[i][k - 1] * ldt[i], Rk, S.m[i][k], nc[i], S.s[i][k - 1],
+                       S.ldG[i][k], ldt[i], ldt[i], 0, 0, -1.0, 1.0});
+        d.push_back({fac + S.fS[i][k], Rk, W + toff[i] + S.soff[i][k] * ldt[i], S.s[i][k], nc[i], S.s[i][k],
+                     S.ldS[i][k], ldt[i], ldt[i], 0, 0, 1.0, 0.0});
+      }
+      run_gemm<T>(tmp, g, s);
+      run_gemm<T>(tmp, d, s);
+    }
+    for (int j = 0; j + 1 < S.Kmax; ++j) {
+      std::vector<GemmTaskP> b;
+      for (int i = 0; i < S.nsub; ++i) {
+        int k = S.K[i] - 2 - j;
+        if (k < 0 || nc[i] == 0 || S.m[i][k + 1] == 0) continue;
+        b.push_back({fac + S.fW[i][k], W + toff[i] + S.soff[i][k + 1] * ldt[i], W + toff[i] + S.soff[i][k] * ldt[i],
+                     S.s[i][k], nc[i], S.m[i][k + 1], S.ldW[i][k], ldt[i], ldt[i], 0, 0, -1.0, 1.0});
+      }
+      run_gemm<T>(tmp, b, s);
+    }
+    GDSW_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    tmp.free_all();
+    throw;
+  }
+  tmp.free_all();
+}
+
+// ------------------------------------------------------------------ apply plans
+static void finish_plan(DevArena& A, GemvPlan& P, std::vector<GemvTask>& tasks, std::vector<GemvTile>& tiles,
+                        cudaStream_t s) {
+  P.d_tasks = A.upload(tasks, s);
+  P.d_tiles = A.upload(tiles, s);
+}
+
+static void add_task(std::vector<GemvTask>& tasks, std::vector<GemvTile>& tiles, const GemvTask& t, int rpt) {
+  if (t.rows <= 0) return;
+  int id = int(tasks.size());
+  tasks.push_back(t);
+  for (int r = 0; r < t.rows; r += rpt) tiles.push_back({id, r});
+}
+
+static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
+  std::vector<GemvTask> tasks;
+  std::vector<GemvTile> tiles;
+  const int rpt = L.fwd.rows_per_tile;
+  const int64_t nv = S.nvec;
+  L.fwd.launch_task_off = {0};
+  L.fwd.launch_tile_off = {0};
+  L.fwd_ld.clear();
+  for (int k = 0; k < S.Kmax; ++k) {
+    int mld = 8;
+    for (int i = 0; i < S.nsub; ++i) {
+      if (k >= S.K[i]) continue;
+      int64_t y = S.voff[i] + S.soff[i][k];
+      GemvTask t{S.fS[i][k], y, nv + y, -1, S.s[i][k], S.s[i][k], S.ldS[i][k], 1.0f};
+      add_task(tasks, tiles, t, rpt);
+      mld = std::max(mld, S.ldS[i][k]);
+      if (k + 1 < S.K[i] && S.m[i][k + 1] > 0) {
+        int64_t y1 = S.voff[i] + S.soff[i][k + 1];
+        GemvTask g{S.fG[i][k + 1], y, y1, y1, S.m[i][k + 1], S.s[i][k], S.ldG[i][k + 1], -1.0f};
+        add_task(tasks, tiles, g, rpt);
+        mld = std::max(mld, S.ldG[i][k + 1]);
+      }
+    }
+    L.fwd.launch_task_off.push_back(int(tasks.size()));
+    L.fwd.launch_tile_off.push_back(int(tiles.size()));
+    L.fwd_ld.push_back(mld);
+  }
+  L.bwd.launch_task_off = {int(tasks.size())};
+  L.bwd.launch_tile_off = {int(tiles.size())};
+  L.bwd_ld.clear();
+  for (int j = 0; j + 1 < S.Kmax; ++j) {
+    int mld = 8;
+    for (int i = 0; i < S.nsub; ++i) {
+      int k = S.K[i] - 2 - j;
+      if (k < 0 || S.m[i][k + 1] == 0) continue;
+      int64_t y = nv + S.voff[i] + S.soff[i][k];
+      int64_t x = nv + S.voff[i] + S.soff[i][k + 1];
+      GemvTask t{S.fW[i][k], x, y, y, S.s[i][k], S.m[i][k + 1], S.ldW[i][k], -1.0f};
+      add_task(tasks, tiles, t, rpt);
+      mld = std::max(mld, S.ldW[i][k]);
+    }
+    L.bwd.launch_task_off.push_back(int(tasks.size()));
+    L.bwd.launch_tile_off.push_back(int(tiles.size()));
+    L.bwd_ld.push_back(mld);
+  }
+  GemvTask* dt = c->arena.upload(tasks, c->stream);
+  GemvTile* dl = c->arena.upload(tiles, c->stream);
+  L.fwd.d_tasks = dt;
+  L.fwd.d_tiles = dl;
+  L.bwd.d_tasks = dt;
+  L.bwd.d_tiles = dl;
+}
+
+// ------------------------------------------------------------------ coarse space upload
+struct CSBuild {
+  std::vector<int64_t> toff;   // per part offset of the n_I x ldt interior blocks
+  std::vector<int> ldt, nc;
+  int64_t ttot = 0;
+  std::vector<int32_t> part_of_irow;
+};
+
+static CSBuild cs_layout(const CoarseSpace& C) {
+  CSBuild b;
+  b.toff.assign(C.nparts + 1, 0);
+  for (int J = 0; J < C.nparts; ++J) {
+    int c = int(C.coff[J + 1] - C.coff[J]);
+    int64_t nI = C.ioff[J + 1] - C.ioff[J];
+    b.nc.push_back(c);
+    b.ldt.push_back(int(pad8(std::max(c, 1))));
+    b.toff[J + 1] = b.toff[J] + nI * b.ldt[J];
+    for (int64_t r = 0; r < nI; ++r) b.part_of_irow.push_back(J);
+  }
+  b.ttot = b.toff[C.nparts];
+  return b;
+}
+
+// upload the apply-side coarse-space data (interior lists, columns, PhiT layout, plans)
+static void upload_coarse_space(gdsw_ctx* c, int l, int phi_prec) {
+  const CoarseSpace& C = c->lh[l].cs;
+  LevelDev& L = c->ld[l];
+  cudaStream_t s = c->stream;
+  L.n0 = C.n0;
+  L.phi_prec = phi_prec;
+  if (C.n0 == 0) return;
+  L.idofs = c->arena.upload(C.idofs, s);
+  L.cols = c->arena.upload(C.cols, s);
+  L.gdofs = c->arena.upload(C.gdofs, s);
+  L.gcol = c->arena.upload(C.gcol, s);
+  L.nidofs = int64_t(C.idofs.size());
+  L.ncols = int64_t(C.cols.size());
+  L.ngamma = int64_t(C.gdofs.size());
+  L.rr_ptr = c->arena.upload(C.rr_ptr, s);
+  L.rr_pos = c->arena.upload(C.rr_pos, s);
+  L.rg_ptr = c->arena.upload(C.rg_ptr, s);
+  L.rg_dof = c->arena.upload(C.rg_dof, s);
+  // PhiT layout: part J stores c_J rows of length pad8(n_IJ)
+  std::vector<ProMeta> meta(C.nparts);
+  std::vector<GemvTask> tasks;
+  std::vector<GemvTile> tiles;
+  std::vector<int32_t> tp, tc;
+  int64_t off = 0;
+  L.max_c = 1;
+  L.max_ld_phi = 8;
+  for (int J = 0; J < C.nparts; ++J) {
+    int cJ = int(C.coff[J + 1] - C.coff[J]);
+    int nI = int(C.ioff[J + 1] - C.ioff[J]);
+    int ld = int(pad8(std::max(nI, 1)));
+    meta[J] = {off, C.ioff[J], C.coff[J], ld, nI, cJ, 0};
+    if (cJ > 0 && nI > 0) {
+      add_task(tasks, tiles, GemvTask{off, C.ioff[J], C.coff[J], -1, cJ, nI, ld, 1.0f}, L.phi_plan.rows_per_tile);
+      for (int col0 = 0; col0 < nI; col0 += 256) {
+        tp.push_back(J);
+        tc.push_back(col0);
+      }
+      L.max_ld_phi = std::max(L.max_ld_phi, ld);
+    }
+    L.max_c = std::max(L.max_c, cJ);
+    off += int64_t(cJ) * ld;
+  }
+  L.phi_plan.launch_task_off = {0, int(tasks.size())};
+  L.phi_plan.launch_tile_off = {0, int(tiles.size())};
+  finish_plan(c->arena, L.phi_plan, tasks, tiles, s);
+  L.pro_meta = reinterpret_cast<int64_t*>(c->arena.upload(meta, s));
+  L.pro_tile_part = c->arena.upload(tp, s);
+  L.pro_tile_col0 = c->arena.upload(tc, s);
+  L.n_pro_tiles = int(tp.size());
+  L.phiT = c->arena.alloc<char>(size_t(std::max<int64_t>(off, 1)) * elem_size(phi_prec));
+  GDSW_CUDA(cudaMemsetAsync(L.phiT, 0, size_t(std::max<int64_t>(off, 1)) * elem_size(phi_prec), s));
+  L.rI = c->arena.alloc<char>(size_t(std::max<int64_t>(L.nidofs, 1)) * elem_size(phi_prec));
+  L.yc = c->arena.alloc<char>(size_t(std::max<int64_t>(L.ncols, 1)) * elem_size(phi_prec));
+  L.r0 = c->arena.alloc<double>(C.n0);
+  L.x0 = c->arena.alloc<double>(C.n0);
+}
+
+static std::vector<int64_t> phi_offsets(const CoarseSpace& C, std::vector<int32_t>& ld) {
+  std::vector<int64_t> off(C.nparts + 1, 0);
+  ld.resize(C.nparts);
+  for (int J = 0; J < C.nparts; ++J) {
+    int cJ = int(C.coff[J + 1] - C.coff[J]);
+    int nI = int(C.ioff[J + 1] - C.ioff[J]);
+    ld[J] = int(pad8(std::max(nI, 1)));
+    off[J + 1] = off[J] + int64_t(cJ) * ld[J];
+  }
+  return off;
+}
+
+// segment lists for A0 = sum of keyed contributions, built on the host
+struct SegList {
+  std::vector<int64_t> key, ptr, pos;
+};
+static SegList make_segments(std::vector<std::pair<int64_t, int64_t>>& kv) {
+  std::stable_sort(kv.begin(), kv.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  SegList L;
+  L.ptr.push_back(0);
+  for (size_t q = 0; q < kv.size(); ++q) {
+    if (q == 0 || kv[q].first != kv[q - 1].first) {
+      if (q > 0) L.ptr.push_back(int64_t(q));
+      L.key.push_back(kv[q].first);
+    }
+    L.pos.push_back(kv[q].second);
+  }
+  if (!kv.empty()) L.ptr.push_back(int64_t(kv.size()));
+  return L;
+}
+
+static void run_segments(gdsw_ctx* c, SegList& L, const double* src, double* dst, DevArena& tmp) {
+  if (L.key.empty()) return;
+  int64_t* k = tmp.upload(L.key, c->stream);
+  int64_t* p = tmp.upload(L.ptr, c->stream);
+  int64_t* q = tmp.upload(L.pos, c->stream);
+  segsum(k, p, q, int64_t(L.key.size()), src, dst, c->stream);
+}
+
+// ------------------------------------------------------------------ level 1 numeric set-up
+template <typename T>
+static void level1_locals(gdsw_ctx* c, double& minpiv) {
+  const SlabSet& S = c->lh[0].loc;
+  LevelDev& L = c->ld[0];
+  cudaStream_t s = c->stream;
+  MatView A = matview(c);
+  DevArena tmp;
+  T* fac = tmp.alloc<T>(S.nfac);
+  GDSW_CUDA(cudaMemsetAsync(fac, 0, S.nfac * sizeof(T), s));
+  std::vector<int32_t> owner;
+  SlabView SV = upload_slabview(tmp, S, s, &owner);
+  int* err = tmp.alloc<int>(1);
+  GDSW_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  // batches of parts with a private global-to-local map each
+  int64_t per_map = c->mesh.n;
+  int batch = int(std::max<int64_t>(1, std::min<int64_t>(S.nsub, (int64_t(2) << 30) / (4 * per_map))));
+  int32_t* map = tmp.alloc<int32_t>(size_t(batch) * per_map);
+  GDSW_CUDA(cudaMemsetAsync(map, 0xff, size_t(batch) * per_map * 4, s));
+  for (int i0 = 0; i0 < S.nsub; i0 += batch) {
+    int i1 = std::min(S.nsub, i0 + batch);
+    extract_slabs<T>(A, SV, S.voff[i0], S.voff[i1], i0, 1, map, fac, err, s);
+  }
+  int herr = 0;
+  GDSW_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GDSW_CUDA(cudaStreamSynchronize(s));
+  GDSW_CHECK(herr == 0, GDSW_ERR_INVALID_ARG, "slab ordering leaves a coupling outside the block tridiagonal");
+  tmp.release(map);
+  factor_slabs<T>(S, fac, minpiv, s);
+  // storage precision
+  int prec = c->opt.precision[0];
+  L.prec = prec;
+  L.nfac = S.nfac;
+  L.nvec = S.nvec;
+  if (prec == GDSW_BF16) {
+    L.fac = c->arena.alloc<__nv_bfloat16>(S.nfac);
+    convert(fac, sizeof(T) == 8 ? GDSW_FP64 : GDSW_FP32, L.fac, GDSW_BF16, S.nfac, s);
+  } else {
+    L.fac = c->arena.alloc<T>(S.nfac);
+    GDSW_CUDA(cudaMemcpyAsync(L.fac, fac, S.nfac * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  }
+  GDSW_CUDA(cudaStreamSynchronize(s));
+  tmp.free_all();
+}
+
+template <typename T>
+static void level1_coarse(gdsw_ctx* c, double* A0, double& minpiv) {
+  const LevelHost& H = c->lh[0];
+  const SlabSet& S = H.inter;
+  const CoarseSpace& C = H.cs;
+  cudaStream_t s = c->stream;
+  MatView A = matview(c);
+  DevArena tmp;
+  try {
+    T* fac = tmp.alloc<T>(S.nfac);
+    GDSW_CUDA(cudaMemsetAsync(fac, 0, S.nfac * sizeof(T), s));
+    std::vector<int32_t> owner;
+    SlabView SV = upload_slabview(tmp, S, s, &owner);
+    int* err = tmp.alloc<int>(1);
+    GDSW_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    int32_t* map = tmp.alloc<int32_t>(c->mesh.n);
+    GDSW_CUDA(cudaMemsetAsync(map, 0xff, c->mesh.n * 4, s));
+    extract_slabs<T>(A, SV, 0, S.nvec, 0, 0, map, fac, err, s);
+    factor_slabs<T>(S, fac, minpiv, s);
+    // right-hand sides Tneg = -A_IGamma Phi_Gamma
+    CSBuild B = cs_layout(C);
+    std::vector<int32_t> gamma_col(c->mesh.n, -1), ilocal(c->mesh.n, -1);
+    for (size_t q = 0; q < C.gdofs.size(); ++q) gamma_col[C.gdofs[q]] = C.gcol[q];
+    for (int64_t p = 0; p < S.nvec; ++p) ilocal[S.gdof[p]] = int32_t(p);
+    int32_t* d_gc = tmp.upload(gamma_col, s);
+    int32_t* d_il = tmp.upload(ilocal, s);
+    int32_t* d_cols = tmp.upload(C.cols, s);
+    int64_t* d_coff = tmp.upload(C.coff, s);
+    int64_t* d_toff = tmp.upload(B.toff, s);
+    int32_t* d_ldt = tmp.upload(B.ldt, s);
+    double* Tn = tmp.alloc<double>(B.ttot);
+    GDSW_CUDA(cudaMemsetAsync(Tn, 0, B.ttot * 8, s));
+    launch_tneg(A, SV, d_gc, d_cols, d_coff, d_toff, d_ldt, Tn, err, s);
+    int herr = 0;
+    GDSW_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GDSW_CUDA(cudaStreamSynchronize(s));
+    GDSW_CHECK(herr == 0, GDSW_ERR_INVALID_ARG, "interior coupling outside the part's coarse columns");
+    // X = A_II^{-1} Tneg  (= Phi_I)
+    T* R = tmp.alloc<T>(B.ttot);
+    T* W = tmp.alloc<T>(B.ttot);
+    GDSW_CUDA(cudaMemsetAsync(W, 0, B.ttot * sizeof(T), s));
+    if (sizeof(T) == 8)
+      GDSW_CUDA(cudaMemcpyAsync(R, Tn, B.ttot * 8, cudaMemcpyDeviceToDevice, s));
+    else
+      convert(Tn, GDSW_FP64, R, GDSW_FP32, B.ttot, s);
+    sweep_multi<T>(S, fac, R, W, B.toff, B.ldt, B.nc, s);
+    tmp.release(R);
+    tmp.release(fac);
+    double* X = nullptr;
+    if (sizeof(T) == 8) {
+      X = reinterpret_cast<double*>(W);
+    } else {
+      X = tmp.alloc<double>(B.ttot);
+      convert(W, GDSW_FP32, X, GDSW_FP64, B.ttot, s);
+    }
+    // Galerkin product A_0 = Phi^T A Phi = sum_i [X_i^T (A_II X_i - Tn_i) - Tn_i^T X_i] + Phi_G^T A_GG Phi_G
+    double* Y = tmp.alloc<double>(B.ttot);
+    launch_yint(A, SV, d_il, d_coff, d_toff, d_ldt, X, Tn, Y, s);
+    std::vector<int64_t> zoff(C.nparts + 1, 0);
+    for (int J = 0; J < C.nparts; ++J) zoff[J + 1] = zoff[J] + int64_t(B.nc[J]) * B.ldt[J];
+    double* Z = tmp.alloc<double>(std::max<int64_t>(zoff[C.nparts], 1));
+    GDSW_CUDA(cudaMemsetAsync(Z, 0, std::max<int64_t>(zoff[C.nparts], 1) * 8, s));
+    std::vector<GemmTaskP> g1, g2;
+    for (int J = 0; J < C.nparts; ++J) {
+      int nc = B.nc[J];
+      int nI = int(C.ioff[J + 1] - C.ioff[J]);
+      if (nc == 0 || nI == 0) continue;
+      g1.push_back({X + B.toff[J], Y + B.toff[J], Z + zoff[J], nc, nc, nI, B.ldt[J], B.ldt[J], B.ldt[J], 1, 0, 1.0, 0.0});
+      g2.push_back({Tn + B.toff[J], X + B.toff[J], Z + zoff[J], nc, nc, nI, B.ldt[J], B.ldt[J], B.ldt[J], 1, 0, -1.0, 1.0});
+    }
+    run_gemm<double>(tmp, g1, s);
+    run_gemm<double>(tmp, g2, s);
+    const int64_t n0 = C.n0;
+    {
+      std::vector<std::pair<int64_t, int64_t>> kv;
+      for (int J = 0; J < C.nparts; ++J) {
+        int nc = B.nc[J];
+        const int32_t* cj = C.cols.data() + C.coff[J];
+        for (int a = 0; a < nc; ++a)
+          for (int b = 0; b < nc; ++b) kv.push_back({int64_t(cj[a]) * n0 + cj[b], zoff[J] + int64_t(a) * B.ldt[J] + b});
+      }
+      SegList L = make_segments(kv);
+      run_segments(c, L, Z, A0, tmp);
+    }
+    {
+      // interface-interface couplings: positions into the value array
+      const MeshHost& M = c->mesh;
+      std::vector<std::pair<int64_t, int64_t>> kv;
+      const int64_t bt0 = 9 * c->nnzb, b0 = bt0 + 3 * c->nbt;
+      for (int k = 0; k < C.n0; ++k) {
+        std::vector<std::pair<int64_t, int64_t>> row;
+        for (int32_t e = C.rg_ptr[k]; e < C.rg_ptr[k + 1]; ++e) {
+          int64_t a = C.rg_dof[e];
+          if (a < M.nu) {
+            int64_t I = a / 3;
+            int cc = int(a - 3 * I);
+            for (int32_t blk = M.a_ptr[I]; blk < M.a_ptr[I + 1]; ++blk)
+              for (int d = 0; d < 3; ++d) {
+                int gc = gamma_col[3 * int64_t(M.a_col[blk]) + d];
+                if (gc >= 0) row.push_back({gc, int64_t(blk) * 9 + cc * 3 + d});
+              }
+            for (int32_t q = M.bt_ptr[I]; q < M.bt_ptr[I + 1]; ++q) {
+              int gc = gamma_col[M.nu + M.bt_col[q]];
+              if (gc >= 0) row.push_back({gc, bt0 + int64_t(q) * 3 + cc});
+            }
+          } else {
+            int64_t P = a - M.nu;
+            for (int32_t q = M.b_ptr[P]; q < M.b_ptr[P + 1]; ++q)
+              for (int d = 0; d < 3; ++d) {
+                int gc = gamma_col[3 * int64_t(M.b_col[q]) + d];
+                if (gc >= 0) row.push_back({gc, b0 + int64_t(q) * 3 + d});
+              }
+          }
+        }
+        std::stable_sort(row.begin(), row.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+        for (auto& pr : row) kv.push_back({int64_t(k) * n0 + pr.first, pr.second});
+      }
+      SegList L = make_segments(kv);
+      run_segments(c, L, c->d_val, A0, tmp);
+    }
+    // store Phi_I^T in the storage precision
+    std::vector<int32_t> phild;
+    std::vector<int64_t> phioff = phi_offsets(C, phild);
+    int64_t* d_phioff = tmp.upload(phioff, s);
+    int32_t* d_phild = tmp.upload(phild, s);
+    int32_t* d_por = tmp.upload(B.part_of_irow, s);
+    int64_t* d_ioff = tmp.upload(C.ioff, s);
+    LevelDev& L = c->ld[0];
+    if (L.phi_prec == GDSW_FP64)
+      store_phiT<double>(X, d_toff, d_ldt, d_por, d_ioff, S.nvec, d_coff, d_phioff, d_phild,
+                         static_cast<double*>(L.phiT), nullptr, nullptr, nullptr, 0, s);
+    else
+      store_phiT<float>(X, d_toff, d_ldt, d_por, d_ioff, S.nvec, d_coff, d_phioff, d_phild,
+                        static_cast<float*>(L.phiT), nullptr, nullptr, nullptr, 0, s);
+    GDSW_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    tmp.free_all();
+    throw;
+  }
+  tmp.free_all();
+}
+
+// ------------------------------------------------------------------ coarse levels (dense operators)
+template <typename T>
+static void coarse_locals(gdsw_ctx* c, int l, double& minpiv) {
+  const SlabSet& S = c->lh[l].loc;
+  LevelDev& L = c->ld[l];
+  cudaStream_t s = c->stream;
+  DevArena tmp;
+  T* fac = tmp.alloc<T>(S.nfac);
+  GDSW_CUDA(cudaMemsetAsync(fac, 0, S.nfac * sizeof(T), s));
+  std::vector<int64_t> oo(S.nsub);
+  std::vector<int32_t> ol(S.nsub), por;
+  for (int i = 0; i < S.nsub; ++i) {
+    oo[i] = S.K[i] ? S.fS[i][0] : 0;
+    ol[i] = S.K[i] ? S.ldS[i][0] : 8;
+    for (int64_t r = S.voff[i]; r < S.voff[i + 1]; ++r) por.push_back(i);
+  }
+  int32_t* d_dofs = tmp.upload(S.gdof, s);
+  int64_t* d_voff = tmp.upload(S.voff, s);
+  int32_t* d_por = tmp.upload(por, s);
+  int64_t* d_oo = tmp.upload(oo, s);
+  int32_t* d_ol = tmp.upload(ol, s);
+  gather_dense<T>(L.A, L.n, d_dofs, d_voff, d_por, S.nvec, d_oo, d_ol, fac, s);
+  std::vector<InvTaskP> inv;
+  for (int i = 0; i < S.nsub; ++i)
+    if (S.K[i]) inv.push_back({fac + S.fS[i][0], S.s[i][0], S.ldS[i][0], 0});
+  std::vector<double> mp;
+  run_inverse<T>(tmp, inv, mp, s);
+  minpiv = 1e300;
+  for (double v : mp) minpiv = std::min(minpiv, v);
+  int prec = c->opt.precision[l];
+  L.prec = prec;
+  L.nfac = S.nfac;
+  L.nvec = S.nvec;
+  if (prec == GDSW_BF16) {
+    L.fac = c->arena.alloc<__nv_bfloat16>(S.nfac);
+    convert(fac, sizeof(T) == 8 ? GDSW_FP64 : GDSW_FP32, L.fac, GDSW_BF16, S.nfac, s);
+  } else {
+    L.fac = c->arena.alloc<T>(S.nfac);
+    GDSW_CUDA(cudaMemcpyAsync(L.fac, fac, S.nfac * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  }
+  GDSW_CUDA(cudaStreamSynchronize(s));
+  tmp.free_all();
+}
+
+// coarse basis of a coarse level and the next coarse operator A0n = Phi^T A Phi (FP64)
+static void coarse_basis(gdsw_ctx* c, int l, double* A0n, double& minpiv) {
+  const LevelHost& H = c->lh[l];
+  const SlabSet& S = H.inter;
+  const CoarseSpace& C = H.cs;
+  LevelDev& L = c->ld[l];
+  cudaStream_t s = c->stream;
+  const int64_t n = L.n, n0 = C.n0;
+  DevArena tmp;
+  try {
+    double* fac = tmp.alloc<double>(S.nfac);
+    GDSW_CUDA(cudaMemsetAsync(fac, 0, S.nfac * 8, s));
+    std::vector<int64_t> oo(S.nsub);
+    std::vector<int32_t> ol(S.nsub);
+    for (int i = 0; i < S.nsub; ++i) {
+      oo[i] = S.K[i] ? S.fS[i][0] : 0;
+      ol[i] = S.K[i] ? S.ldS[i][0] : 8;
+    }
+    CSBuild B = cs_layout(C);
+    int32_t* d_idofs = tmp.upload(C.idofs, s);
+    int64_t* d_ioff = tmp.upload(C.ioff, s);
+    int32_t* d_por = tmp.upload(B.part_of_irow, s);
+    int64_t* d_oo = tmp.upload(oo, s);
+    int32_t* d_ol = tmp.upload(ol, s);
+    gather_dense<double>(L.A, n, d_idofs, d_ioff, d_por, S.nvec, d_oo, d_ol, fac, s);
+    std::vector<InvTaskP> inv;
+    for (int i = 0; i < S.nsub; ++i)
+      if (S.K[i]) inv.push_back({fac + S.fS[i][0], S.s[i][0], S.ldS[i][0], 0});
+    std::vector<double> mp;
+    run_inverse<double>(tmp, inv, mp, s);
+    minpiv = 1e300;
+    for (double v : mp) minpiv = std::min(minpiv, v);
+    int32_t* d_gd = tmp.upload(C.gdofs, s);
+    int32_t* d_gc = tmp.upload(C.gcol, s);
+    int32_t* d_cols = tmp.upload(C.cols, s);
+    int64_t* d_coff = tmp.upload(C.coff, s);
+    int64_t* d_toff = tmp.upload(B.toff, s);
+    int32_t* d_ldt = tmp.upload(B.ldt, s);
+    double* Tn = tmp.alloc<double>(std::max<int64_t>(B.ttot, 1));
+    GDSW_CUDA(cudaMemsetAsync(Tn, 0, std::max<int64_t>(B.ttot, 1) * 8, s));
+    coarse_tneg(L.A, n, d_idofs, d_ioff, d_por, S.nvec, d_gd, d_gc, int64_t(C.gdofs.size()), d_cols, d_coff, d_toff,
+                d_ldt, Tn, s);
+    double* X = tmp.alloc<double>(std::max<int64_t>(B.ttot, 1));
+    std::vector<GemmTaskP> g;
+    for (int J = 0; J < C.nparts; ++J) {
+      int nI = int(C.ioff[J + 1] - C.ioff[J]);
+      if (nI == 0 || B.nc[J] == 0) continue;
+      g.push_back({fac + S.fS[J][0], Tn + B.toff[J], X + B.toff[J], nI, B.nc[J], nI, S.ldS[J][0], B.ldt[J], B.ldt[J],
+                   0, 0, 1.0, 0.0});
+    }
+    run_gemm<double>(tmp, g, s);
+    double* dense = tmp.alloc<double>(n * n0);
+    GDSW_CUDA(cudaMemsetAsync(dense, 0, n * n0 * 8, s));
+    std::vector<int32_t> phild;
+    std::vector<int64_t> phioff = phi_offsets(C, phild);
+    int64_t* d_phioff = tmp.upload(phioff, s);
+    int32_t* d_phild = tmp.upload(phild, s);
+    if (L.phi_prec == GDSW_FP64)
+      store_phiT<double>(X, d_toff, d_ldt, d_por, d_ioff, S.nvec, d_coff, d_phioff, d_phild,
+                         static_cast<double*>(L.phiT), d_idofs, d_cols, dense, n0, s);
+    else
+      store_phiT<float>(X, d_toff, d_ldt, d_por, d_ioff, S.nvec, d_coff, d_phioff, d_phild, static_cast<float*>(L.phiT),
+                        d_idofs, d_cols, dense, n0, s);
+    dense_gamma(d_gd, d_gc, int64_t(C.gdofs.size()), dense, n0, s);
+    double* T1 = tmp.alloc<double>(n * n0);
+    run_gemm<double>(tmp, {{L.A, dense, T1, int(n), int(n0), int(n), int(n), int(n0), int(n0), 0, 0, 1.0, 0.0}}, s);
+    run_gemm<double>(tmp, {{dense, T1, A0n, int(n0), int(n0), int(n), int(n0), int(n0), int(n0), 1, 0, 1.0, 0.0}}, s);
+    GDSW_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    tmp.free_all();
+    throw;
+  }
+  tmp.free_all();
+}
+
+// ------------------------------------------------------------------ apply
+static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStream_t s) {
+  LevelDev& L = c->ld[l];
+  const LevelHost& H = c->lh[l];
+  const int64_t nv = L.nvec;
+  double gbytes = 0;
+  {
+    ProfScope ps(c, GDSW_K_GATHER, double(nv) * (4 + 8 + (L.prec == GDSW_FP64 ? 8 : 4)), s);
+    if (L.prec == GDSW_FP64)
+      launch_gather<double>(r, L.gdof, static_cast<double*>(L.vec), nv, s);
+    else
+      launch_gather<float>(r, L.gdof, static_cast<float*>(L.vec), nv, s);
+  }
+  {
+    ProfScope ps(c, GDSW_K_LOCAL, double(L.local_bytes), s);
+    for (int k = 0; k < L.fwd.nlaunch(); ++k) {
+      if (L.prec == GDSW_FP64) {
+        double* v = static_cast<double*>(L.vec);
+        launch_gemv<double, double>(static_cast<const double*>(L.fac), v, v, v, L.fwd, k, L.fwd_ld[k], s);
+      } else if (L.prec == GDSW_FP32) {
+        float* v = static_cast<float*>(L.vec);
+        launch_gemv<float, float>(static_cast<const float*>(L.fac), v, v, v, L.fwd, k, L.fwd_ld[k], s);
+      } else {
+        float* v = static_cast<float*>(L.vec);
+        launch_gemv<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), v, v, v, L.fwd, k, L.fwd_ld[k], s);
+      }
+    }
+    for (int k = 0; k < L.bwd.nlaunch(); ++k) {
+      if (L.prec == GDSW_FP64) {
+        double* v = static_cast<double*>(L.vec);
+        launch_gemv<double, double>(static_cast<const double*>(L.fac), v, v, v, L.bwd, k, L.bwd_ld[k], s);
+      } else if (L.prec == GDSW_FP32) {
+        float* v = static_cast<float*>(L.vec);
+        launch_gemv<float, float>(static_cast<const float*>(L.fac), v, v, v, L.bwd, k, L.bwd_ld[k], s);
+      } else {
+        float* v = static_cast<float*>(L.vec);
+        launch_gemv<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), v, v, v, L.bwd, k, L.bwd_ld[k], s);
+      }
+    }
+  }
+  {
+    ProfScope ps(c, GDSW_K_SCATTER, double(nv) * (4 + 8 + (L.prec == GDSW_FP64 ? 8 : 4)) + 8.0 * L.n, s);
+    if (L.prec == GDSW_FP64)
+      launch_scatter<double>(static_cast<const double*>(L.vec) + nv, L.sc_ptr, L.sc_pos, L.sc_w, z, L.n, 0, s);
+    else
+      launch_scatter<float>(static_cast<const float*>(L.vec) + nv, L.sc_ptr, L.sc_pos, L.sc_w, z, L.n, 0, s);
+  }
+  (void)H;
+  (void)gbytes;
+}
+
+static void restrict_level(gdsw_ctx* c, int l, const double* r, double* r0, cudaStream_t s) {
+  LevelDev& L = c->ld[l];
+  if (L.n0 == 0) return;
+  ProfScope ps(c, GDSW_K_RESTRICT, double(L.phi_bytes) + 16.0 * L.nidofs, s);
+  if (L.phi_prec == GDSW_FP64) {
+    launch_gather<double>(r, L.idofs, static_cast<double*>(L.rI), L.nidofs, s);
+    launch_gemv<double, double>(static_cast<const double*>(L.phiT), static_cast<const double*>(L.rI),
+                                static_cast<double*>(L.yc), nullptr, L.phi_plan, 0, L.max_ld_phi, s);
+  } else {
+    launch_gather<float>(r, L.idofs, static_cast<float*>(L.rI), L.nidofs, s);
+    launch_gemv<float, float>(static_cast<const float*>(L.phiT), static_cast<const float*>(L.rI),
+                              static_cast<float*>(L.yc), nullptr, L.phi_plan, 0, L.max_ld_phi, s);
+  }
+  launch_restrict_reduce(L.yc, L.phi_prec, r, L.rr_ptr, L.rr_pos, L.rg_ptr, L.rg_dof, r0, L.n0, s);
+}
+
+static void coarsest_solve(gdsw_ctx* c, const double* r0, double* x0, cudaStream_t s) {
+  ProfScope ps(c, GDSW_K_COARSE, 8.0 * double(c->n_coarsest) * c->ld_coarsest, s);
+  launch_gemv<double, double>(c->d_coarsest_inv, r0, x0, nullptr, c->coarsest_plan, 0, c->ld_coarsest, s);
+}
+
+static void apply_level(gdsw_ctx* c, int l, const double* r, double* z, cudaStream_t s) {
+  LevelDev& L = c->ld[l];
+  const int nlev = int(c->ld.size());
+  const bool coarse = L.n0 > 0;
+  const bool fork = coarse && l == 0 && c->stream2 != nullptr && !c->prof.enabled;
+  cudaStream_t sc = fork ? c->stream2 : s;
+  if (fork) {
+    GDSW_CUDA(cudaEventRecord(c->ev_fork, s));
+    GDSW_CUDA(cudaStreamWaitEvent(sc, c->ev_fork, 0));
+  }
+  if (coarse) {
+    restrict_level(c, l, r, L.r0, sc);
+    if (l + 1 < nlev)
+      apply_level(c, l + 1, L.r0, L.x0, sc);
+    else
+      coarsest_solve(c, L.r0, L.x0, sc);
+  }
+  local_solve(c, l, r, z, s);
+  if (fork) {
+    GDSW_CUDA(cudaEventRecord(c->ev_join, sc));
+    GDSW_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+  }
+  if (coarse) {
+    ProfScope ps(c, GDSW_K_PROLONG, double(L.phi_bytes) + 16.0 * L.nidofs, s);
+    launch_prolong(L, L.x0, z, s);
+  }
+}
+
+void apply_precond(gdsw_ctx* c, const double* r, double* z, cudaStream_t s) {
+  if (c->apply_graph && !c->prof.enabled) {
+    GDSW_CUDA(cudaMemcpyAsync(c->d_graph_r, r, sizeof(double) * c->mesh.n, cudaMemcpyDeviceToDevice, s));
+    GDSW_CUDA(cudaGraphLaunch(c->apply_graph, s));
+    GDSW_CUDA(cudaMemcpyAsync(z, c->d_graph_z, sizeof(double) * c->mesh.n, cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  ProfScope ps(c, GDSW_K_APPLY, 0.0, s);
+  apply_level(c, 0, r, z, s);
+}
+
+static void capture_graph(gdsw_ctx* c) {
+  c->d_graph_r = c->arena.alloc<double>(c->mesh.n);
+  c->d_graph_z = c->arena.alloc<double>(c->mesh.n);
+  GDSW_CUDA(cudaMemsetAsync(c->d_graph_r, 0, 8 * c->mesh.n, c->stream));
+  GDSW_CUDA(cudaStreamSynchronize(c->stream));
+  cudaGraph_t g;
+  GDSW_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    apply_level(c, 0, c->d_graph_r, c->d_graph_z, c->stream);
+  } catch (...) {
+    cudaStreamEndCapture(c->stream, &g);
+    throw;
+  }
+  GDSW_CUDA(cudaStreamEndCapture(c->stream, &g));
+  GDSW_CUDA(cudaGraphInstantiate(&c->apply_graph, g, 0));
+  GDSW_CUDA(cudaGraphDestroy(g));
+}
+
+// ------------------------------------------------------------------ set-up driver
+static void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, const gdsw_partition* part,
+                       const gdsw_levels* lv, const gdsw_options* opt) {
+  GDSW_CHECK(mesh && visc && part && lv && opt, GDSW_ERR_INVALID_ARG, "null argument");
+  GDSW_CHECK(mesh->nx > 0 && mesh->ny > 0 && mesh->nz > 0 && mesh->h > 0, GDSW_ERR_INVALID_ARG, "bad mesh size");
+  GDSW_CHECK(mesh->mask && mesh->tags && mesh->g && part->elem_part, GDSW_ERR_INVALID_ARG, "null mesh array");
+  GDSW_CHECK(lv->levels >= 2 && lv->levels <= 4, GDSW_ERR_INVALID_ARG, "levels must be 2, 3 or 4");
+  GDSW_CHECK(part->n_groups == lv->levels - 2, GDSW_ERR_INVALID_ARG, "need levels-2 grouping arrays");
+  GDSW_CHECK(lv->overlap >= 1 && lv->overlap <= 4, GDSW_ERR_INVALID_ARG, "overlap must be 1..4");
+  GDSW_CHECK(opt->slab_elems >= 0, GDSW_ERR_INVALID_ARG, "slab_elems must be >= 0");
+  for (int l = 0; l < lv->levels - 1; ++l)
+    GDSW_CHECK(opt->precision[l] >= GDSW_FP64 && opt->precision[l] <= GDSW_BF16, GDSW_ERR_INVALID_ARG, "bad precision");
+  GDSW_CHECK(opt->phi_precision == GDSW_FP64 || opt->phi_precision == GDSW_FP32, GDSW_ERR_INVALID_ARG,
+             "phi precision must be FP64 or FP32");
+  GDSW_CHECK(visc->form == GDSW_FORM_GRADIENT || visc->form == GDSW_FORM_SYMMETRIC, GDSW_ERR_INVALID_ARG, "bad form");
+  c->opt = *opt;
+  if (c->opt.restart <= 0) c->opt.restart = 100;
+  if (c->opt.max_it <= 0) c->opt.max_it = 1000;
+  c->L = lv->levels;
+  double t0 = now_ms();
+  if (c->host_only) {
+    build_mesh(c->mesh, mesh);
+    const int nlev = c->L - 1;
+    c->lh.assign(nlev, LevelHost());
+    build_level1(c, part, lv->overlap, opt->slab_elems);
+    for (int l = 1; l < nlev; ++l) {
+      GDSW_CHECK(part->groups[l - 1] != nullptr, GDSW_ERR_INVALID_ARG, "null grouping array");
+      build_coarse_level(c, l, part->groups[l - 1], part->group_len[l - 1]);
+    }
+    c->setup_ms[0] = now_ms() - t0;
+    // device memory the full set-up would hold (factors, bases, operator, Krylov space)
+    const MeshHost& M = c->mesh;
+    double b = 8.0 * (9.0 * M.a_col.size() + 3.0 * M.bt_col.size() + 3.0 * M.b_col.size());
+    b += 4.0 * (M.a_col.size() + M.bt_col.size() + M.b_col.size() + 4.0 * M.n) + 8.0 * 27 * M.fluid.size();
+    for (int l = 0; l < nlev; ++l) {
+      const LevelHost& H = c->lh[l];
+      b += double(H.loc.nfac) * elem_size(opt->precision[l]) + 16.0 * H.loc.nvec + 16.0 * H.loc.nvec;
+      for (int J = 0; J < H.cs.nparts; ++J)  // Phi_I^T blocks
+        b += double(H.cs.ioff[J + 1] - H.cs.ioff[J]) * double(H.cs.coff[J + 1] - H.cs.coff[J]) *
+             elem_size(l == 0 ? opt->phi_precision : GDSW_FP64);
+    }
+    b += 8.0 * (2.0 * c->opt.restart + 2.0) * M.n;
+    c->est_device_bytes = int64_t(b);
+    return;
+  }
+  if (opt->stream) {
+    c->stream = static_cast<cudaStream_t>(opt->stream);
+  } else {
+    GDSW_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  GDSW_CUDA(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
+  GDSW_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  GDSW_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  cudaStream_t s = c->stream;
+  set_gemv_smem_limits();
+  set_prolong_smem_limits();
+  // ---- host symbolic set-up
+  build_mesh(c->mesh, mesh);
+  const int nlev = c->L - 1;
+  c->lh.assign(nlev, LevelHost());
+  c->ld.assign(nlev, LevelDev());
+  build_level1(c, part, lv->overlap, opt->slab_elems);
+  for (int l = 1; l < nlev; ++l) {
+    GDSW_CHECK(part->groups[l - 1] != nullptr, GDSW_ERR_INVALID_ARG, "null grouping array");
+    build_coarse_level(c, l, part->groups[l - 1], part->group_len[l - 1]);
+  }
+  double t1 = now_ms();
+  c->setup_ms[0] = t1 - t0;
+  // ---- device mesh and operator
+  MeshHost& M = c->mesh;
+  c->form = visc->form;
+  c->nu0 = visc->nu0;
+  c->nu_inf = visc->nu_inf;
+  c->lam = visc->lambda;
+  c->ncar = visc->n;
+  c->has_uk = visc->uk != nullptr;
+  upload_tables(c, s);
+  c->d_mask = c->arena.upload(M.mask, s);
+  c->d_fluid = c->arena.upload(M.fluid, s);
+  c->d_felem = c->arena.upload(M.felem, s);
+  c->d_vnode = c->arena.upload(M.vnode, s);
+  c->d_pnode = c->arena.upload(M.pnode, s);
+  c->d_a_ptr = c->arena.upload(M.a_ptr, s);
+  c->d_a_col = c->arena.upload(M.a_col, s);
+  c->d_bt_ptr = c->arena.upload(M.bt_ptr, s);
+  c->d_bt_col = c->arena.upload(M.bt_col, s);
+  c->d_b_ptr = c->arena.upload(M.b_ptr, s);
+  c->d_b_col = c->arena.upload(M.b_col, s);
+  c->d_bt2b = c->arena.upload(M.bt2b, s);
+  c->d_ad_ptr = c->arena.upload(M.ad_ptr, s);
+  c->d_ad_col = c->arena.upload(M.ad_col, s);
+  c->d_bd_ptr = c->arena.upload(M.bd_ptr, s);
+  c->d_bd_col = c->arena.upload(M.bd_col, s);
+  c->d_gdir = c->arena.upload(M.g, s);
+  c->d_uk = c->arena.alloc<double>(3 * M.nnodes);
+  if (visc->uk)
+    GDSW_CUDA(cudaMemcpyAsync(c->d_uk, visc->uk, 24 * M.nnodes, cudaMemcpyHostToDevice, s));
+  c->d_nu = c->arena.alloc<double>(27 * M.fluid.size());
+  c->nnzb = int64_t(M.a_col.size());
+  c->nbt = int64_t(M.bt_col.size());
+  c->nb = int64_t(M.b_col.size());
+  c->d_val = c->arena.alloc<double>(9 * c->nnzb + 3 * c->nbt + 3 * c->nb);
+  launch_viscosity(c, s);
+  launch_assembly(c, s);
+  GDSW_CUDA(cudaStreamSynchronize(s));
+  double t2 = now_ms();
+  c->setup_ms[1] = t2 - t1;
+  // ---- level 1
+  double minpiv = 0;
+  {
+    LevelDev& L = c->ld[0];
+    L.n = int(M.n);
+    L.N = c->lh[0].N;
+    const bool f64 = opt->precision[0] == GDSW_FP64;
+    if (f64)
+      level1_locals<double>(c, minpiv);
+    else
+      level1_locals<float>(c, minpiv);
+    GDSW_CHECK(minpiv > 0 && std::isfinite(minpiv), GDSW_ERR_SINGULAR, "level-1 local factorisation: zero pivot");
+    L.minpiv = minpiv;
+    const LevelHost& H = c->lh[0];
+    L.gdof = c->arena.upload(H.loc.gdof, s);
+    L.vec = c->arena.alloc<char>(size_t(2 * std::max<int64_t>(H.loc.nvec, 1)) * (L.prec == GDSW_FP64 ? 8 : 4));
+    GDSW_CUDA(cudaMemsetAsync(L.vec, 0, size_t(2 * std::max<int64_t>(H.loc.nvec, 1)) * (L.prec == GDSW_FP64 ? 8 : 4), s));
+    L.sc_ptr = c->arena.upload(H.sc_ptr, s);
+    L.sc_pos = c->arena.upload(H.sc_pos, s);
+    L.sc_w = c->arena.upload(H.sc_w, s);
+    build_local_plan(c, H.loc, L);
+    L.local_bytes = double(H.loc.nfac) * elem_size(L.prec) + 2.0 * H.loc.nvec * (L.prec == GDSW_FP64 ? 8 : 4);
+  }
+  double t3 = now_ms();
+  c->setup_ms[2] = t3 - t2;
+  // ---- level-1 coarse space and A_0^(2)
+  double* A0 = nullptr;
+  int64_t n0 = c->lh[0].cs.n0;
+  {
+    LevelDev& L = c->ld[0];
+    upload_coarse_space(c, 0, opt->phi_precision);
+    L.phi_bytes = 0;
+    if (n0 > 0) {
+      A0 = c->arena.alloc<double>(n0 * n0);
+      GDSW_CUDA(cudaMemsetAsync(A0, 0, n0 * n0 * 8, s));
+      if (opt->phi_precision == GDSW_FP64)
+        level1_coarse<double>(c, A0, minpiv);
+      else
+        level1_coarse<float>(c, A0, minpiv);
+      GDSW_CHECK(minpiv > 0 && std::isfinite(minpiv), GDSW_ERR_SINGULAR, "interior factorisation: zero pivot");
+      std::vector<int32_t> ld;
+      std::vector<int64_t> off = phi_offsets(c->lh[0].cs, ld);
+      L.phi_bytes = double(off.back()) * elem_size(opt->phi_precision);
+    }
+  }
+  double t4 = now_ms();
+  c->setup_ms[3] = t4 - t3;
+  // ---- coarse levels
+  for (int l = 1; l < nlev; ++l) {
+    LevelDev& L = c->ld[l];
+    const LevelHost& H = c->lh[l];
+    L.n = H.n;
+    L.N = H.N;
+    L.A = A0;
+    if (opt->precision[l] == GDSW_FP64)
+      coarse_locals<double>(c, l, minpiv);
+    else
+      coarse_locals<float>(c, l, minpiv);
+    GDSW_CHECK(minpiv > 0 && std::isfinite(minpiv), GDSW_ERR_SINGULAR, "coarse local factorisation: zero pivot");
+    L.minpiv = minpiv;
+    L.gdof = c->arena.upload(H.loc.gdof, s);
+    size_t vb = size_t(2 * std::max<int64_t>(H.loc.nvec, 1)) * (L.prec == GDSW_FP64 ? 8 : 4);
+    L.vec = c->arena.alloc<char>(vb);
+    GDSW_CUDA(cudaMemsetAsync(L.vec, 0, vb, s));
+    L.sc_ptr = c->arena.upload(H.sc_ptr, s);
+    L.sc_pos = c->arena.upload(H.sc_pos, s);
+    L.sc_w = c->arena.upload(H.sc_w, s);
+    build_local_plan(c, H.loc, L);
+    L.local_bytes = double(H.loc.nfac) * elem_size(L.prec) + 2.0 * H.loc.nvec * (L.prec == GDSW_FP64 ? 8 : 4);
+    upload_coarse_space(c, l, GDSW_FP64);
+    int64_t m0 = H.cs.n0;
+    double* A0n = nullptr;
+    if (m0 > 0) {
+      A0n = c->arena.alloc<double>(m0 * m0);
+      coarse_basis(c, l, A0n, minpiv);
+      GDSW_CHECK(minpiv > 0 && std::isfinite(minpiv), GDSW_ERR_SINGULAR, "coarse interior factorisation: zero pivot");
+      std::vector<int32_t> ldv;
+      std::vector<int64_t> off = phi_offsets(H.cs, ldv);
+      L.phi_bytes = double(off.back()) * 8.0;
+    }
+    A0 = A0n;
+    n0 = m0;
+  }
+  // ---- coarsest direct solve: explicit FP64 inverse of A_0^(L)
+  c->n_coarsest = int(n0);
+  c->coarsest_A = A0;
+  if (n0 > 0) {
+    int ldc = int(pad8(n0));
+    c->ld_coarsest = ldc;
+    c->d_coarsest_inv = c->arena.alloc<double>(n0 * ldc);
+    GDSW_CUDA(cudaMemsetAsync(c->d_coarsest_inv, 0, n0 * ldc * 8, s));
+    GDSW_CUDA(cudaMemcpy2DAsync(c->d_coarsest_inv, ldc * 8, A0, n0 * 8, n0 * 8, n0, cudaMemcpyDeviceToDevice, s));
+    DevArena tmp;
+    std::vector<double> mp;
+    run_inverse<double>(tmp, {{c->d_coarsest_inv, int(n0), ldc, 0}}, mp, s);
+    tmp.free_all();
+    GDSW_CHECK(mp[0] > 0 && std::isfinite(mp[0]), GDSW_ERR_SINGULAR, "coarsest operator is singular");
+    c->coarsest_minpiv = mp[0];
+    std::vector<GemvTask> tasks;
+    std::vector<GemvTile> tiles;
+    add_task(tasks, tiles, GemvTask{0, 0, 0, -1, int(n0), int(n0), ldc, 1.0f}, c->coarsest_plan.rows_per_tile);
+    c->coarsest_plan.launch_task_off = {0, int(tasks.size())};
+    c->coarsest_plan.launch_tile_off = {0, int(tiles.size())};
+    finish_plan(c->arena, c->coarsest_plan, tasks, tiles, s);
+  }
+  double t5 = now_ms();
+  c->setup_ms[4] = t5 - t4;
+  GDSW_CUDA(cudaStreamSynchronize(s));
+  if (opt->use_graph) capture_graph(c);
+  c->setup_ms[5] = now_ms() - t0;
+}
+
+}  // namespace gdsw
+
+using namespace gdsw;
+
+// ------------------------------------------------------------------ C ABI
+#define GDSW_TRY(ctx, body)                                                                  \
+  try {                                                                                      \
+    body;                                                                                    \
+    return GDSW_OK;                                                                          \
+  } catch (const gdsw::Error& e) {                                                           \
+    if (ctx) (ctx)->err = e.msg;                                                             \
+    return e.code;                                                                           \
+  } catch (const std::bad_alloc&) {                                                          \
+    if (ctx) (ctx)->err = "host allocation failed";                                          \
+    return GDSW_ERR_OOM;                                                                     \
+  } catch (...) {                                                                            \
+    if (ctx) (ctx)->err = "unknown error";                                                   \
+    return GDSW_ERR_CUDA;                                                                    \
+  }
+
+extern "C" {
+
+int gdsw_setup(const gdsw_mesh* mesh, const gdsw_viscosity* visc, const gdsw_partition* part, const gdsw_levels* lv,
+               const gdsw_options* opt, gdsw_ctx** out) {
+  if (!out) return GDSW_ERR_INVALID_ARG;
+  *out = nullptr;
+  gdsw_ctx* c = new (std::nothrow) gdsw_ctx();
+  if (!c) return GDSW_ERR_OOM;
+  int rc;
+  try {
+    setup_impl(c, mesh, visc, part, lv, opt);
+    rc = GDSW_OK;
+  } catch (const gdsw::Error& e) {
+    g_setup_error = e.msg;
+    rc = e.code;
+  } catch (const std::bad_alloc&) {
+    g_setup_error = "host allocation failed";
+    rc = GDSW_ERR_OOM;
+  } catch (...) {
+    g_setup_error = "unknown error";
+    rc = GDSW_ERR_CUDA;
+  }
+  if (rc != GDSW_OK) {
+    gdsw_destroy(c);
+    return rc;
+  }
+  g_setup_error.clear();
+  *out = c;
+  return GDSW_OK;
+}
+
+int gdsw_analyze(const gdsw_mesh* mesh, const gdsw_viscosity* visc, const gdsw_partition* part,
+                 const gdsw_levels* lv, const gdsw_options* opt, gdsw_ctx** out) {
+  if (!out) return GDSW_ERR_INVALID_ARG;
+  *out = nullptr;
+  gdsw_ctx* c = new (std::nothrow) gdsw_ctx();
+  if (!c) return GDSW_ERR_OOM;
+  c->host_only = true;
+  int rc = GDSW_OK;
+  try {
+    setup_impl(c, mesh, visc, part, lv, opt);
+  } catch (const gdsw::Error& e) {
+    g_setup_error = e.msg;
+    rc = e.code;
+  } catch (const std::bad_alloc&) {
+    g_setup_error = "host allocation failed";
+    rc = GDSW_ERR_OOM;
+  }
+  if (rc != GDSW_OK) {
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return GDSW_OK;
+}
+
+void gdsw_destroy(gdsw_ctx* c) {
+  if (!c) return;
+  if (c->host_only) {
+    delete c;
+    return;
+  }
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->apply_graph) cudaGraphExecDestroy(c->apply_graph);
+  for (auto& p : c->pending) {
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  c->arena.free_all();
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->stream2) cudaStreamDestroy(c->stream2);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* gdsw_last_error(const gdsw_ctx* c) { return c ? c->err.c_str() : g_setup_error.c_str(); }
+
+int gdsw_sizes(const gdsw_ctx* c, gdsw_sizes_info* info) {
+  if (!c || !info) return GDSW_ERR_INVALID_ARG;
+  gdsw_sizes_info s{};
+  s.n = c->mesh.n;
+  s.n_u = c->mesh.nu;
+  s.n_p = c->mesh.np;
+  s.n_elems = int64_t(c->mesh.fluid.size());
+  s.n_nodes = c->mesh.nnodes;
+  s.levels = c->L;
+  for (size_t l = 0; l < c->lh.size() && l < 3; ++l) {
+    s.n_coarse[l] = c->lh[l].cs.n0;
+    s.n_parts[l] = c->lh[l].N;
+    s.local_dofs[l] = c->lh[l].loc.nvec;
+    s.factor_entries[l] = c->lh[l].loc.nfac;
+    s.max_local[l] = c->lh[l].loc.max_local;
+  }
+  s.max_slabs = c->lh.empty() ? 0 : c->lh[0].loc.Kmax;
+  s.nnzb_A = c->nnzb;
+  s.nnz_B = c->nb;
+  s.phi_entries = c->lh.empty() ? 0 : int64_t(c->lh[0].cs.idofs.size());
+  s.device_bytes = c->host_only ? c->est_device_bytes : int64_t(c->arena.bytes);
+  for (int q = 0; q < 6; ++q) s.setup_ms[q] = c->setup_ms[q];
+  *info = s;
+  return GDSW_OK;
+}
+
+int gdsw_rhs_lift(gdsw_ctx* c, double* b) {
+  if (!c || c->host_only || !b) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, launch_lift(c, b, c->stream));
+}
+
+int gdsw_spmv(gdsw_ctx* c, const double* x, double* y) {
+  if (!c || c->host_only || !x || !y) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, {
+    ProfScope ps(c, GDSW_K_SPMV, c->spmv_bytes(), c->stream);
+    launch_spmv(c, x, y, nullptr, c->stream);
+  });
+}
+
+int gdsw_apply(gdsw_ctx* c, const double* r, double* z) {
+  if (!c || c->host_only || !r || !z) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, apply_precond(c, r, z, c->stream));
+}
+
+int gdsw_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info) {
+  if (!c || c->host_only || !b || !x) return GDSW_ERR_INVALID_ARG;
+  gdsw_solve_info tmp{};
+  if (!info) info = &tmp;
+  int rc;
+  try {
+    fgmres_solve(c, b, x, info);
+    rc = info->status;
+  } catch (const gdsw::Error& e) {
+    c->err = e.msg;
+    rc = e.code;
+  } catch (...) {
+    c->err = "unknown error";
+    rc = GDSW_ERR_CUDA;
+  }
+  return rc;
+}
+
+int gdsw_solve_host(gdsw_ctx* c, const double* bh, double* xh, gdsw_solve_info* info) {
+  if (!c || c->host_only || !bh || !xh) return GDSW_ERR_INVALID_ARG;
+  try {
+    if (!c->d_hb) {
+      c->d_hb = c->arena.alloc<double>(c->mesh.n);
+      c->d_hx = c->arena.alloc<double>(c->mesh.n);
+    }
+    GDSW_CUDA(cudaMemcpyAsync(c->d_hb, bh, 8 * c->mesh.n, cudaMemcpyHostToDevice, c->stream));
+    GDSW_CUDA(cudaMemcpyAsync(c->d_hx, xh, 8 * c->mesh.n, cudaMemcpyHostToDevice, c->stream));
+    int rc = gdsw_solve(c, c->d_hb, c->d_hx, info);
+    GDSW_CUDA(cudaMemcpyAsync(xh, c->d_hx, 8 * c->mesh.n, cudaMemcpyDeviceToHost, c->stream));
+    GDSW_CUDA(cudaStreamSynchronize(c->stream));
+    return rc;
+  } catch (const gdsw::Error& e) {
+    c->err = e.msg;
+    return e.code;
+  }
+}
+
+int gdsw_reassemble(gdsw_ctx* c, const double* uk) {
+  if (!c) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, {
+    if (uk) {
+      GDSW_CUDA(cudaMemcpyAsync(c->d_uk, uk, 24 * c->mesh.nnodes, cudaMemcpyHostToDevice, c->stream));
+      c->has_uk = true;
+    }
+    {
+      ProfScope ps(c, GDSW_K_VISCOSITY, 8.0 * 27 * c->mesh.fluid.size(), c->stream);
+      launch_viscosity(c, c->stream);
+    }
+    {
+      ProfScope ps(c, GDSW_K_ASSEMBLY, 8.0 * (9 * c->nnzb + 6 * c->nb), c->stream);
+      launch_assembly(c, c->stream);
+    }
+  });
+}
+
+int gdsw_apply_local(gdsw_ctx* c, int32_t level, const double* r, double* z) {
+  if (!c || c->host_only || level < 0 || level >= int(c->ld.size()) || !r || !z) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, local_solve(c, level, r, z, c->stream));
+}
+
+int gdsw_restrict(gdsw_ctx* c, int32_t level, const double* r, double* r0) {
+  if (!c || c->host_only || level < 0 || level >= int(c->ld.size()) || !r || !r0) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, restrict_level(c, level, r, r0, c->stream));
+}
+
+int gdsw_prolong(gdsw_ctx* c, int32_t level, const double* x0, double* z) {
+  if (!c || c->host_only || level < 0 || level >= int(c->ld.size()) || !x0 || !z) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, launch_prolong(c->ld[level], x0, z, c->stream));
+}
+
+int gdsw_coarse_matrix(gdsw_ctx* c, int32_t l, double* host) {
+  if (!c || c->host_only || !host || l < 0 || l >= c->L - 1) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, {
+    const double* A = (l + 1 < int(c->ld.size())) ? c->ld[l + 1].A : c->coarsest_A;
+    int64_t n = (l + 1 < int(c->ld.size())) ? c->ld[l + 1].n : c->n_coarsest;
+    if (n > 0) GDSW_CUDA(cudaMemcpy(host, A, 8 * n * n, cudaMemcpyDeviceToHost));
+  });
+}
+
+int gdsw_matrix_csr(gdsw_ctx* c, int64_t* row_ptr, int32_t* col, double* val, int64_t* nnz) {
+  if (!c || c->host_only || !nnz) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, {
+    const MeshHost& M = c->mesh;
+    int64_t total = 9 * c->nnzb + 3 * c->nbt + 3 * c->nb;
+    *nnz = total;
+    if (row_ptr && col && val) {
+      std::vector<double> v(total);
+      GDSW_CUDA(cudaMemcpy(v.data(), c->d_val, 8 * total, cudaMemcpyDeviceToHost));
+      const double* bt = v.data() + 9 * c->nnzb;
+      const double* bb = bt + 3 * c->nbt;
+      int64_t e = 0;
+      row_ptr[0] = 0;
+      for (int64_t I = 0; I < M.nv; ++I)
+        for (int cc = 0; cc < 3; ++cc) {
+          for (int32_t blk = M.a_ptr[I]; blk < M.a_ptr[I + 1]; ++blk)
+            for (int d = 0; d < 3; ++d) {
+              col[e] = 3 * M.a_col[blk] + d;
+              val[e++] = v[int64_t(blk) * 9 + cc * 3 + d];
+            }
+          for (int32_t q = M.bt_ptr[I]; q < M.bt_ptr[I + 1]; ++q) {
+            col[e] = int32_t(M.nu + M.bt_col[q]);
+            val[e++] = bt[int64_t(q) * 3 + cc];
+          }
+          row_ptr[3 * I + cc + 1] = e;
+        }
+      for (int64_t P = 0; P < M.np; ++P) {
+        for (int32_t q = M.b_ptr[P]; q < M.b_ptr[P + 1]; ++q)
+          for (int d = 0; d < 3; ++d) {
+            col[e] = 3 * M.b_col[q] + d;
+            val[e++] = bb[int64_t(q) * 3 + d];
+          }
+        row_ptr[M.nu + P + 1] = e;
+      }
+    }
+  });
+}
+
+int gdsw_viscosity_values(gdsw_ctx* c, double* host) {
+  if (!c || c->host_only || !host) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, GDSW_CUDA(cudaMemcpy(host, c->d_nu, 8 * 27 * c->mesh.fluid.size(), cudaMemcpyDeviceToHost)));
+}
+
+int gdsw_level_dofs(gdsw_ctx* c, int32_t level, int64_t* offsets, int32_t* dofs) {
+  if (!c || level < 0 || level >= int(c->lh.size()) || !offsets) return GDSW_ERR_INVALID_ARG;
+  const LevelHost& H = c->lh[level];
+  std::copy(H.dof_off.begin(), H.dof_off.end(), offsets);
+  if (dofs) std::copy(H.dof_sorted.begin(), H.dof_sorted.end(), dofs);
+  return GDSW_OK;
+}
+
+int gdsw_level_entities(gdsw_ctx* c, int32_t level, int32_t* n_entities) {
+  if (!c || level < 0 || level >= int(c->lh.size()) || !n_entities) return GDSW_ERR_INVALID_ARG;
+  *n_entities = c->lh[level].cs.n_entities;
+  return GDSW_OK;
+}
+
+int gdsw_profile_enable(gdsw_ctx* c, int32_t on) {
+  if (!c) return GDSW_ERR_INVALID_ARG;
+  c->prof.enabled = on ? 1 : 0;
+  return GDSW_OK;
+}
+
+int gdsw_profile_read(gdsw_ctx* c, gdsw_profile* p) {
+  if (!c || !p) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, {
+    prof_collect(c);
+    *p = c->prof;
+  });
+}
+
+int gdsw_profile_reset(gdsw_ctx* c) {
+  if (!c) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, {
+    prof_collect(c);
+    int en = c->prof.enabled;
+    c->prof = gdsw_profile{};
+    c->prof.enabled = en;
+  });
+}
+
+}  // extern "C"

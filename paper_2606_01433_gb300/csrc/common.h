@@ -1,0 +1,298 @@
+// Internal definitions shared by the translation units of libgdsw.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/gdsw.h"
+
+namespace gdsw {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define GDSW_CUDA(call)                                                                      \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::gdsw::Error{e_ == cudaErrorMemoryAllocation ? GDSW_ERR_OOM : GDSW_ERR_CUDA,    \
+                          std::string(#call) + ": " + cudaGetErrorString(e_)};              \
+  } while (0)
+
+#define GDSW_CHECK(cond, code, text)                                                         \
+  do {                                                                                       \
+    if (!(cond)) throw ::gdsw::Error{(code), (text)};                                        \
+  } while (0)
+
+inline void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error{GDSW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+// ------------------------------------------------------------------ device memory
+struct DevArena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  template <typename T>
+  T* alloc(size_t n) {
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    GDSW_CUDA(cudaMalloc(&p, n * sizeof(T)));
+    ptrs.push_back(p);
+    bytes += n * sizeof(T);
+    return static_cast<T*>(p);
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v, cudaStream_t s) {
+    T* p = alloc<T>(v.size());
+    if (!v.empty()) GDSW_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return p;
+  }
+  void release(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+      }
+  }
+  void free_all() {
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+inline size_t elem_size(int prec) { return prec == GDSW_FP64 ? 8 : (prec == GDSW_FP32 ? 4 : 2); }
+inline int64_t pad8(int64_t x) { return (x + 7) & ~int64_t(7); }
+
+// ------------------------------------------------------------------ device task descriptors
+// One dense matrix-vector product y[r] = base[r] + alpha * sum_c M[r, c] x[c] over rows of a
+// row-major block M (leading dimension ld, padded with zeros to a multiple of 8 columns).
+struct GemvTask {
+  int64_t mat;      // element offset of M in the factor buffer
+  int64_t x;        // element offset of x in the vector buffer
+  int64_t y;        // element offset of y
+  int64_t base;     // element offset of base (or -1: zero)
+  int32_t rows, cols, ld;
+  float alpha;
+};
+// A CTA's share of a GEMV launch: rows [row0, row0 + nrows) of task `task`.
+struct GemvTile {
+  int32_t task, row0;
+};
+
+// Batched GEMM C = alpha op(A) op(B) + beta C (row-major, element offsets into buffers).
+struct GemmTask {
+  int64_t a, b, c;
+  int32_t M, N, K, lda, ldb, ldc;
+  int32_t ta, tb;   // 1 = transposed operand
+  double alpha, beta;
+};
+
+// Batched dense inverse (in place) of square n x n blocks with leading dimension ld.
+struct InvTask {
+  int64_t a;        // element offset of the matrix
+  int32_t n, ld;
+  int32_t id;       // index into the status / scratch arrays
+};
+
+// ------------------------------------------------------------------ host symbolic structures
+// A batch of block-tridiagonal local problems: dof lists in slab order, slab sizes, the
+// number of back-coupled dofs (those coupled to the previous slab, ordered first) and the
+// offsets of the LDU blocks Sinv_k (s_k x s_k), G_k (m_k x s_{k-1}), W_k (s_k x m_{k+1}).
+struct SlabSet {
+  int nsub = 0;
+  int Kmax = 0;
+  std::vector<int> K;
+  std::vector<std::vector<int>> s, m;
+  std::vector<int64_t> voff;                 // subdomain offset in the concatenated local vector
+  std::vector<std::vector<int64_t>> soff;    // slab offset relative to voff
+  std::vector<std::vector<int64_t>> fS, fG, fW;
+  std::vector<std::vector<int>> ldS, ldG, ldW;
+  int64_t nvec = 0, nfac = 0;
+  std::vector<int32_t> gdof;                 // local position -> global dof of the level
+  int64_t max_local = 0;
+  void layout();                             // fills voff/soff/f*/ld*/nvec/nfac from s, m, K
+};
+
+// A coarse space towards the next level, in the form the apply uses on every level:
+// interior blocks Phi_I,J (stored transposed, c_J x n_IJ) per part, plus the interface map.
+struct CoarseSpace {
+  int n = 0;        // size of this level
+  int n0 = 0;       // coarse size
+  int nparts = 0;
+  std::vector<int32_t> idofs;       // concatenated interior dofs per part (slab order for level 1)
+  std::vector<int64_t> ioff;        // per part offset into idofs (nparts + 1)
+  std::vector<int32_t> cols;        // concatenated coarse columns per part (ascending)
+  std::vector<int64_t> coff;        // per part offset into cols (nparts + 1)
+  std::vector<int32_t> gdofs, gcol; // interface dofs (ascending) and their coarse column
+  // restriction reduce lists per coarse dof: positions in the concatenated per-part
+  // result buffer (offset coff[J] + local column) and interface dofs
+  std::vector<int32_t> rr_ptr, rr_pos, rg_ptr, rg_dof;
+  // coarse nodes of the next level: sharing set (parts of this level), dofs, modes
+  std::vector<std::vector<int>> cn_set;
+  std::vector<std::vector<int>> cn_dofs, cn_modes;
+  int n_entities = 0;
+};
+
+struct LevelHost {
+  int n = 0, N = 0;
+  SlabSet loc;                      // overlapping local problems
+  std::vector<int32_t> sc_ptr, sc_pos;   // scatter lists per dof of the level
+  std::vector<double> sc_w;              // weights (1/multiplicity or 1)
+  std::vector<int64_t> dof_off;     // sorted overlapping dof lists (for gdsw_level_dofs)
+  std::vector<int32_t> dof_sorted;
+  CoarseSpace cs;
+  SlabSet inter;                    // level 1: interior problems (slab order)
+};
+
+struct MeshHost {
+  int nx, ny, nz;
+  double h, origin[3];
+  int NX, NY, NZ;
+  int64_t nnodes;
+  std::vector<uint8_t> mask, tags;
+  std::vector<double> g;
+  std::vector<int32_t> felem;       // element -> fluid index or -1
+  std::vector<int32_t> fluid;       // fluid index -> element
+  std::vector<int32_t> vidx, pidx;  // node -> free velocity / pressure index, -1
+  std::vector<int32_t> vnode, pnode;// index -> node
+  std::vector<uint8_t> active;
+  int64_t nv = 0, np = 0, n = 0, nu = 0;
+  // patterns
+  std::vector<int32_t> a_ptr, a_col;     // velocity node rows x velocity node cols
+  std::vector<int32_t> bt_ptr, bt_col;   // velocity node rows x pressure cols
+  std::vector<int32_t> b_ptr, b_col;     // pressure rows x velocity node cols
+  std::vector<int32_t> bt2b;             // BT entry -> B entry with the same value
+  std::vector<int32_t> ad_ptr, ad_col;   // velocity rows x Dirichlet velocity nodes (node ids)
+  std::vector<int32_t> bd_ptr, bd_col;   // pressure rows x Dirichlet velocity nodes
+  bool shares_element(int64_t a, int64_t b) const;
+  void coords(int64_t node, int& i, int& j, int& k) const {
+    i = int(node % NX);
+    j = int((node / NX) % NY);
+    k = int(node / (int64_t(NX) * NY));
+  }
+};
+
+// ------------------------------------------------------------------ device-side level data
+struct GemvPlan {
+  std::vector<int> launch_task_off, launch_tile_off;  // nlaunch + 1
+  GemvTask* d_tasks = nullptr;
+  GemvTile* d_tiles = nullptr;
+  int rows_per_tile = 32;
+  int nlaunch() const { return int(launch_task_off.size()) - 1; }
+};
+
+struct LevelDev {
+  int n = 0, N = 0, prec = GDSW_FP64;
+  // local problems
+  void* fac = nullptr;          // factors in storage precision
+  int64_t nfac = 0, nvec = 0;
+  int32_t* gdof = nullptr;
+  GemvPlan fwd, bwd;            // forward launches (Sinv, G) and backward launches (W)
+  void* vec = nullptr;          // local vector workspace (2 * nvec, compute precision)
+  int32_t *sc_ptr = nullptr, *sc_pos = nullptr;
+  double* sc_w = nullptr;
+  // coarse space
+  int n0 = 0, phi_prec = GDSW_FP64;
+  int32_t *idofs = nullptr, *cols = nullptr, *gdofs = nullptr, *gcol = nullptr;
+  int64_t nidofs = 0, ncols = 0, ngamma = 0;
+  void* phiT = nullptr;         // concatenated Phi_I^T blocks
+  void* rI = nullptr;           // gathered interior residual (phi precision)
+  void* yc = nullptr;           // per-part restricted values (phi precision)
+  GemvPlan phi_plan;            // y_J = PhiT_J rI_J
+  int32_t *pro_part = nullptr;  // per prolongation tile: part
+  int64_t* pro_meta = nullptr;  // per part: phiT offset, ld, idofs offset, n_I, cols offset, c
+  int n_pro_tiles = 0;
+  int max_c = 0;
+  int max_ld_fwd = 0, max_ld_phi = 0;
+  std::vector<int> fwd_ld, bwd_ld;  // largest input length per launch
+  int32_t *pro_tile_part = nullptr, *pro_tile_col0 = nullptr;
+  int32_t *rr_ptr = nullptr, *rr_pos = nullptr, *rg_ptr = nullptr, *rg_dof = nullptr;
+  // level vectors (FP64)
+  double* r = nullptr;          // this level's right-hand side (coarse levels)
+  double* z = nullptr;          // this level's result (coarse levels)
+  double* x0 = nullptr;         // next-level solution (n0)
+  double* r0 = nullptr;         // restricted residual (n0)
+  double* zc = nullptr;         // local-branch result when the branches overlap
+  // dense coarse operator of THIS level (levels >= 2), FP64 row-major
+  double* A = nullptr;
+  double minpiv = 0;            // smallest pivot magnitude met by the local factorisation
+  double local_bytes = 0;       // algorithmic bytes of one local-solve sweep pair
+  double phi_bytes = 0;         // bytes of the stored Phi_I^T blocks
+};
+
+}  // namespace gdsw
+
+// ------------------------------------------------------------------ the context
+struct gdsw_ctx {
+  std::string err;
+  bool host_only = false;           // created by gdsw_analyze: no device state
+  int64_t est_device_bytes = 0;
+  cudaStream_t stream = nullptr, stream2 = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  gdsw_options opt{};
+  int L = 2;
+  gdsw::DevArena arena;
+  gdsw::MeshHost mesh;
+  std::vector<gdsw::LevelHost> lh;
+  std::vector<gdsw::LevelDev> ld;
+  // viscosity parameters
+  int form = GDSW_FORM_GRADIENT;
+  double nu0 = 1, nu_inf = 0, lam = 0, ncar = 1;
+  bool has_uk = false;
+  // device mesh / matrix
+  double* d_uk = nullptr;
+  double* d_nu = nullptr;           // nu[fluid element][27]
+  uint8_t* d_mask = nullptr;
+  int32_t* d_fluid = nullptr;       // fluid index -> element
+  int32_t* d_felem = nullptr;
+  int32_t *d_vnode = nullptr, *d_pnode = nullptr, *d_vidx = nullptr;
+  int32_t *d_a_ptr = nullptr, *d_a_col = nullptr, *d_bt_ptr = nullptr, *d_bt_col = nullptr;
+  int32_t *d_b_ptr = nullptr, *d_b_col = nullptr, *d_bt2b = nullptr;
+  int32_t *d_ad_ptr = nullptr, *d_ad_col = nullptr, *d_bd_ptr = nullptr, *d_bd_col = nullptr;
+  double* d_gdir = nullptr;         // Dirichlet datum, 3 per node
+  void* d_tables = nullptr;         // RefTables
+  double* d_val = nullptr;          // [A blocks (9 per block) | BT (3 per entry) | B (3 per entry)]
+  int64_t nnzb = 0, nbt = 0, nb = 0;
+  double* d_coarsest_inv = nullptr; // inverse of A_0^(L), FP64
+  int n_coarsest = 0;
+  int ld_coarsest = 8;
+  gdsw::GemvPlan coarsest_plan;
+  double* coarsest_A = nullptr;     // A_0^(L) itself (kept for inspection)
+  double coarsest_minpiv = 0;
+  double *d_hb = nullptr, *d_hx = nullptr;  // device staging for gdsw_solve_host
+  double spmv_bytes() const {
+    return 76.0 * nnzb + 28.0 * double(nbt + nb) + 16.0 * double(mesh.n) + 8.0 * double(mesh.nv + mesh.np);
+  }
+  // FGMRES workspace
+  int m_alloc = 0;
+  double *d_V = nullptr, *d_Z = nullptr, *d_w = nullptr, *d_H = nullptr, *d_gvec = nullptr;
+  double *d_cs = nullptr, *d_sn = nullptr, *d_part = nullptr, *d_scal = nullptr, *d_y = nullptr;
+  double* h_scal = nullptr;         // pinned host mirror of a few scalars
+  int n_part_blocks = 0;
+  int* d_status = nullptr;          // device error word
+  // CUDA graph of the apply
+  cudaGraphExec_t apply_graph = nullptr;
+  const double* graph_r = nullptr;
+  double* graph_z = nullptr;
+  double *d_graph_r = nullptr, *d_graph_z = nullptr;
+  // profiling
+  gdsw_profile prof{};
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending { int group; cudaEvent_t a, b; double bytes; };
+  std::vector<Pending> pending;
+  double bytes_group[12] = {0};
+  gdsw_sizes_info sizes{};
+  double setup_ms[6] = {0};
+};

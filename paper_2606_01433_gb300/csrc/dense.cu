@@ -1,0 +1,549 @@
+// Batched dense kernels: the ragged GEMV that carries every local and coarse solve of the
+// preconditioner apply (arXiv 2606.01433, Section 2.1/2.2: the A_i^{-1} terms, applied as
+// block-LDU sweeps with explicit inverse diagonal blocks), and the set-up kernels that
+// build those factors: a batched GEMM and a batched blocked Gauss-Jordan inverse with
+// partial pivoting.
+#include <cfloat>
+
+#include "common.h"
+#include "kernels.h"
+
+namespace gdsw {
+
+// ------------------------------------------------------------------ load helpers
+template <typename T> struct Vec16;
+template <> struct Vec16<double> { static constexpr int N = 2; };
+template <> struct Vec16<float> { static constexpr int N = 4; };
+template <> struct Vec16<__nv_bfloat16> { static constexpr int N = 8; };
+
+__device__ __forceinline__ void load16(const double* p, double* v) {
+  double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void load16(const float* p, float* v) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load16(const __nv_bfloat16* p, float* v) {
+  uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&t);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float2 f = __bfloat1622float2(h[q]);
+    v[2 * q] = f.x; v[2 * q + 1] = f.y;
+  }
+}
+// streaming (evict-first) variant for matrices read once per apply
+__device__ __forceinline__ void load16s(const double* p, double* v) {
+  double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+  v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void load16s(const float* p, float* v) {
+  float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load16s(const __nv_bfloat16* p, float* v) {
+  uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&t);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float2 f = __bfloat1622float2(h[q]);
+    v[2 * q] = f.x; v[2 * q + 1] = f.y;
+  }
+}
+
+// ------------------------------------------------------------------ ragged batched GEMV
+// One CTA = 8 warps = ROWS rows of one task; each warp owns ROWS/8 rows and streams them
+// with 16-byte loads (four rows in flight per warp).  The task's input vector is staged in
+// shared memory once per CTA.  y[r] = base[r] + alpha * sum_c M[r][c] x[c].
+template <typename TM, typename TV, int RPW>
+__global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV* xbase, TV* ybase,
+                                              const TV* bbase, const GemvTask* __restrict__ tasks,
+                                              const GemvTile* __restrict__ tiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TV* xs = reinterpret_cast<TV*>(smem_raw);
+  const GemvTile tl = tiles[blockIdx.x];
+  const GemvTask t = tasks[tl.task];
+  const int ld = t.ld;
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = c < t.cols ? xbase[t.x + c] : TV(0);
+  __syncthreads();
+  constexpr int V = Vec16<TM>::N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rbeg = tl.row0 + warp * RPW;
+  TV acc[RPW];
+  const TM* rowp[RPW];
+#pragma unroll
+  for (int q = 0; q < RPW; ++q) {
+    acc[q] = TV(0);
+    int r = rbeg + q;
+    rowp[q] = M + t.mat + int64_t(r < t.rows ? r : 0) * ld;
+  }
+  for (int c = lane * V; c < ld; c += 32 * V) {
+    TV xv[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) xv[u] = xs[c + u];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      if (rbeg + q < t.rows) {
+        TV mv[V];
+        load16s(rowp[q] + c, mv);
+#pragma unroll
+        for (int u = 0; u < V; ++u) acc[q] = fma(mv[u], xv[u], acc[q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RPW; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  }
+  if (lane < RPW) {
+    TV a = acc[0];
+#pragma unroll
+    for (int q = 1; q < RPW; ++q)
+      if (lane == q) a = acc[q];
+    int r = rbeg + lane;
+    if (r < t.rows) {
+      TV v = TV(t.alpha) * a;
+      if (t.base >= 0) v += bbase[t.base + r];
+      ybase[t.y + r] = v;
+    }
+  }
+}
+
+template <typename TM, typename TV>
+void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P, int launch, int max_ld,
+                 cudaStream_t s) {
+  int t0 = P.launch_tile_off[launch], t1 = P.launch_tile_off[launch + 1];
+  if (t1 <= t0) return;
+  size_t smem = size_t(max_ld) * sizeof(TV);
+  k_gemv<TM, TV, 4><<<t1 - t0, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+  check_launch("k_gemv");
+}
+
+template void launch_gemv<double, double>(const double*, const double*, double*, const double*, const GemvPlan&,
+                                          int, int, cudaStream_t);
+template void launch_gemv<float, float>(const float*, const float*, float*, const float*, const GemvPlan&, int,
+                                        int, cudaStream_t);
+template void launch_gemv<__nv_bfloat16, float>(const __nv_bfloat16*, const float*, float*, const float*,
+                                                const GemvPlan&, int, int, cudaStream_t);
+
+void set_gemv_smem_limits() {
+  cudaFuncSetAttribute(k_gemv<double, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<float, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<__nv_bfloat16, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+// ------------------------------------------------------------------ batched GEMM (set-up)
+// 64x64 output tile per CTA, 256 threads computing 4x4 each, K staged 16 at a time.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(const GemmTaskP* __restrict__ tasks, const int32_t* __restrict__ tile_task,
+                                              const int32_t* __restrict__ tile_id) {
+  __shared__ T As[16][64 + 1];
+  __shared__ T Bs[16][64 + 1];
+  const GemmTaskP t = tasks[tile_task[blockIdx.x]];
+  const int tiles_n = (t.N + 63) / 64;
+  const int tm = tile_id[blockIdx.x] / tiles_n, tn = tile_id[blockIdx.x] % tiles_n;
+  const T* A = static_cast<const T*>(t.a);
+  const T* B = static_cast<const T*>(t.b);
+  T* C = static_cast<T*>(t.c);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4] = {};
+  for (int k0 = 0; k0 < t.K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int kk = e / 64, mm = e % 64;
+      int gm = tm * 64 + mm, gk = k0 + kk;
+      T v = T(0);
+      if (gm < t.M && gk < t.K) v = t.ta ? A[int64_t(gk) * t.lda + gm] : A[int64_t(gm) * t.lda + gk];
+      As[kk][mm] = v;
+      int gn = tn * 64 + mm;
+      T w = T(0);
+      if (gn < t.N && gk < t.K) w = t.tb ? B[int64_t(gn) * t.ldb + gk] : B[int64_t(gk) * t.ldb + gn];
+      Bs[kk][mm] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gm = tm * 64 + ty * 4 + i;
+    if (gm >= t.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gn = tn * 64 + tx * 4 + j;
+      if (gn >= t.N) continue;
+      T* cp = C + int64_t(gm) * t.ldc + gn;
+      T v = T(t.alpha) * acc[i][j];
+      if (t.beta != 0.0) v += T(t.beta) * *cp;
+      *cp = v;
+    }
+  }
+}
+
+template <typename T>
+void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s) {
+  if (tasks.empty()) return;
+  std::vector<int32_t> tt, ti;
+  for (size_t q = 0; q < tasks.size(); ++q) {
+    const auto& t = tasks[q];
+    if (t.M <= 0 || t.N <= 0) continue;
+    int nt = ((t.M + 63) / 64) * ((t.N + 63) / 64);
+    for (int i = 0; i < nt; ++i) {
+      tt.push_back(int32_t(q));
+      ti.push_back(i);
+    }
+  }
+  if (tt.empty()) return;
+  GemmTaskP* d_t = tmp.upload(tasks, s);
+  int32_t* d_tt = tmp.upload(tt, s);
+  int32_t* d_ti = tmp.upload(ti, s);
+  for (size_t off = 0; off < tt.size(); off += 1 << 30) {
+    int nb = int(std::min<size_t>(tt.size() - off, size_t(1) << 30));
+    k_gemm<T><<<nb, 256, 0, s>>>(d_t, d_tt + off, d_ti + off);
+    check_launch("k_gemm");
+  }
+}
+template void run_gemm<double>(DevArena&, const std::vector<GemmTaskP>&, cudaStream_t);
+template void run_gemm<float>(DevArena&, const std::vector<GemmTaskP>&, cudaStream_t);
+
+// ------------------------------------------------------------------ batched Gauss-Jordan inverse
+// In-place inversion of square blocks with partial pivoting, blocked by panels of NB
+// columns: (1) LU with partial pivoting of the remaining rows of the panel chooses the
+// pivot rows, (2) those rows are swapped into place, (3) the NB x NB pivot block D is
+// inverted, (4) the block sweep A_PP <- D^-1, A_Pj <- D^-1 A_Pj, A_iP <- -A_iP D^-1,
+// A_ij <- A_ij - A_iP D^-1 A_Pj is applied as a rank-NB update, and (5) at the end the
+// columns are permuted back in reverse pivot order.
+constexpr int GJ_NB = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_panel(const InvTaskP* tasks, int kb, T* scratch, int64_t scr_stride,
+                                                  int32_t* piv, int64_t piv_stride, double* minpiv) {
+  const InvTaskP t = tasks[blockIdx.x];
+  if (kb >= t.n) return;
+  T* A = static_cast<T*>(t.a);
+  const int w = min(GJ_NB, t.n - kb), rows = t.n - kb;
+  T* P = scratch + int64_t(t.id) * scr_stride;  // rows x GJ_NB
+  int32_t* pv = piv + int64_t(t.id) * piv_stride;
+  for (int e = threadIdx.x; e < rows * w; e += blockDim.x) {
+    int r = e / w, c = e % w;
+    P[int64_t(r) * GJ_NB + c] = A[int64_t(kb + r) * t.ld + kb + c];
+  }
+  __syncthreads();
+  __shared__ double bv[256];
+  __shared__ int bi[256];
+  __shared__ T prow[GJ_NB];
+  for (int j = 0; j < w; ++j) {
+    double best = -1.0;
+    int besti = rows;
+    for (int r = j + threadIdx.x; r < rows; r += blockDim.x) {
+      double a = fabs(double(P[int64_t(r) * GJ_NB + j]));
+      if (a > best) { best = a; besti = r; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = besti;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        double a = bv[threadIdx.x + o];
+        int ia = bi[threadIdx.x + o];
+        if (a > bv[threadIdx.x] || (a == bv[threadIdx.x] && ia < bi[threadIdx.x])) {
+          bv[threadIdx.x] = a;
+          bi[threadIdx.x] = ia;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = bi[0];
+    const double pmag = bv[0];
+    if (threadIdx.x == 0) {
+      pv[kb + j] = kb + p;
+      if (pmag < minpiv[t.id]) minpiv[t.id] = pmag;
+    }
+    // swap rows j and p of the panel copy
+    if (p != j)
+      for (int c = threadIdx.x; c < w; c += blockDim.x) {
+        T a = P[int64_t(j) * GJ_NB + c];
+        P[int64_t(j) * GJ_NB + c] = P[int64_t(p) * GJ_NB + c];
+        P[int64_t(p) * GJ_NB + c] = a;
+      }
+    __syncthreads();
+    for (int c = threadIdx.x; c < w; c += blockDim.x) prow[c] = P[int64_t(j) * GJ_NB + c];
+    __syncthreads();
+    T d = prow[j];
+    if (d == T(0)) d = T(1);  // singular: recorded through minpiv, keep the numbers finite
+    for (int r = j + 1 + threadIdx.x; r < rows; r += blockDim.x) {
+      T* pr = P + int64_t(r) * GJ_NB;
+      T l = pr[j] / d;
+      pr[j] = l;
+      for (int c = j + 1; c < w; ++c) pr[c] -= l * prow[c];
+    }
+    __syncthreads();
+  }
+}
+
+// swap the chosen pivot rows into place across the full width of the matrix
+template <typename T>
+__global__ void k_gj_swap(const InvTaskP* tasks, int kb, const int32_t* piv, int64_t piv_stride) {
+  const InvTaskP t = tasks[blockIdx.y];
+  if (kb >= t.n) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= t.n) return;
+  T* A = static_cast<T*>(t.a);
+  const int32_t* pv = piv + int64_t(t.id) * piv_stride;
+  const int w = min(GJ_NB, t.n - kb);
+  for (int j = 0; j < w; ++j) {
+    int p = pv[kb + j];
+    if (p != kb + j) {
+      T a = A[int64_t(kb + j) * t.ld + c];
+      A[int64_t(kb + j) * t.ld + c] = A[int64_t(p) * t.ld + c];
+      A[int64_t(p) * t.ld + c] = a;
+    }
+  }
+}
+
+// invert the w x w pivot block (pivot order fixed by the panel LU, so no further pivoting)
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_dinv(const InvTaskP* tasks, int kb, T* dinv) {
+  const InvTaskP t = tasks[blockIdx.x];
+  if (kb >= t.n) return;
+  const T* A = static_cast<const T*>(t.a);
+  const int w = min(GJ_NB, t.n - kb);
+  __shared__ T D[GJ_NB][GJ_NB + 1];
+  __shared__ T colk[GJ_NB], rk[GJ_NB];
+  for (int e = threadIdx.x; e < GJ_NB * GJ_NB; e += blockDim.x) {
+    int r = e / GJ_NB, c = e % GJ_NB;
+    D[r][c] = (r < w && c < w) ? A[int64_t(kb + r) * t.ld + kb + c] : T(r == c ? 1 : 0);
+  }
+  __syncthreads();
+  const int r0 = threadIdx.x / GJ_NB, c = threadIdx.x % GJ_NB;  // 8 rows x 32 cols per pass
+  for (int k = 0; k < w; ++k) {
+    if (threadIdx.x < GJ_NB) {
+      colk[threadIdx.x] = D[threadIdx.x][k];
+      rk[threadIdx.x] = D[k][threadIdx.x];
+    }
+    __syncthreads();
+    T p = rk[k];
+    if (p == T(0)) p = T(1);
+    const T inv = T(1) / p;
+    for (int rr = r0; rr < GJ_NB; rr += 8) {
+      T v;
+      if (rr == k) v = (c == k) ? inv : rk[c] * inv;
+      else v = (c == k) ? -colk[rr] * inv : D[rr][c] - colk[rr] * rk[c] * inv;
+      D[rr][c] = v;
+    }
+    __syncthreads();
+  }
+  T* out = dinv + int64_t(t.id) * GJ_NB * GJ_NB;
+  for (int e = threadIdx.x; e < GJ_NB * GJ_NB; e += blockDim.x) out[e] = D[e / GJ_NB][e % GJ_NB];
+}
+
+// Fp = D^-1 A[P, :] (w x n) and E = A[:, P] (n x w) saved before the update
+template <typename T>
+__global__ void k_gj_fe(const InvTaskP* tasks, int kb, const T* dinv, T* Fp, T* E, int64_t stride) {
+  const InvTaskP t = tasks[blockIdx.y];
+  if (kb >= t.n) return;
+  const T* A = static_cast<const T*>(t.a);
+  const int w = min(GJ_NB, t.n - kb);
+  const T* Di = dinv + int64_t(t.id) * GJ_NB * GJ_NB;
+  T* F = Fp + int64_t(t.id) * stride;
+  T* Ee = E + int64_t(t.id) * stride;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= t.n) return;
+  // column idx of Fp
+  T col[GJ_NB];
+#pragma unroll
+  for (int q = 0; q < GJ_NB; ++q) col[q] = q < w ? A[int64_t(kb + q) * t.ld + idx] : T(0);
+  for (int r = 0; r < w; ++r) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < GJ_NB; ++q) s = fma(Di[r * GJ_NB + q], col[q], s);
+    F[int64_t(r) * t.n + idx] = s;
+  }
+  // row idx of E
+#pragma unroll
+  for (int q = 0; q < GJ_NB; ++q) Ee[int64_t(idx) * GJ_NB + q] = q < w ? A[int64_t(idx) * t.ld + kb + q] : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_update(const InvTaskP* tasks, const int32_t* tile_task,
+                                                   const int32_t* tile_id, int kb, const T* dinv, const T* Fp,
+                                                   const T* E, int64_t stride) {
+  const InvTaskP t = tasks[tile_task[blockIdx.x]];
+  if (kb >= t.n) return;
+  T* A = static_cast<T*>(t.a);
+  const int w = min(GJ_NB, t.n - kb);
+  const int tiles = (t.n + 63) / 64;
+  const int ti = tile_id[blockIdx.x] / tiles, tj = tile_id[blockIdx.x] % tiles;
+  const T* Di = dinv + int64_t(t.id) * GJ_NB * GJ_NB;
+  const T* F = Fp + int64_t(t.id) * stride;
+  const T* Ee = E + int64_t(t.id) * stride;
+  __shared__ T Es[64][GJ_NB + 1];
+  __shared__ T Fs[GJ_NB][64 + 1];
+  __shared__ T Ds[GJ_NB][GJ_NB + 1];
+  for (int e = threadIdx.x; e < 64 * GJ_NB; e += 256) {
+    int r = e / GJ_NB, q = e % GJ_NB;
+    int gi = ti * 64 + r;
+    Es[r][q] = (gi < t.n) ? Ee[int64_t(gi) * GJ_NB + q] : T(0);
+    int q2 = e / 64, c = e % 64;
+    int gj = tj * 64 + c;
+    Fs[q2][c] = (gj < t.n && q2 < w) ? F[int64_t(q2) * t.n + gj] : T(0);
+  }
+  for (int e = threadIdx.x; e < GJ_NB * GJ_NB; e += 256) Ds[e / GJ_NB][e % GJ_NB] = Di[e];
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int li = ty * 4 + a, gi = ti * 64 + li;
+    if (gi >= t.n) continue;
+    bool pi = gi >= kb && gi < kb + w;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int lj = tx * 4 + b, gj = tj * 64 + lj;
+      if (gj >= t.n) continue;
+      bool pj = gj >= kb && gj < kb + w;
+      T* ap = A + int64_t(gi) * t.ld + gj;
+      if (pi && pj) {
+        *ap = Ds[gi - kb][gj - kb];
+      } else if (pi) {
+        *ap = Fs[gi - kb][lj];
+      } else if (pj) {
+        T s = T(0);
+        for (int q = 0; q < w; ++q) s = fma(Es[li][q], Ds[q][gj - kb], s);
+        *ap = -s;
+      } else {
+        T s = *ap;
+        for (int q = 0; q < w; ++q) s = fma(-Es[li][q], Fs[q][lj], s);
+        *ap = s;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_gj_colperm(const InvTaskP* tasks, const int32_t* piv, int64_t piv_stride) {
+  const InvTaskP t = tasks[blockIdx.y];
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= t.n) return;
+  T* A = static_cast<T*>(t.a) + int64_t(r) * t.ld;
+  const int32_t* pv = piv + int64_t(t.id) * piv_stride;
+  for (int j = t.n - 1; j >= 0; --j) {
+    int p = pv[j];
+    if (p != j) {
+      T a = A[j];
+      A[j] = A[p];
+      A[p] = a;
+    }
+  }
+}
+
+__global__ void k_fill_d(double* p, double v, int64_t n) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// Invert every task's matrix in place; returns the smallest pivot magnitude per task.
+template <typename T>
+void run_inverse(DevArena& tmp, const std::vector<InvTaskP>& tasks_in, std::vector<double>& minpiv,
+                 cudaStream_t s) {
+  minpiv.assign(tasks_in.size(), 0.0);
+  std::vector<InvTaskP> tasks;
+  int nmax = 0;
+  for (size_t q = 0; q < tasks_in.size(); ++q) {
+    InvTaskP t = tasks_in[q];
+    t.id = int32_t(q);
+    if (t.n > 0) {
+      tasks.push_back(t);
+      nmax = std::max(nmax, t.n);
+    }
+  }
+  if (tasks.empty()) return;
+  const int nt = int(tasks.size());
+  const int64_t nq = int64_t(tasks_in.size());
+  const int64_t stride = int64_t(nmax) * GJ_NB;
+  T* scratch = tmp.alloc<T>(size_t(nq) * stride);
+  T* Fp = tmp.alloc<T>(size_t(nq) * stride);
+  T* E = tmp.alloc<T>(size_t(nq) * stride);
+  T* dinv = tmp.alloc<T>(size_t(nq) * GJ_NB * GJ_NB);
+  int32_t* piv = tmp.alloc<int32_t>(size_t(nq) * nmax);
+  double* d_min = tmp.alloc<double>(nq);
+  k_fill_d<<<int((nq + 255) / 256), 256, 0, s>>>(d_min, DBL_MAX, nq);
+  InvTaskP* d_tasks = tmp.upload(tasks, s);
+  std::vector<int32_t> tt, ti;
+  for (int q = 0; q < nt; ++q) {
+    int tl = (tasks[q].n + 63) / 64;
+    for (int i = 0; i < tl * tl; ++i) {
+      tt.push_back(q);
+      ti.push_back(i);
+    }
+  }
+  int32_t* d_tt = tmp.upload(tt, s);
+  int32_t* d_ti = tmp.upload(ti, s);
+  dim3 gcol((nmax + 255) / 256, nt);
+  for (int kb = 0; kb < nmax; kb += GJ_NB) {
+    k_gj_panel<T><<<nt, 256, 0, s>>>(d_tasks, kb, scratch, stride, piv, nmax, d_min);
+    k_gj_swap<T><<<gcol, 256, 0, s>>>(d_tasks, kb, piv, nmax);
+    k_gj_dinv<T><<<nt, 256, 0, s>>>(d_tasks, kb, dinv);
+    k_gj_fe<T><<<gcol, 256, 0, s>>>(d_tasks, kb, dinv, Fp, E, stride);
+    k_gj_update<T><<<int(tt.size()), 256, 0, s>>>(d_tasks, d_tt, d_ti, kb, dinv, Fp, E, stride);
+    check_launch("gauss-jordan panel");
+  }
+  k_gj_colperm<T><<<gcol, 256, 0, s>>>(d_tasks, piv, nmax);
+  check_launch("k_gj_colperm");
+  GDSW_CUDA(cudaMemcpyAsync(minpiv.data(), d_min, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
+  GDSW_CUDA(cudaStreamSynchronize(s));
+  for (size_t q = 0; q < tasks_in.size(); ++q)
+    if (tasks_in[q].n == 0) minpiv[q] = 1.0;
+  tmp.release(scratch); tmp.release(Fp); tmp.release(E); tmp.release(dinv); tmp.release(piv);
+  tmp.release(d_min); tmp.release(d_tasks); tmp.release(d_tt); tmp.release(d_ti);
+}
+template void run_inverse<double>(DevArena&, const std::vector<InvTaskP>&, std::vector<double>&, cudaStream_t);
+template void run_inverse<float>(DevArena&, const std::vector<InvTaskP>&, std::vector<double>&, cudaStream_t);
+
+// ------------------------------------------------------------------ conversions
+__global__ void k_f64_to_f32(const double* a, float* b, int64_t n) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) b[i] = float(a[i]);
+}
+__global__ void k_f32_to_f64(const float* a, double* b, int64_t n) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) b[i] = double(a[i]);
+}
+__global__ void k_f32_to_bf16(const float* a, __nv_bfloat16* b, int64_t n) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+__global__ void k_f64_to_bf16(const double* a, __nv_bfloat16* b, int64_t n) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn(float(a[i]));
+}
+void convert(const void* src, int sprec, void* dst, int dprec, int64_t n, cudaStream_t s) {
+  if (n == 0) return;
+  int blocks = int((n + 255) / 256);
+  if (sprec == GDSW_FP64 && dprec == GDSW_FP32)
+    k_f64_to_f32<<<blocks, 256, 0, s>>>(static_cast<const double*>(src), static_cast<float*>(dst), n);
+  else if (sprec == GDSW_FP32 && dprec == GDSW_FP64)
+    k_f32_to_f64<<<blocks, 256, 0, s>>>(static_cast<const float*>(src), static_cast<double*>(dst), n);
+  else if (sprec == GDSW_FP32 && dprec == GDSW_BF16)
+    k_f32_to_bf16<<<blocks, 256, 0, s>>>(static_cast<const float*>(src), static_cast<__nv_bfloat16*>(dst), n);
+  else if (sprec == GDSW_FP64 && dprec == GDSW_BF16)
+    k_f64_to_bf16<<<blocks, 256, 0, s>>>(static_cast<const double*>(src), static_cast<__nv_bfloat16*>(dst), n);
+  else if (sprec == dprec)
+    GDSW_CUDA(cudaMemcpyAsync(dst, src, n * elem_size(sprec), cudaMemcpyDeviceToDevice, s));
+  else
+    throw Error{GDSW_ERR_INVALID_ARG, "unsupported precision conversion"};
+  check_launch("convert");
+}
+
+}  // namespace gdsw

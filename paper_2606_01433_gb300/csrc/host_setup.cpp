@@ -1,0 +1,769 @@
+// Host symbolic setup: dof numbering, sparsity patterns, overlapping subdomains, slab
+// orderings of the local problems, interface entities and the coarse-space index maps of
+// every level (arXiv 2606.01433, Section 2.1 and Section 2.2).  No floating-point
+// arithmetic of the method happens here; the device does all numeric work.
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <map>
+#include <thread>
+
+#include "common.h"
+
+namespace gdsw {
+
+// ------------------------------------------------------------------ small utilities
+template <typename F>
+static void parallel_for(int64_t n, F f) {
+  int nt = int(std::thread::hardware_concurrency());
+  if (nt < 1) nt = 1;
+  if (nt > 32) nt = 32;
+  if (n < 4096 || nt == 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (n + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t) {
+    int64_t a = t * chunk, b = std::min(n, a + chunk);
+    if (a >= b) break;
+    th.emplace_back([=] {
+      for (int64_t i = a; i < b; ++i) f(i);
+    });
+  }
+  for (auto& x : th) x.join();
+}
+
+// elements (per axis) containing node coordinate c on an axis with n elements
+static inline int elem_range(int c, int n, int* e) {
+  int cnt = 0;
+  if (c % 2 == 0) {
+    if (c / 2 - 1 >= 0) e[cnt++] = c / 2 - 1;
+    if (c / 2 < n) e[cnt++] = c / 2;
+  } else {
+    e[cnt++] = c / 2;
+  }
+  return cnt;
+}
+
+bool MeshHost::shares_element(int64_t a, int64_t b) const {
+  int ia, ja, ka, ib, jb, kb;
+  coords(a, ia, ja, ka);
+  coords(b, ib, jb, kb);
+  int lo[3] = {std::max(ia, ib), std::max(ja, jb), std::max(ka, kb)};
+  int hi[3] = {std::min(ia, ib), std::min(ja, jb), std::min(ka, kb)};
+  int nn[3] = {nx, ny, nz};
+  int e0[3], e1[3];
+  for (int d = 0; d < 3; ++d) {
+    if (lo[d] - hi[d] > 2) return false;
+    // element e contains both iff 2e <= hi and 2e + 2 >= lo
+    e0[d] = std::max(0, (lo[d] - 1) / 2);  // ceil((lo-2)/2) for lo >= 0
+    if (lo[d] < 2) e0[d] = 0;
+    e1[d] = std::min(nn[d] - 1, hi[d] / 2);
+    if (e0[d] > e1[d]) return false;
+  }
+  for (int ez = e0[2]; ez <= e1[2]; ++ez)
+    for (int ey = e0[1]; ey <= e1[1]; ++ey)
+      for (int ex = e0[0]; ex <= e1[0]; ++ex)
+        if (mask[ex + int64_t(nx) * (ey + int64_t(ny) * ez)]) return true;
+  return false;
+}
+
+// visit every node within +-2 of `node` (in each direction) that shares a fluid element
+template <typename F>
+static void for_neighbors(const MeshHost& M, int64_t node, F f) {
+  int i, j, k;
+  M.coords(node, i, j, k);
+  for (int dk = -2; dk <= 2; ++dk) {
+    int kk = k + dk;
+    if (kk < 0 || kk >= M.NZ) continue;
+    for (int dj = -2; dj <= 2; ++dj) {
+      int jj = j + dj;
+      if (jj < 0 || jj >= M.NY) continue;
+      for (int di = -2; di <= 2; ++di) {
+        int ii = i + di;
+        if (ii < 0 || ii >= M.NX) continue;
+        int64_t w = ii + int64_t(M.NX) * (jj + int64_t(M.NY) * kk);
+        if (M.active[w] && M.shares_element(node, w)) f(w);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ mesh and patterns
+void build_mesh(MeshHost& M, const gdsw_mesh* m) {
+  M.nx = m->nx; M.ny = m->ny; M.nz = m->nz;
+  M.h = m->h;
+  for (int d = 0; d < 3; ++d) M.origin[d] = m->origin[d];
+  M.NX = 2 * M.nx + 1; M.NY = 2 * M.ny + 1; M.NZ = 2 * M.nz + 1;
+  M.nnodes = int64_t(M.NX) * M.NY * M.NZ;
+  int64_t ne = int64_t(M.nx) * M.ny * M.nz;
+  M.mask.assign(m->mask, m->mask + ne);
+  M.tags.assign(m->tags, m->tags + M.nnodes);
+  M.g.assign(m->g, m->g + 3 * M.nnodes);
+  M.felem.assign(ne, -1);
+  M.fluid.clear();
+  for (int64_t e = 0; e < ne; ++e)
+    if (M.mask[e]) {
+      M.felem[e] = int32_t(M.fluid.size());
+      M.fluid.push_back(int32_t(e));
+    }
+  GDSW_CHECK(!M.fluid.empty(), GDSW_ERR_INVALID_ARG, "mesh has no fluid element");
+  M.active.assign(M.nnodes, 0);
+  for (int32_t e : M.fluid) {
+    int ex = e % M.nx, ey = (e / M.nx) % M.ny, ez = e / (M.nx * M.ny);
+    for (int c = 0; c < 3; ++c)
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a)
+          M.active[(2 * ex + a) + int64_t(M.NX) * ((2 * ey + b) + int64_t(M.NY) * (2 * ez + c))] = 1;
+  }
+  M.vidx.assign(M.nnodes, -1);
+  M.pidx.assign(M.nnodes, -1);
+  M.vnode.clear();
+  M.pnode.clear();
+  for (int64_t v = 0; v < M.nnodes; ++v) {
+    if (!M.active[v]) continue;
+    uint8_t t = M.tags[v];
+    if (t != GDSW_TAG_WALL && t != GDSW_TAG_INFLOW) {
+      M.vidx[v] = int32_t(M.vnode.size());
+      M.vnode.push_back(int32_t(v));
+    }
+    int i, j, k;
+    M.coords(v, i, j, k);
+    if (i % 2 == 0 && j % 2 == 0 && k % 2 == 0) {
+      M.pidx[v] = int32_t(M.pnode.size());
+      M.pnode.push_back(int32_t(v));
+    }
+  }
+  M.nv = int64_t(M.vnode.size());
+  M.np = int64_t(M.pnode.size());
+  M.nu = 3 * M.nv;
+  M.n = M.nu + M.np;
+  GDSW_CHECK(M.n < (int64_t(1) << 31), GDSW_ERR_INVALID_ARG, "problem too large for int32 dof indices");
+
+  // neighbour lists (free velocity, pressure, Dirichlet velocity) per row node
+  auto build = [&](const std::vector<int32_t>& rows, int which, std::vector<int32_t>& ptr,
+                   std::vector<int32_t>& col) {
+    int64_t nr = int64_t(rows.size());
+    std::vector<std::vector<int32_t>> tmp(nr);
+    parallel_for(nr, [&](int64_t r) {
+      auto& out = tmp[r];
+      for_neighbors(M, rows[r], [&](int64_t w) {
+        if (which == 0) {
+          if (M.vidx[w] >= 0) out.push_back(M.vidx[w]);
+        } else if (which == 1) {
+          if (M.pidx[w] >= 0) out.push_back(M.pidx[w]);
+        } else {
+          uint8_t t = M.tags[w];
+          if (t == GDSW_TAG_WALL || t == GDSW_TAG_INFLOW) out.push_back(int32_t(w));
+        }
+      });
+      std::sort(out.begin(), out.end());
+    });
+    ptr.assign(nr + 1, 0);
+    for (int64_t r = 0; r < nr; ++r) ptr[r + 1] = ptr[r] + int32_t(tmp[r].size());
+    col.resize(ptr[nr]);
+    for (int64_t r = 0; r < nr; ++r) std::copy(tmp[r].begin(), tmp[r].end(), col.begin() + ptr[r]);
+  };
+  build(M.vnode, 0, M.a_ptr, M.a_col);
+  build(M.vnode, 1, M.bt_ptr, M.bt_col);
+  build(M.pnode, 0, M.b_ptr, M.b_col);
+  build(M.vnode, 2, M.ad_ptr, M.ad_col);
+  build(M.pnode, 2, M.bd_ptr, M.bd_col);
+  // BT entry (I, P) has the value of B entry (P, I)
+  M.bt2b.resize(M.bt_col.size());
+  for (int64_t I = 0; I < M.nv; ++I)
+    for (int32_t e = M.bt_ptr[I]; e < M.bt_ptr[I + 1]; ++e) {
+      int32_t P = M.bt_col[e];
+      auto b0 = M.b_col.begin() + M.b_ptr[P], b1 = M.b_col.begin() + M.b_ptr[P + 1];
+      auto it = std::lower_bound(b0, b1, int32_t(I));
+      GDSW_CHECK(it != b1 && *it == int32_t(I), GDSW_ERR_INVALID_ARG, "asymmetric B pattern");
+      M.bt2b[e] = int32_t(it - M.b_col.begin());
+    }
+}
+
+// ------------------------------------------------------------------ slab layout
+void SlabSet::layout() {
+  nsub = int(K.size());
+  voff.assign(nsub + 1, 0);
+  soff.assign(nsub, {});
+  fS.assign(nsub, {}); fG.assign(nsub, {}); fW.assign(nsub, {});
+  ldS.assign(nsub, {}); ldG.assign(nsub, {}); ldW.assign(nsub, {});
+  nfac = 0;
+  Kmax = 0;
+  max_local = 0;
+  for (int i = 0; i < nsub; ++i) {
+    Kmax = std::max(Kmax, K[i]);
+    int64_t off = 0;
+    for (int k = 0; k < K[i]; ++k) {
+      soff[i].push_back(off);
+      off += s[i][k];
+    }
+    voff[i + 1] = voff[i] + off;
+    max_local = std::max(max_local, off);
+    for (int k = 0; k < K[i]; ++k) {
+      int sk = s[i][k];
+      int ld = int(pad8(sk));
+      ldS[i].push_back(ld);
+      fS[i].push_back(nfac);
+      nfac += int64_t(sk) * ld;
+      // G_k: m_k x s_{k-1}
+      int ldg = k > 0 ? int(pad8(s[i][k - 1])) : 8;
+      ldG[i].push_back(ldg);
+      fG[i].push_back(nfac);
+      if (k > 0) nfac += int64_t(m[i][k]) * ldg;
+      // W_k: s_k x m_{k+1}
+      int ldw = k + 1 < K[i] ? int(pad8(m[i][k + 1])) : 8;
+      ldW[i].push_back(ldw);
+      fW[i].push_back(nfac);
+      if (k + 1 < K[i]) nfac += int64_t(sk) * ldw;
+    }
+  }
+  nvec = voff[nsub];
+}
+
+// Order the free dofs of a node set for a block-tridiagonal factorisation: slabs of
+// `t` element layers across the longest axis of the set (t = 0: one slab); inside each
+// slab the dofs of nodes coupled to the previous slab come first.  Appends to `S`.
+static void slab_order(const MeshHost& M, std::vector<int64_t> nodes, int t, SlabSet& S) {
+  std::sort(nodes.begin(), nodes.end());
+  if (nodes.empty()) {
+    S.K.push_back(0);
+    S.s.push_back({});
+    S.m.push_back({});
+    return;
+  }
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+  for (int64_t v : nodes) {
+    int c[3];
+    M.coords(v, c[0], c[1], c[2]);
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], c[d]);
+      hi[d] = std::max(hi[d], c[d]);
+    }
+  }
+  int ax = 0;
+  for (int d = 1; d < 3; ++d)
+    if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
+  int c0 = lo[ax] - (lo[ax] % 2);
+  // membership lookup over the bounding box
+  int bx = hi[0] - lo[0] + 1, by = hi[1] - lo[1] + 1, bz = hi[2] - lo[2] + 1;
+  std::vector<int32_t> box(int64_t(bx) * by * bz, -1);
+  auto bidx = [&](int i, int j, int k) { return (i - lo[0]) + int64_t(bx) * ((j - lo[1]) + int64_t(by) * (k - lo[2])); };
+  std::vector<int> raw(nodes.size());
+  for (size_t q = 0; q < nodes.size(); ++q) {
+    int c[3];
+    M.coords(nodes[q], c[0], c[1], c[2]);
+    box[bidx(c[0], c[1], c[2])] = int32_t(q);
+    raw[q] = t > 0 ? (c[ax] - c0) / (2 * t) : 0;
+  }
+  std::vector<int> uniq(raw);
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  std::vector<int> slab(nodes.size());
+  for (size_t q = 0; q < nodes.size(); ++q)
+    slab[q] = int(std::lower_bound(uniq.begin(), uniq.end(), raw[q]) - uniq.begin());
+  int K = int(uniq.size());
+  std::vector<uint8_t> back(nodes.size(), 0);
+  for (size_t q = 0; q < nodes.size(); ++q) {
+    if (slab[q] == 0) continue;
+    int c[3];
+    M.coords(nodes[q], c[0], c[1], c[2]);
+    bool found = false;
+    for (int dk = -2; dk <= 2 && !found; ++dk)
+      for (int dj = -2; dj <= 2 && !found; ++dj)
+        for (int di = -2; di <= 2 && !found; ++di) {
+          int i = c[0] + di, j = c[1] + dj, k = c[2] + dk;
+          if (i < lo[0] || i > hi[0] || j < lo[1] || j > hi[1] || k < lo[2] || k > hi[2]) continue;
+          int32_t w = box[bidx(i, j, k)];
+          if (w < 0 || slab[w] != slab[q] - 1) continue;
+          if (M.shares_element(nodes[q], nodes[w])) found = true;
+        }
+    back[q] = found;
+  }
+  std::vector<std::vector<int32_t>> A(K), B(K);
+  for (size_t q = 0; q < nodes.size(); ++q) {
+    int64_t v = nodes[q];
+    auto& dst = back[q] ? A[slab[q]] : B[slab[q]];
+    if (M.vidx[v] >= 0)
+      for (int c = 0; c < 3; ++c) dst.push_back(int32_t(3 * M.vidx[v] + c));
+    if (M.pidx[v] >= 0) dst.push_back(int32_t(M.nu + M.pidx[v]));
+  }
+  std::vector<int> s, m;
+  for (int k = 0; k < K; ++k) {
+    std::sort(A[k].begin(), A[k].end());
+    std::sort(B[k].begin(), B[k].end());
+    s.push_back(int(A[k].size() + B[k].size()));
+    m.push_back(int(A[k].size()));
+    S.gdof.insert(S.gdof.end(), A[k].begin(), A[k].end());
+    S.gdof.insert(S.gdof.end(), B[k].begin(), B[k].end());
+  }
+  // drop empty slabs (a slab can be empty of dofs if all its nodes are Dirichlet-only)
+  std::vector<int> s2, m2;
+  for (int k = 0; k < K; ++k)
+    if (s[k] > 0) {
+      s2.push_back(s[k]);
+      m2.push_back(m[k]);
+    } else if (k + 1 < K) {
+      m[k + 1] = 0;
+    }
+  if (!s2.empty()) m2[0] = 0;
+  S.K.push_back(int(s2.size()));
+  S.s.push_back(s2);
+  S.m.push_back(m2);
+}
+
+// One dense block holding sorted dofs (coarse levels).
+static void dense_order(const std::vector<int32_t>& dofs, SlabSet& S) {
+  std::vector<int32_t> d(dofs);
+  std::sort(d.begin(), d.end());
+  if (d.empty()) {
+    S.K.push_back(0);
+    S.s.push_back({});
+    S.m.push_back({});
+    return;
+  }
+  S.K.push_back(1);
+  S.s.push_back({int(d.size())});
+  S.m.push_back({0});
+  S.gdof.insert(S.gdof.end(), d.begin(), d.end());
+}
+
+static void scatter_lists(LevelHost& L, int weighting) {
+  const SlabSet& S = L.loc;
+  std::vector<int32_t> mult(L.n, 0);
+  for (int32_t g : S.gdof) mult[g]++;
+  L.sc_ptr.assign(L.n + 1, 0);
+  for (int32_t g : S.gdof) L.sc_ptr[g + 1]++;
+  for (int g = 0; g < L.n; ++g) L.sc_ptr[g + 1] += L.sc_ptr[g];
+  L.sc_pos.resize(S.gdof.size());
+  L.sc_w.resize(S.gdof.size());
+  std::vector<int32_t> fill(L.sc_ptr.begin(), L.sc_ptr.end() - 1);
+  for (int64_t p = 0; p < int64_t(S.gdof.size()); ++p) {
+    int32_t g = S.gdof[p];
+    L.sc_pos[fill[g]] = int32_t(p);
+    L.sc_w[fill[g]] = weighting == GDSW_WEIGHT_POU ? 1.0 / double(mult[g]) : 1.0;
+    fill[g]++;
+  }
+  // sorted overlapping dof lists per part
+  L.dof_off.assign(S.nsub + 1, 0);
+  L.dof_sorted.clear();
+  for (int i = 0; i < S.nsub; ++i) {
+    std::vector<int32_t> d(S.gdof.begin() + S.voff[i], S.gdof.begin() + S.voff[i + 1]);
+    std::sort(d.begin(), d.end());
+    L.dof_sorted.insert(L.dof_sorted.end(), d.begin(), d.end());
+    L.dof_off[i + 1] = int64_t(L.dof_sorted.size());
+  }
+}
+
+// restriction lists and part column lists, shared by every level
+static void coarse_lists(CoarseSpace& C, const std::vector<std::vector<int>>& ent_set,
+                         const std::vector<std::vector<int>>& ent_cols) {
+  // columns of every part: columns of entities whose set contains the part
+  std::vector<std::vector<int32_t>> pc(C.nparts);
+  for (size_t e = 0; e < ent_set.size(); ++e)
+    for (int p : ent_set[e])
+      for (int c : ent_cols[e]) pc[p].push_back(c);
+  C.coff.assign(C.nparts + 1, 0);
+  C.cols.clear();
+  for (int p = 0; p < C.nparts; ++p) {
+    std::sort(pc[p].begin(), pc[p].end());
+    C.cols.insert(C.cols.end(), pc[p].begin(), pc[p].end());
+    C.coff[p + 1] = int64_t(C.cols.size());
+  }
+  // restriction reduce: coarse column k <- parts in increasing order
+  std::vector<std::vector<int32_t>> rr(C.n0);
+  for (int p = 0; p < C.nparts; ++p)
+    for (int64_t q = C.coff[p]; q < C.coff[p + 1]; ++q) rr[C.cols[q]].push_back(int32_t(q));
+  C.rr_ptr.assign(C.n0 + 1, 0);
+  C.rr_pos.clear();
+  for (int k = 0; k < C.n0; ++k) {
+    C.rr_pos.insert(C.rr_pos.end(), rr[k].begin(), rr[k].end());
+    C.rr_ptr[k + 1] = int32_t(C.rr_pos.size());
+  }
+  std::vector<std::vector<int32_t>> rg(C.n0);
+  for (size_t q = 0; q < C.gdofs.size(); ++q) rg[C.gcol[q]].push_back(C.gdofs[q]);
+  C.rg_ptr.assign(C.n0 + 1, 0);
+  C.rg_dof.clear();
+  for (int k = 0; k < C.n0; ++k) {
+    std::sort(rg[k].begin(), rg[k].end());
+    C.rg_dof.insert(C.rg_dof.end(), rg[k].begin(), rg[k].end());
+    C.rg_ptr[k + 1] = int32_t(C.rg_dof.size());
+  }
+}
+
+// ------------------------------------------------------------------ level 1
+void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int slab_elems) {
+  MeshHost& M = ctx->mesh;
+  LevelHost& L = ctx->lh[0];
+  const int64_t ne = int64_t(M.nx) * M.ny * M.nz;
+  std::vector<int32_t> ep(ne, -1);
+  int N = 0;
+  for (int32_t e : M.fluid) {
+    int32_t p = part->elem_part[e];
+    GDSW_CHECK(p >= 0, GDSW_ERR_INVALID_ARG, "fluid element without subdomain");
+    ep[e] = p;
+    N = std::max(N, p + 1);
+  }
+  L.n = int(M.n);
+  L.N = N;
+  // element bounding boxes per subdomain
+  std::vector<std::array<int, 6>> bb(N, {1 << 30, 1 << 30, 1 << 30, -1, -1, -1});
+  std::vector<int> cnt(N, 0);
+  for (int32_t e : M.fluid) {
+    int c[3] = {int(e % M.nx), int((e / M.nx) % M.ny), int(e / (int64_t(M.nx) * M.ny))};
+    auto& b = bb[ep[e]];
+    for (int d = 0; d < 3; ++d) {
+      b[d] = std::min(b[d], c[d]);
+      b[3 + d] = std::max(b[3 + d], c[d]);
+    }
+    cnt[ep[e]]++;
+  }
+  for (int i = 0; i < N; ++i) GDSW_CHECK(cnt[i] > 0, GDSW_ERR_INVALID_ARG, "empty subdomain id");
+  // sharing sets of active nodes
+  std::vector<std::array<int32_t, 8>> sh(M.nnodes);
+  std::vector<uint8_t> nsh(M.nnodes, 0);
+  parallel_for(M.nnodes, [&](int64_t v) {
+    if (!M.active[v]) return;
+    int i, j, k, ei[2], ej[2], ek[2];
+    M.coords(v, i, j, k);
+    int ni = elem_range(i, M.nx, ei), nj = elem_range(j, M.ny, ej), nk = elem_range(k, M.nz, ek);
+    int32_t tmp[8];
+    int c = 0;
+    for (int a = 0; a < nk; ++a)
+      for (int b = 0; b < nj; ++b)
+        for (int d = 0; d < ni; ++d) {
+          int64_t e = ei[d] + int64_t(M.nx) * (ej[b] + int64_t(M.ny) * ek[a]);
+          if (M.mask[e]) tmp[c++] = ep[e];
+        }
+    std::sort(tmp, tmp + c);
+    int u = int(std::unique(tmp, tmp + c) - tmp);
+    for (int q = 0; q < u; ++q) sh[v][q] = tmp[q];
+    nsh[v] = uint8_t(u);
+  });
+  auto has_free = [&](int64_t v) { return M.vidx[v] >= 0 || M.pidx[v] >= 0; };
+
+  // ---- overlapping subdomains (Section 2.1: k layers of elements) ----
+  std::vector<std::vector<int64_t>> onodes(N);
+  parallel_for(N, [&](int64_t i) {
+    int lo[3], hi[3], nn[3] = {M.nx, M.ny, M.nz};
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::max(0, bb[i][d] - overlap);
+      hi[d] = std::min(nn[d] - 1, bb[i][3 + d] + overlap);
+    }
+    int E[3] = {hi[0] - lo[0] + 1, hi[1] - lo[1] + 1, hi[2] - lo[2] + 1};
+    int V[3] = {2 * E[0] + 1, 2 * E[1] + 1, 2 * E[2] + 1};
+    std::vector<uint8_t> em(int64_t(E[0]) * E[1] * E[2], 0), nm(int64_t(V[0]) * V[1] * V[2], 0);
+    auto gel = [&](int a, int b, int c) { return (lo[0] + a) + int64_t(M.nx) * ((lo[1] + b) + int64_t(M.ny) * (lo[2] + c)); };
+    auto lel = [&](int a, int b, int c) { return a + int64_t(E[0]) * (b + int64_t(E[1]) * c); };
+    auto lnd = [&](int a, int b, int c) { return a + int64_t(V[0]) * (b + int64_t(V[1]) * c); };
+    for (int c = 0; c < E[2]; ++c)
+      for (int b = 0; b < E[1]; ++b)
+        for (int a = 0; a < E[0]; ++a) em[lel(a, b, c)] = (ep[gel(a, b, c)] == i);
+    for (int it = 0; it < overlap; ++it) {
+      std::fill(nm.begin(), nm.end(), 0);
+      for (int c = 0; c < E[2]; ++c)
+        for (int b = 0; b < E[1]; ++b)
+          for (int a = 0; a < E[0]; ++a)
+            if (em[lel(a, b, c)])
+              for (int z = 0; z < 3; ++z)
+                for (int y = 0; y < 3; ++y)
+                  for (int x = 0; x < 3; ++x) nm[lnd(2 * a + x, 2 * b + y, 2 * c + z)] = 1;
+      for (int c = 0; c < E[2]; ++c)
+        for (int b = 0; b < E[1]; ++b)
+          for (int a = 0; a < E[0]; ++a) {
+            if (!M.mask[gel(a, b, c)]) continue;
+            bool any = false;
+            for (int z = 0; z < 3 && !any; ++z)
+              for (int y = 0; y < 3 && !any; ++y)
+                for (int x = 0; x < 3 && !any; ++x) any = nm[lnd(2 * a + x, 2 * b + y, 2 * c + z)];
+            if (any) em[lel(a, b, c)] = 1;
+          }
+    }
+    // nodes whose every fluid element lies in the overlapping subdomain
+    for (int c = 0; c < V[2]; ++c)
+      for (int b = 0; b < V[1]; ++b)
+        for (int a = 0; a < V[0]; ++a) {
+          int gi = 2 * lo[0] + a, gj = 2 * lo[1] + b, gk = 2 * lo[2] + c;
+          int64_t v = gi + int64_t(M.NX) * (gj + int64_t(M.NY) * gk);
+          if (!M.active[v] || !has_free(v)) continue;
+          int ei[2], ej[2], ek[2];
+          int ni = elem_range(gi, M.nx, ei), nj = elem_range(gj, M.ny, ej), nk = elem_range(gk, M.nz, ek);
+          bool all = true;
+          for (int z = 0; z < nk && all; ++z)
+            for (int y = 0; y < nj && all; ++y)
+              for (int x = 0; x < ni && all; ++x) {
+                int64_t e = ei[x] + int64_t(M.nx) * (ej[y] + int64_t(M.ny) * ek[z]);
+                if (!M.mask[e]) continue;
+                int la = ei[x] - lo[0], lb = ej[y] - lo[1], lc = ek[z] - lo[2];
+                if (la < 0 || lb < 0 || lc < 0 || la >= E[0] || lb >= E[1] || lc >= E[2] || !em[lel(la, lb, lc)])
+                  all = false;
+              }
+          if (all) onodes[i].push_back(v);
+        }
+  });
+  {
+    std::vector<SlabSet> parts(N);
+    parallel_for(N, [&](int64_t i) { slab_order(M, onodes[i], slab_elems, parts[i]); });
+    SlabSet& S = L.loc;
+    S = SlabSet();
+    for (int i = 0; i < N; ++i) {
+      S.K.push_back(parts[i].K[0]);
+      S.s.push_back(parts[i].s[0]);
+      S.m.push_back(parts[i].m[0]);
+      S.gdof.insert(S.gdof.end(), parts[i].gdof.begin(), parts[i].gdof.end());
+    }
+    S.layout();
+  }
+  scatter_lists(L, ctx->opt.weighting);
+
+  // ---- interface entities (Section 2.1) ----
+  std::map<std::vector<int32_t>, int> gid;
+  std::vector<int32_t> grp(M.nnodes, -1);
+  std::vector<std::vector<int32_t>> gset;
+  for (int64_t v = 0; v < M.nnodes; ++v) {
+    if (!M.active[v] || nsh[v] < 2 || !has_free(v)) continue;
+    std::vector<int32_t> key(sh[v].begin(), sh[v].begin() + nsh[v]);
+    auto it = gid.find(key);
+    if (it == gid.end()) {
+      it = gid.emplace(key, int(gset.size())).first;
+      gset.push_back(key);
+    }
+    grp[v] = it->second;
+  }
+  struct Ent { std::vector<int32_t> set; std::vector<int64_t> nodes; };
+  std::vector<Ent> ents;
+  {
+    std::vector<uint8_t> seen(M.nnodes, 0);
+    for (int64_t v = 0; v < M.nnodes; ++v) {
+      if (grp[v] < 0 || seen[v]) continue;
+      Ent E;
+      E.set = gset[grp[v]];
+      std::vector<int64_t> stack{v};
+      seen[v] = 1;
+      while (!stack.empty()) {
+        int64_t a = stack.back();
+        stack.pop_back();
+        E.nodes.push_back(a);
+        for_neighbors(M, a, [&](int64_t w) {
+          if (!seen[w] && grp[w] == grp[a]) {
+            seen[w] = 1;
+            stack.push_back(w);
+          }
+        });
+      }
+      std::sort(E.nodes.begin(), E.nodes.end());
+      ents.push_back(std::move(E));
+    }
+    std::sort(ents.begin(), ents.end(), [](const Ent& a, const Ent& b) {
+      if (a.set != b.set) return a.set < b.set;
+      return a.nodes[0] < b.nodes[0];
+    });
+  }
+  CoarseSpace& C = L.cs;
+  C.n = L.n;
+  C.nparts = N;
+  C.n_entities = int(ents.size());
+  std::vector<std::vector<int>> ent_cols(ents.size());
+  int n0 = 0;
+  std::vector<std::array<int, 4>> ecol(ents.size());
+  C.cn_set.clear(); C.cn_dofs.clear(); C.cn_modes.clear();
+  for (size_t e = 0; e < ents.size(); ++e) {
+    bool hv = false, hp = false;
+    for (int64_t v : ents[e].nodes) {
+      hv |= M.vidx[v] >= 0;
+      hp |= M.pidx[v] >= 0;
+    }
+    std::vector<int> dofs, modes;
+    for (int md = 0; md < 4; ++md) {
+      bool present = md < 3 ? hv : hp;
+      ecol[e][md] = present ? n0 : -1;
+      if (present) {
+        dofs.push_back(n0);
+        modes.push_back(md);
+        ent_cols[e].push_back(n0);
+        n0++;
+      }
+    }
+    C.cn_set.push_back(std::vector<int>(ents[e].set.begin(), ents[e].set.end()));
+    C.cn_dofs.push_back(dofs);
+    C.cn_modes.push_back(modes);
+  }
+  C.n0 = n0;
+  C.gdofs.clear();
+  C.gcol.clear();
+  {
+    std::vector<std::pair<int32_t, int32_t>> gl;
+    for (size_t e = 0; e < ents.size(); ++e)
+      for (int64_t v : ents[e].nodes) {
+        if (M.vidx[v] >= 0)
+          for (int c = 0; c < 3; ++c) gl.push_back({int32_t(3 * M.vidx[v] + c), ecol[e][c]});
+        if (M.pidx[v] >= 0) gl.push_back({int32_t(M.nu + M.pidx[v]), ecol[e][3]});
+      }
+    std::sort(gl.begin(), gl.end());
+    for (auto& q : gl) {
+      C.gdofs.push_back(q.first);
+      C.gcol.push_back(q.second);
+    }
+  }
+  // interiors: nodes whose sharing set is {i}
+  std::vector<std::vector<int64_t>> inodes(N);
+  for (int64_t v = 0; v < M.nnodes; ++v)
+    if (M.active[v] && nsh[v] == 1 && has_free(v)) inodes[sh[v][0]].push_back(v);
+  {
+    std::vector<SlabSet> parts(N);
+    parallel_for(N, [&](int64_t i) { slab_order(M, inodes[i], slab_elems, parts[i]); });
+    SlabSet& S = L.inter;
+    S = SlabSet();
+    for (int i = 0; i < N; ++i) {
+      S.K.push_back(parts[i].K[0]);
+      S.s.push_back(parts[i].s[0]);
+      S.m.push_back(parts[i].m[0]);
+      S.gdof.insert(S.gdof.end(), parts[i].gdof.begin(), parts[i].gdof.end());
+    }
+    S.layout();
+    C.idofs = S.gdof;
+    C.ioff = S.voff;
+  }
+  std::vector<std::vector<int>> eset(ents.size());
+  for (size_t e = 0; e < ents.size(); ++e) eset[e] = C.cn_set[e];
+  coarse_lists(C, eset, ent_cols);
+}
+
+// ------------------------------------------------------------------ coarse levels
+void build_coarse_level(gdsw_ctx* ctx, int l, const int32_t* group, int group_len) {
+  CoarseSpace& P = ctx->lh[l - 1].cs;     // coarse space of the finer level
+  LevelHost& L = ctx->lh[l];
+  const int nn = int(P.cn_set.size());
+  GDSW_CHECK(group_len == P.nparts, GDSW_ERR_INVALID_ARG, "grouping array has the wrong length");
+  int N = 0;
+  for (int p = 0; p < group_len; ++p) {
+    GDSW_CHECK(group[p] >= 0, GDSW_ERR_INVALID_ARG, "negative group id");
+    N = std::max(N, group[p] + 1);
+  }
+  L.n = P.n0;
+  L.N = N;
+  std::vector<std::vector<int>> R(nn);
+  for (int v = 0; v < nn; ++v) {
+    for (int p : P.cn_set[v]) R[v].push_back(group[p]);
+    std::sort(R[v].begin(), R[v].end());
+    R[v].erase(std::unique(R[v].begin(), R[v].end()), R[v].end());
+  }
+  // coupling: sharing sets intersect
+  std::vector<std::vector<int>> byp(P.nparts);
+  for (int v = 0; v < nn; ++v)
+    for (int p : P.cn_set[v]) byp[p].push_back(v);
+  auto neighbors = [&](int v, std::vector<int>& out) {
+    out.clear();
+    for (int p : P.cn_set[v]) out.insert(out.end(), byp[p].begin(), byp[p].end());
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+  };
+  std::vector<std::vector<int>> closure(N);
+  for (int v = 0; v < nn; ++v)
+    for (int J : R[v]) closure[J].push_back(v);
+  SlabSet& S = L.loc;
+  S = SlabSet();
+  std::vector<int> nb;
+  for (int J = 0; J < N; ++J) {
+    std::vector<char> in(nn, 0);
+    for (int v : closure[J]) {
+      in[v] = 1;
+      neighbors(v, nb);
+      for (int w : nb) in[w] = 1;
+    }
+    std::vector<int32_t> d;
+    for (int v = 0; v < nn; ++v)
+      if (in[v])
+        for (int dd : P.cn_dofs[v]) d.push_back(dd);
+    dense_order(d, S);
+  }
+  S.layout();
+  scatter_lists(L, ctx->opt.weighting);
+  // entities of this level
+  std::map<std::vector<int>, int> gid;
+  std::vector<int> grp(nn, -1);
+  for (int v = 0; v < nn; ++v) {
+    if (R[v].size() < 2) continue;
+    auto it = gid.find(R[v]);
+    if (it == gid.end()) it = gid.emplace(R[v], int(gid.size())).first;
+    grp[v] = it->second;
+  }
+  struct Ent { std::vector<int> set; std::vector<int> nodes; };
+  std::vector<Ent> ents;
+  std::vector<char> seen(nn, 0);
+  for (int v = 0; v < nn; ++v) {
+    if (grp[v] < 0 || seen[v]) continue;
+    Ent E;
+    E.set = R[v];
+    std::vector<int> stack{v};
+    seen[v] = 1;
+    while (!stack.empty()) {
+      int a = stack.back();
+      stack.pop_back();
+      E.nodes.push_back(a);
+      neighbors(a, nb);
+      for (int w : nb)
+        if (!seen[w] && grp[w] == grp[a]) {
+          seen[w] = 1;
+          stack.push_back(w);
+        }
+    }
+    std::sort(E.nodes.begin(), E.nodes.end());
+    ents.push_back(std::move(E));
+  }
+  std::sort(ents.begin(), ents.end(), [](const Ent& a, const Ent& b) {
+    if (a.set != b.set) return a.set < b.set;
+    return a.nodes[0] < b.nodes[0];
+  });
+  CoarseSpace& C = L.cs;
+  C = CoarseSpace();
+  C.n = L.n;
+  C.nparts = N;
+  C.n_entities = int(ents.size());
+  int n0 = 0;
+  std::vector<std::vector<int>> ent_cols(ents.size()), eset(ents.size());
+  std::vector<std::pair<int32_t, int32_t>> gl;
+  for (size_t e = 0; e < ents.size(); ++e) {
+    bool present[4] = {false, false, false, false};
+    for (int v : ents[e].nodes)
+      for (int md : P.cn_modes[v]) present[md] = true;
+    int col[4];
+    std::vector<int> dofs, modes;
+    for (int md = 0; md < 4; ++md) {
+      col[md] = present[md] ? n0 : -1;
+      if (present[md]) {
+        dofs.push_back(n0);
+        modes.push_back(md);
+        ent_cols[e].push_back(n0);
+        n0++;
+      }
+    }
+    for (int v : ents[e].nodes)
+      for (size_t q = 0; q < P.cn_dofs[v].size(); ++q) gl.push_back({P.cn_dofs[v][q], col[P.cn_modes[v][q]]});
+    C.cn_set.push_back(ents[e].set);
+    C.cn_dofs.push_back(dofs);
+    C.cn_modes.push_back(modes);
+    eset[e] = ents[e].set;
+  }
+  C.n0 = n0;
+  std::sort(gl.begin(), gl.end());
+  for (auto& q : gl) {
+    C.gdofs.push_back(q.first);
+    C.gcol.push_back(q.second);
+  }
+  // interiors: nodes whose part set is {J}
+  SlabSet& I = L.inter;
+  I = SlabSet();
+  std::vector<std::vector<int32_t>> idof(N);
+  for (int v = 0; v < nn; ++v)
+    if (R[v].size() == 1)
+      for (int dd : P.cn_dofs[v]) idof[R[v][0]].push_back(dd);
+  for (int J = 0; J < N; ++J) dense_order(idof[J], I);
+  I.layout();
+  C.idofs = I.gdof;
+  C.ioff = I.voff;
+  coarse_lists(C, eset, ent_cols);
+}
+
+}  // namespace gdsw

@@ -1,0 +1,65 @@
+// Declarations of the kernel launchers shared between translation units.
+#pragma once
+
+#include "common.h"
+
+namespace gdsw {
+
+struct GemmTaskP {
+  const void* a;
+  const void* b;
+  void* c;
+  int32_t M, N, K, lda, ldb, ldc;
+  int32_t ta, tb;
+  double alpha, beta;
+};
+
+struct InvTaskP {
+  void* a;
+  int32_t n, ld;
+  int32_t id;
+};
+
+// Q2 / Q1 reference tables at the 27 Gauss points (host computed, device resident)
+struct RefTables {
+  double dphi[27][27][3];   // [q][a][l]
+  double psi[27][8];        // [q][P]
+  double w[27];
+};
+void host_tables(RefTables& T);
+
+// dense.cu
+template <typename TM, typename TV>
+void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P, int launch, int max_ld,
+                 cudaStream_t s);
+void set_gemv_smem_limits();
+template <typename T>
+void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s);
+template <typename T>
+void run_inverse(DevArena& tmp, const std::vector<InvTaskP>& tasks, std::vector<double>& minpiv, cudaStream_t s);
+void convert(const void* src, int sprec, void* dst, int dprec, int64_t n, cudaStream_t s);
+
+// operator.cu
+void launch_viscosity(gdsw_ctx* c, cudaStream_t s);
+void launch_assembly(gdsw_ctx* c, cudaStream_t s);
+void launch_lift(gdsw_ctx* c, double* b, cudaStream_t s);
+void launch_spmv(gdsw_ctx* c, const double* x, double* y, const double* b, cudaStream_t s);
+void upload_tables(gdsw_ctx* c, cudaStream_t s);
+
+// schwarz.cu
+struct ProMeta {
+  int64_t phi, ioff, coff;
+  int32_t ld, nI, c, pad;
+};
+template <typename TV>
+void launch_gather(const double* r, const int32_t* idx, TV* out, int64_t n, cudaStream_t s);
+template <typename TV>
+void launch_scatter(const TV* x, const int32_t* ptr, const int32_t* pos, const double* w, double* z, int n,
+                    int accumulate, cudaStream_t s);
+void launch_restrict_reduce(const void* yc, int prec, const double* r, const int32_t* rr_ptr, const int32_t* rr_pos,
+                            const int32_t* rg_ptr, const int32_t* rg_dof, double* r0, int n0, cudaStream_t s);
+void launch_prolong(const LevelDev& L, const double* x0, double* z, cudaStream_t s);
+void launch_axpy_gamma(const int32_t* gdofs, const int32_t* gcol, int64_t ng, const double* x0, double* z,
+                       cudaStream_t s);
+
+}  // namespace gdsw

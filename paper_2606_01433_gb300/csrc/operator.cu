@@ -1,0 +1,359 @@
+// The saddle-point operator on the device: Carreau viscosity at the Gauss points, the
+// assembly of A_cal = [[A, B^T], [B, 0]], the Dirichlet lifting and the FP64 SpMV.
+//   arXiv 2606.01433, Section 2 (weak form, saddle-point equation), Section 3 (Carreau
+//   law nu = nu0 (1 + (lambda gamma_dot)^2)^((n-1)/2), gamma_dot = sqrt(2 D:D), here with
+//   an infinite-shear offset nu_inf; symmetric form 2 nu D(u):D(v)).
+// Storage: 3x3 velocity blocks per (free velocity node, free velocity node) pair sharing
+// a fluid element (row-major block, 72 bytes); pressure-velocity entries as 3-vectors in
+// both row orientations (B rows per pressure node, B^T rows per velocity node).
+#include "common.h"
+#include "kernels.h"
+
+namespace gdsw {
+
+void host_tables(RefTables& T) {
+  const double gx[3] = {-0.7745966692414834, 0.0, 0.7745966692414834};  // -sqrt(3/5), 0, sqrt(3/5)
+  const double gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+  auto q2 = [](int a, double x) { return a == 0 ? 0.5 * x * (x - 1.0) : (a == 1 ? 1.0 - x * x : 0.5 * x * (x + 1.0)); };
+  auto dq2 = [](int a, double x) { return a == 0 ? x - 0.5 : (a == 1 ? -2.0 * x : x + 0.5); };
+  auto q1 = [](int a, double x) { return a == 0 ? 0.5 * (1.0 - x) : 0.5 * (1.0 + x); };
+  for (int qz = 0; qz < 3; ++qz)
+    for (int qy = 0; qy < 3; ++qy)
+      for (int qx = 0; qx < 3; ++qx) {
+        int q = qx + 3 * qy + 9 * qz;
+        double x = gx[qx], y = gx[qy], z = gx[qz];
+        T.w[q] = gw[qx] * gw[qy] * gw[qz];
+        for (int az = 0; az < 3; ++az)
+          for (int ay = 0; ay < 3; ++ay)
+            for (int ax = 0; ax < 3; ++ax) {
+              int a = ax + 3 * ay + 9 * az;
+              T.dphi[q][a][0] = dq2(ax, x) * q2(ay, y) * q2(az, z);
+              T.dphi[q][a][1] = q2(ax, x) * dq2(ay, y) * q2(az, z);
+              T.dphi[q][a][2] = q2(ax, x) * q2(ay, y) * dq2(az, z);
+            }
+        for (int pz = 0; pz < 2; ++pz)
+          for (int py = 0; py < 2; ++py)
+            for (int px = 0; px < 2; ++px) T.psi[q][px + 2 * py + 4 * pz] = q1(px, x) * q1(py, y) * q1(pz, z);
+      }
+}
+
+struct Geo {
+  int nx, ny, nz, NX, NY;
+  double h;
+};
+
+__device__ __forceinline__ void node_ijk(int64_t v, const Geo& G, int& i, int& j, int& k) {
+  i = int(v % G.NX);
+  j = int((v / G.NX) % G.NY);
+  k = int(v / (int64_t(G.NX) * G.NY));
+}
+
+// elements (per axis) containing both node coordinates a and b
+__device__ __forceinline__ int shared_range(int a, int b, int n, int& e0) {
+  int lo = max(a, b), hi = min(a, b);
+  if (lo - hi > 2) return 0;
+  e0 = lo < 2 ? 0 : (lo - 1) / 2;
+  int e1 = min(n - 1, hi / 2);
+  return e1 >= e0 ? e1 - e0 + 1 : 0;
+}
+
+// ------------------------------------------------------------------ a1: Carreau viscosity
+__global__ void k_viscosity(const int32_t* __restrict__ fluid, int64_t nfe, const double* __restrict__ uk,
+                            const RefTables* __restrict__ T, Geo G, int form, int has_uk, double nu0, double nu_inf,
+                            double lam, double ncar, double* __restrict__ nu) {
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= nfe * 27) return;
+  int64_t fe = t / 27;
+  int q = int(t - fe * 27);
+  if (!has_uk || form == GDSW_FORM_GRADIENT) {
+    nu[t] = nu0;
+    return;
+  }
+  int e = fluid[fe];
+  int ex = e % G.nx, ey = (e / G.nx) % G.ny, ez = e / (G.nx * G.ny);
+  double gr[3][3] = {};
+  for (int a = 0; a < 27; ++a) {
+    int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+    int64_t v = (2 * ex + ax) + int64_t(G.NX) * ((2 * ey + ay) + int64_t(G.NY) * (2 * ez + az));
+    const double* dp = T->dphi[q][a];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double u = uk[3 * v + c];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) gr[c][l] = fma(u, dp[l], gr[c][l]);
+    }
+  }
+  const double s = 2.0 / G.h;
+  double dd = 0.0;  // D : D
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double d = 0.5 * s * (gr[c][l] + gr[l][c]);
+      dd = fma(d, d, dd);
+    }
+  double gdot = sqrt(2.0 * dd);
+  double lg = lam * gdot;
+  nu[t] = nu_inf + (nu0 - nu_inf) * pow(1.0 + lg * lg, 0.5 * (ncar - 1.0));
+}
+
+// 3x3 velocity block between nodes I and J (Section 2 gradient form / Section 3 symmetric form)
+__device__ void velocity_block(int64_t I, int64_t J, const Geo& G, const uint8_t* mask, const int32_t* felem,
+                               const double* nu, const RefTables* T, int form, double out[9]) {
+  int ii, ij, ik, ji, jj, jk;
+  node_ijk(I, G, ii, ij, ik);
+  node_ijk(J, G, ji, jj, jk);
+#pragma unroll
+  for (int c = 0; c < 9; ++c) out[c] = 0.0;
+  int e0x, e0y, e0z;
+  int nxr = shared_range(ii, ji, G.nx, e0x), nyr = shared_range(ij, jj, G.ny, e0y), nzr = shared_range(ik, jk, G.nz, e0z);
+  const double sc = 0.5 * G.h;  // (h/2)^3 * (2/h)^2
+  for (int cz = 0; cz < nzr; ++cz)
+    for (int cy = 0; cy < nyr; ++cy)
+      for (int cx = 0; cx < nxr; ++cx) {
+        int ex = e0x + cx, ey = e0y + cy, ez = e0z + cz;
+        int64_t e = ex + int64_t(G.nx) * (ey + int64_t(G.ny) * ez);
+        if (!mask[e]) continue;
+        int fe = felem[e];
+        int a = (ii - 2 * ex) + 3 * (ij - 2 * ey) + 9 * (ik - 2 * ez);
+        int b = (ji - 2 * ex) + 3 * (jj - 2 * ey) + 9 * (jk - 2 * ez);
+        const double* nq = nu + int64_t(fe) * 27;
+        for (int q = 0; q < 27; ++q) {
+          const double* da = T->dphi[q][a];
+          const double* db = T->dphi[q][b];
+          double f = nq[q] * T->w[q] * sc;
+          double g = da[0] * db[0] + da[1] * db[1] + da[2] * db[2];
+          out[0] = fma(f, g, out[0]);
+          out[4] = fma(f, g, out[4]);
+          out[8] = fma(f, g, out[8]);
+          if (form == GDSW_FORM_SYMMETRIC) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+              for (int d = 0; d < 3; ++d) out[c * 3 + d] = fma(f, da[d] * db[c], out[c * 3 + d]);
+          }
+        }
+      }
+}
+
+// pressure-velocity entry: -int psi_P d_d phi_J over shared fluid elements, d = 0..2
+__device__ void divergence_entry(int64_t P, int64_t J, const Geo& G, const uint8_t* mask, const RefTables* T,
+                                 double out[3]) {
+  int pi, pj, pk, ji, jj, jk;
+  node_ijk(P, G, pi, pj, pk);
+  node_ijk(J, G, ji, jj, jk);
+  out[0] = out[1] = out[2] = 0.0;
+  int e0x, e0y, e0z;
+  int nxr = shared_range(pi, ji, G.nx, e0x), nyr = shared_range(pj, jj, G.ny, e0y), nzr = shared_range(pk, jk, G.nz, e0z);
+  const double sc = 0.25 * G.h * G.h;  // (h/2)^3 * (2/h)
+  for (int cz = 0; cz < nzr; ++cz)
+    for (int cy = 0; cy < nyr; ++cy)
+      for (int cx = 0; cx < nxr; ++cx) {
+        int ex = e0x + cx, ey = e0y + cy, ez = e0z + cz;
+        int64_t e = ex + int64_t(G.nx) * (ey + int64_t(G.ny) * ez);
+        if (!mask[e]) continue;
+        int pl = ((pi - 2 * ex) >> 1) + 2 * ((pj - 2 * ey) >> 1) + 4 * ((pk - 2 * ez) >> 1);
+        int b = (ji - 2 * ex) + 3 * (jj - 2 * ey) + 9 * (jk - 2 * ez);
+        for (int q = 0; q < 27; ++q) {
+          double f = -T->w[q] * sc * T->psi[q][pl];
+          const double* db = T->dphi[q][b];
+          out[0] = fma(f, db[0], out[0]);
+          out[1] = fma(f, db[1], out[1]);
+          out[2] = fma(f, db[2], out[2]);
+        }
+      }
+}
+
+// ------------------------------------------------------------------ a2: assembly
+__global__ void k_assemble_A(const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_col,
+                             const int32_t* __restrict__ vnode, int64_t nv, Geo G, const uint8_t* mask,
+                             const int32_t* felem, const double* nu, const RefTables* T, int form,
+                             double* __restrict__ val) {
+  int64_t I = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (I >= nv) return;
+  for (int blk = a_ptr[I] + lane; blk < a_ptr[I + 1]; blk += 32) {
+    double out[9];
+    velocity_block(vnode[I], vnode[a_col[blk]], G, mask, felem, nu, T, form, out);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) val[int64_t(blk) * 9 + c] = out[c];
+  }
+}
+
+__global__ void k_assemble_B(const int32_t* __restrict__ b_ptr, const int32_t* __restrict__ b_col,
+                             const int32_t* __restrict__ pnode, const int32_t* __restrict__ vnode, int64_t np, Geo G,
+                             const uint8_t* mask, const RefTables* T, double* __restrict__ bval) {
+  int64_t P = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (P >= np) return;
+  for (int e = b_ptr[P] + lane; e < b_ptr[P + 1]; e += 32) {
+    double out[3];
+    divergence_entry(pnode[P], vnode[b_col[e]], G, mask, T, out);
+    bval[int64_t(e) * 3 + 0] = out[0];
+    bval[int64_t(e) * 3 + 1] = out[1];
+    bval[int64_t(e) * 3 + 2] = out[2];
+  }
+}
+
+__global__ void k_copy_bt(const int32_t* __restrict__ bt2b, int64_t nbt, const double* __restrict__ bval,
+                          double* __restrict__ btval) {
+  int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (e >= nbt) return;
+  int64_t s = bt2b[e];
+  btval[e * 3 + 0] = bval[s * 3 + 0];
+  btval[e * 3 + 1] = bval[s * 3 + 1];
+  btval[e * 3 + 2] = bval[s * 3 + 2];
+}
+
+// b = -A_(free, D) g_D
+__global__ void k_lift(const int32_t* ad_ptr, const int32_t* ad_col, const int32_t* vnode, int64_t nv,
+                       const int32_t* bd_ptr, const int32_t* bd_col, const int32_t* pnode, int64_t np, Geo G,
+                       const uint8_t* mask, const int32_t* felem, const double* nu, const RefTables* T, int form,
+                       const double* g, double* b) {
+  int64_t row = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (row < nv) {
+    double acc[3] = {0, 0, 0};
+    for (int e = ad_ptr[row]; e < ad_ptr[row + 1]; ++e) {
+      int64_t J = ad_col[e];
+      double blk[9];
+      velocity_block(vnode[row], J, G, mask, felem, nu, T, form, blk);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[c] = fma(blk[c * 3 + d], g[3 * J + d], acc[c]);
+    }
+    b[3 * row + 0] = -acc[0];
+    b[3 * row + 1] = -acc[1];
+    b[3 * row + 2] = -acc[2];
+  } else if (row < nv + np) {
+    int64_t P = row - nv;
+    double acc = 0.0;
+    for (int e = bd_ptr[P]; e < bd_ptr[P + 1]; ++e) {
+      int64_t J = bd_col[e];
+      double v[3];
+      divergence_entry(pnode[P], J, G, mask, T, v);
+      acc = fma(v[0], g[3 * J], fma(v[1], g[3 * J + 1], fma(v[2], g[3 * J + 2], acc)));
+    }
+    b[3 * nv + P] = -acc;
+  }
+}
+
+// ------------------------------------------------------------------ a3: SpMV
+// Velocity rows: one warp per node row; lanes 3g+c (g < 10) own output component c and
+// walk the row's blocks g, g+10, ...  Pressure rows: one warp per row streaming the
+// contiguous 3-vectors.  FP64 throughout; y = A x or y = b - A x.
+__global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_col,
+                                              const double* __restrict__ aval, const int32_t* __restrict__ bt_ptr,
+                                              const int32_t* __restrict__ bt_col, const double* __restrict__ btval,
+                                              const int32_t* __restrict__ b_ptr, const int32_t* __restrict__ b_col,
+                                              const double* __restrict__ bval, int64_t nv, int64_t np,
+                                              const double* __restrict__ x, double* __restrict__ y,
+                                              const double* __restrict__ rhs) {
+  __shared__ double red[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row = blockIdx.x * int64_t(8) + warp;
+  const int64_t nu = 3 * nv;
+  if (row < nv) {
+    const int g = lane / 3, c = lane - 3 * g;
+    double acc = 0.0;
+    if (lane < 30) {
+      const int b0 = a_ptr[row], b1 = a_ptr[row + 1];
+      for (int blk = b0 + g; blk < b1; blk += 10) {
+        const double* v = aval + int64_t(blk) * 9 + c * 3;
+        const double* xj = x + 3 * int64_t(__ldg(a_col + blk));
+        acc = fma(__ldcs(v + 0), __ldg(xj + 0), acc);
+        acc = fma(__ldcs(v + 1), __ldg(xj + 1), acc);
+        acc = fma(__ldcs(v + 2), __ldg(xj + 2), acc);
+      }
+      const int e0 = bt_ptr[row], e1 = bt_ptr[row + 1];
+      for (int e = e0 + g; e < e1; e += 10) acc = fma(__ldcs(btval + int64_t(e) * 3 + c), __ldg(x + nu + bt_col[e]), acc);
+    }
+    red[warp][lane] = acc;
+    __syncwarp();
+    if (lane < 3) {
+      double s = 0.0;
+      for (int q = lane; q < 30; q += 3) s += red[warp][q];
+      double out = rhs ? rhs[3 * row + lane] - s : s;
+      y[3 * row + lane] = out;
+    }
+  } else if (row < nv + np) {
+    const int64_t P = row - nv;
+    const int64_t f0 = int64_t(b_ptr[P]) * 3, f1 = int64_t(b_ptr[P + 1]) * 3;
+    double acc = 0.0;
+    for (int64_t f = f0 + lane; f < f1; f += 32) {
+      int64_t e = f / 3;
+      int d = int(f - 3 * e);
+      acc = fma(__ldcs(bval + f), __ldg(x + 3 * int64_t(b_col[e]) + d), acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[nu + P] = rhs ? rhs[nu + P] - acc : acc;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static Geo geo(const gdsw_ctx* c) {
+  Geo G;
+  G.nx = c->mesh.nx; G.ny = c->mesh.ny; G.nz = c->mesh.nz;
+  G.NX = c->mesh.NX; G.NY = c->mesh.NY;
+  G.h = c->mesh.h;
+  return G;
+}
+
+void upload_tables(gdsw_ctx* c, cudaStream_t s) {
+  RefTables T;
+  host_tables(T);
+  RefTables* d = c->arena.alloc<RefTables>(1);
+  GDSW_CUDA(cudaMemcpyAsync(d, &T, sizeof(T), cudaMemcpyHostToDevice, s));
+  GDSW_CUDA(cudaStreamSynchronize(s));
+  c->d_tables = d;
+}
+
+void launch_viscosity(gdsw_ctx* c, cudaStream_t s) {
+  int64_t nfe = int64_t(c->mesh.fluid.size());
+  int64_t n = nfe * 27;
+  k_viscosity<<<int((n + 255) / 256), 256, 0, s>>>(c->d_fluid, nfe, c->d_uk, static_cast<RefTables*>(c->d_tables),
+                                                  geo(c), c->form, c->has_uk ? 1 : 0, c->nu0, c->nu_inf, c->lam,
+                                                  c->ncar, c->d_nu);
+  check_launch("k_viscosity");
+}
+
+void launch_assembly(gdsw_ctx* c, cudaStream_t s) {
+  const auto* T = static_cast<RefTables*>(c->d_tables);
+  int64_t nv = c->mesh.nv, np = c->mesh.np;
+  double* aval = c->d_val;
+  double* btval = c->d_val + 9 * c->nnzb;
+  double* bval = btval + 3 * c->nbt;
+  k_assemble_A<<<int((nv + 7) / 8), 256, 0, s>>>(c->d_a_ptr, c->d_a_col, c->d_vnode, nv, geo(c), c->d_mask,
+                                                 c->d_felem, c->d_nu, T, c->form, aval);
+  check_launch("k_assemble_A");
+  k_assemble_B<<<int((np + 7) / 8), 256, 0, s>>>(c->d_b_ptr, c->d_b_col, c->d_pnode, c->d_vnode, np, geo(c),
+                                                 c->d_mask, T, bval);
+  check_launch("k_assemble_B");
+  if (c->nbt > 0) {
+    k_copy_bt<<<int((c->nbt + 255) / 256), 256, 0, s>>>(c->d_bt2b, c->nbt, bval, btval);
+    check_launch("k_copy_bt");
+  }
+}
+
+void launch_lift(gdsw_ctx* c, double* b, cudaStream_t s) {
+  int64_t nv = c->mesh.nv, np = c->mesh.np;
+  int64_t n = nv + np;
+  k_lift<<<int((n + 127) / 128), 128, 0, s>>>(c->d_ad_ptr, c->d_ad_col, c->d_vnode, nv, c->d_bd_ptr, c->d_bd_col,
+                                              c->d_pnode, np, geo(c), c->d_mask, c->d_felem, c->d_nu,
+                                              static_cast<RefTables*>(c->d_tables), c->form, c->d_gdir, b);
+  check_launch("k_lift");
+}
+
+void launch_spmv(gdsw_ctx* c, const double* x, double* y, const double* rhs, cudaStream_t s) {
+  int64_t nv = c->mesh.nv, np = c->mesh.np;
+  const double* aval = c->d_val;
+  const double* btval = c->d_val + 9 * c->nnzb;
+  const double* bval = btval + 3 * c->nbt;
+  int64_t rows = nv + np;
+  k_spmv<<<int((rows + 7) / 8), 256, 0, s>>>(c->d_a_ptr, c->d_a_col, aval, c->d_bt_ptr, c->d_bt_col, btval, c->d_b_ptr,
+                                             c->d_b_col, bval, nv, np, x, y, rhs);
+  check_launch("k_spmv");
+}
+
+}  // namespace gdsw

@@ -1,0 +1,140 @@
+// Overlapping Schwarz data movement and the GDSW coarse transfer, on every level
+// (arXiv 2606.01433, Section 2.1: R_i r, sum_i R_i^T (.) and Phi^T r / Phi x; Section 2.2:
+// the same on the coarse decompositions).  Every reduction has a fixed order, so results
+// are bitwise reproducible run to run.
+#include "common.h"
+#include "kernels.h"
+
+namespace gdsw {
+
+// r_i = R_i r for all parts at once: one thread per local position, cast to the local
+// precision on the fly.
+template <typename TV>
+__global__ void k_gather(const double* __restrict__ r, const int32_t* __restrict__ idx, TV* __restrict__ out,
+                         int64_t n) {
+  int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (p < n) out[p] = TV(__ldg(r + __ldg(idx + p)));
+}
+
+template <typename TV>
+void launch_gather(const double* r, const int32_t* idx, TV* out, int64_t n, cudaStream_t s) {
+  if (n == 0) return;
+  k_gather<TV><<<int((n + 255) / 256), 256, 0, s>>>(r, idx, out, n);
+  check_launch("k_gather");
+}
+template void launch_gather<double>(const double*, const int32_t*, double*, int64_t, cudaStream_t);
+template void launch_gather<float>(const double*, const int32_t*, float*, int64_t, cudaStream_t);
+
+// z[g] = sum over the overlapping copies of dof g of w * x_i[local] (partition-of-unity
+// weights, or 1 for the plain sum), accumulated in FP64 in list order.
+template <typename TV>
+__global__ void k_scatter(const TV* __restrict__ x, const int32_t* __restrict__ ptr, const int32_t* __restrict__ pos,
+                          const double* __restrict__ w, double* __restrict__ z, int n, int accumulate) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  double acc = 0.0;
+  for (int e = ptr[g]; e < ptr[g + 1]; ++e) acc = fma(w[e], double(x[pos[e]]), acc);
+  z[g] = accumulate ? z[g] + acc : acc;
+}
+
+template <typename TV>
+void launch_scatter(const TV* x, const int32_t* ptr, const int32_t* pos, const double* w, double* z, int n,
+                    int accumulate, cudaStream_t s) {
+  if (n == 0) return;
+  k_scatter<TV><<<(n + 255) / 256, 256, 0, s>>>(x, ptr, pos, w, z, n, accumulate);
+  check_launch("k_scatter");
+}
+template void launch_scatter<double>(const double*, const int32_t*, const int32_t*, const double*, double*, int, int,
+                                     cudaStream_t);
+template void launch_scatter<float>(const float*, const int32_t*, const int32_t*, const double*, double*, int, int,
+                                    cudaStream_t);
+
+// r0[k] = sum over parts of (Phi_I,J^T r_I,J)[k] + sum of r over the interface dofs of
+// column k (Phi_Gamma is the entity indicator).  One warp per coarse dof; lane-strided
+// partial sums and a fixed butterfly make the order deterministic.
+template <typename TP>
+__global__ void k_restrict_reduce(const TP* __restrict__ yc, const double* __restrict__ r,
+                                  const int32_t* __restrict__ rr_ptr, const int32_t* __restrict__ rr_pos,
+                                  const int32_t* __restrict__ rg_ptr, const int32_t* __restrict__ rg_dof,
+                                  double* __restrict__ r0, int n0) {
+  int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (k >= n0) return;
+  double acc = 0.0;
+  for (int e = rr_ptr[k] + lane; e < rr_ptr[k + 1]; e += 32) acc += double(yc[rr_pos[e]]);
+  for (int e = rg_ptr[k] + lane; e < rg_ptr[k + 1]; e += 32) acc += r[rg_dof[e]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) r0[k] = acc;
+}
+
+void launch_restrict_reduce(const void* yc, int prec, const double* r, const int32_t* rr_ptr, const int32_t* rr_pos,
+                            const int32_t* rg_ptr, const int32_t* rg_dof, double* r0, int n0, cudaStream_t s) {
+  if (n0 == 0) return;
+  int blocks = (n0 + 7) / 8;
+  if (prec == GDSW_FP64)
+    k_restrict_reduce<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(yc), r, rr_ptr, rr_pos, rg_ptr, rg_dof,
+                                                     r0, n0);
+  else
+    k_restrict_reduce<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(yc), r, rr_ptr, rr_pos, rg_ptr, rg_dof,
+                                                    r0, n0);
+  check_launch("k_restrict_reduce");
+}
+
+// z[I_J[l]] += sum_j PhiT_J[j][l] x0[cols_J[j]]: one thread per interior dof, coalesced
+// along the rows of the stored transpose; every interior dof belongs to exactly one part.
+template <typename TP>
+__global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, const ProMeta* __restrict__ meta,
+                                                 const int32_t* __restrict__ tile_part,
+                                                 const int32_t* __restrict__ tile_col0,
+                                                 const int32_t* __restrict__ idofs, const int32_t* __restrict__ cols,
+                                                 const double* __restrict__ x0, double* __restrict__ z) {
+  extern __shared__ double xs[];
+  const int J = tile_part[blockIdx.x];
+  const ProMeta m = meta[J];
+  for (int j = threadIdx.x; j < m.c; j += blockDim.x) xs[j] = x0[cols[m.coff + j]];
+  __syncthreads();
+  const int l = tile_col0[blockIdx.x] + threadIdx.x;
+  if (l >= m.nI) return;
+  double acc = 0.0;
+  const TP* p = phiT + m.phi + l;
+  for (int j = 0; j < m.c; ++j) acc = fma(double(__ldcs(p + int64_t(j) * m.ld)), xs[j], acc);
+  int64_t g = idofs[m.ioff + l];
+  z[g] += acc;
+}
+
+__global__ void k_axpy_gamma(const int32_t* __restrict__ gdofs, const int32_t* __restrict__ gcol, int64_t ng,
+                             const double* __restrict__ x0, double* __restrict__ z) {
+  int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q < ng) z[gdofs[q]] += x0[gcol[q]];
+}
+
+void launch_prolong(const LevelDev& L, const double* x0, double* z, cudaStream_t s) {
+  if (L.n0 == 0) return;
+  if (L.n_pro_tiles > 0) {
+    size_t smem = size_t(L.max_c) * sizeof(double);
+    const ProMeta* meta = reinterpret_cast<const ProMeta*>(L.pro_meta);
+    if (L.phi_prec == GDSW_FP64)
+      k_prolong<double><<<L.n_pro_tiles, 256, smem, s>>>(static_cast<const double*>(L.phiT), meta, L.pro_tile_part,
+                                                         L.pro_tile_col0, L.idofs, L.cols, x0, z);
+    else
+      k_prolong<float><<<L.n_pro_tiles, 256, smem, s>>>(static_cast<const float*>(L.phiT), meta, L.pro_tile_part,
+                                                        L.pro_tile_col0, L.idofs, L.cols, x0, z);
+    check_launch("k_prolong");
+  }
+  launch_axpy_gamma(L.gdofs, L.gcol, L.ngamma, x0, z, s);
+}
+
+void launch_axpy_gamma(const int32_t* gdofs, const int32_t* gcol, int64_t ng, const double* x0, double* z,
+                       cudaStream_t s) {
+  if (ng == 0) return;
+  k_axpy_gamma<<<int((ng + 255) / 256), 256, 0, s>>>(gdofs, gcol, ng, x0, z);
+  check_launch("k_axpy_gamma");
+}
+
+void set_prolong_smem_limits() {
+  cudaFuncSetAttribute(k_prolong<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_prolong<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+}  // namespace gdsw

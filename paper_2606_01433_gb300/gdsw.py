@@ -1,0 +1,297 @@
+"""Thin ctypes binding of libgdsw.so (C ABI declared in include/gdsw.h).
+
+Argument marshalling only: every numeric step runs inside the CUDA library.  Device
+vectors are passed as torch CUDA tensors (float64, contiguous); their data pointers go
+straight to the library, which works on the current torch stream.  If the library has not
+been built, load() raises -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgdsw.so")
+
+GDSW_OK, GDSW_ERR_INVALID_ARG, GDSW_ERR_OOM, GDSW_ERR_SINGULAR = 0, 1, 2, 3
+GDSW_ERR_NOT_CONVERGED, GDSW_ERR_NAN, GDSW_ERR_TIMEOUT, GDSW_ERR_CUDA = 4, 5, 6, 7
+FP64, FP32, BF16 = 0, 1, 2
+WEIGHT_POU, WEIGHT_PLAIN = 0, 1
+FORM = {"gradient": 0, "symmetric": 1}
+PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
+KERNEL_GROUPS = ["spmv", "gather", "local", "scatter", "restrict", "coarse", "prolong", "arnoldi",
+                 "apply", "assembly", "viscosity", "other"]
+
+
+class GdswError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gdsw error %d: %s" % (code, msg))
+        self.code = code
+
+
+class gdsw_mesh(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double),
+                ("origin", C.c_double * 3), ("mask", C.c_void_p), ("tags", C.c_void_p), ("g", C.c_void_p)]
+
+
+class gdsw_viscosity(C.Structure):
+    _fields_ = [("form", C.c_int32), ("nu0", C.c_double), ("nu_inf", C.c_double), ("lambda_", C.c_double),
+                ("n", C.c_double), ("uk", C.c_void_p)]
+
+
+class gdsw_partition(C.Structure):
+    _fields_ = [("elem_part", C.c_void_p), ("n_groups", C.c_int32), ("groups", C.c_void_p * 2),
+                ("group_len", C.c_int32 * 2)]
+
+
+class gdsw_levels(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("overlap", C.c_int32)]
+
+
+class gdsw_options(C.Structure):
+    _fields_ = [("weighting", C.c_int32), ("precision", C.c_int32 * 3), ("phi_precision", C.c_int32),
+                ("restart", C.c_int32), ("max_it", C.c_int32), ("tol", C.c_double), ("slab_elems", C.c_int32),
+                ("use_graph", C.c_int32), ("stream", C.c_void_p)]
+
+
+class gdsw_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("relres", C.c_double),
+                ("est_relres", C.c_double), ("time_ms", C.c_double), ("apply_ms", C.c_double),
+                ("spmv_ms", C.c_double), ("arnoldi_ms", C.c_double)]
+
+
+class gdsw_sizes_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_u", C.c_int64), ("n_p", C.c_int64), ("n_elems", C.c_int64),
+                ("n_nodes", C.c_int64), ("levels", C.c_int32), ("n_coarse", C.c_int64 * 4),
+                ("n_parts", C.c_int32 * 3), ("local_dofs", C.c_int64 * 3), ("factor_entries", C.c_int64 * 3),
+                ("max_local", C.c_int64 * 3), ("max_slabs", C.c_int32), ("nnzb_A", C.c_int64),
+                ("nnz_B", C.c_int64), ("phi_entries", C.c_int64), ("device_bytes", C.c_int64),
+                ("setup_ms", C.c_double * 6)]
+
+
+class gdsw_profile(C.Structure):
+    _fields_ = [("enabled", C.c_int32), ("calls", C.c_int64 * 12), ("ms", C.c_double * 12),
+                ("bytes", C.c_double * 12)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgdsw.so; raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libgdsw.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = C.CDLL(path)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.c_void_p
+    sig = {
+        "gdsw_setup": ([C.POINTER(gdsw_mesh), C.POINTER(gdsw_viscosity), C.POINTER(gdsw_partition),
+                        C.POINTER(gdsw_levels), C.POINTER(gdsw_options), C.POINTER(vp)], C.c_int),
+        "gdsw_analyze": ([C.POINTER(gdsw_mesh), C.POINTER(gdsw_viscosity), C.POINTER(gdsw_partition),
+                          C.POINTER(gdsw_levels), C.POINTER(gdsw_options), C.POINTER(vp)], C.c_int),
+        "gdsw_destroy": ([vp], None),
+        "gdsw_last_error": ([vp], C.c_char_p),
+        "gdsw_sizes": ([vp, C.POINTER(gdsw_sizes_info)], C.c_int),
+        "gdsw_rhs_lift": ([vp, dp], C.c_int),
+        "gdsw_spmv": ([vp, dp, dp], C.c_int),
+        "gdsw_apply": ([vp, dp, dp], C.c_int),
+        "gdsw_solve": ([vp, dp, dp, C.POINTER(gdsw_solve_info)], C.c_int),
+        "gdsw_solve_host": ([vp, dp, dp, C.POINTER(gdsw_solve_info)], C.c_int),
+        "gdsw_reassemble": ([vp, dp], C.c_int),
+        "gdsw_apply_local": ([vp, i32, dp, dp], C.c_int),
+        "gdsw_restrict": ([vp, i32, dp, dp], C.c_int),
+        "gdsw_prolong": ([vp, i32, dp, dp], C.c_int),
+        "gdsw_coarse_matrix": ([vp, i32, dp], C.c_int),
+        "gdsw_matrix_csr": ([vp, dp, dp, dp, C.POINTER(i64)], C.c_int),
+        "gdsw_viscosity_values": ([vp, dp], C.c_int),
+        "gdsw_level_dofs": ([vp, i32, dp, dp], C.c_int),
+        "gdsw_level_entities": ([vp, i32, C.POINTER(i32)], C.c_int),
+        "gdsw_profile_enable": ([vp, i32], C.c_int),
+        "gdsw_profile_read": ([vp, C.POINTER(gdsw_profile)], C.c_int),
+        "gdsw_profile_reset": ([vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    """Function names declared in include/gdsw.h (for the export check)."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(HERE), "include", "gdsw.h")).read()
+    return sorted(set(re.findall(r"\b(gdsw_[a-z_]+)\s*\(", hdr)))
+
+
+def _ptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Context:
+    """One preconditioner/solver context (gdsw_ctx*)."""
+
+    def __init__(self, prob, levels=None, weighting="pou", precision=("fp64", "fp64", "fp64"),
+                 phi_precision="fp64", restart=100, max_it=1000, tol=1e-8, slab_elems=1, use_graph=False,
+                 overlap=1, stream=None, analyze_only=False):
+        lib = load()
+        self.lib = lib
+        self.prob = prob
+        L = prob.levels if levels is None else levels
+        self._keep = []
+        mask = _np(prob.mask, np.uint8)
+        tags = _np(prob.tags, np.uint8)
+        g = _np(prob.g, np.float64)
+        part = _np(prob.part, np.int32)
+        self._keep += [mask, tags, g, part]
+        m = gdsw_mesh(prob.nx, prob.ny, prob.nz, prob.h, (C.c_double * 3)(*prob.origin),
+                      mask.ctypes.data, tags.ctypes.data, g.ctypes.data)
+        uk = None
+        if prob.uk is not None:
+            uk = _np(prob.uk, np.float64)
+            self._keep.append(uk)
+        v = gdsw_viscosity(FORM[prob.form], prob.nu0, prob.nu_inf, prob.lam, prob.n_carreau,
+                           uk.ctypes.data if uk is not None else None)
+        pa = gdsw_partition()
+        pa.elem_part = part.ctypes.data
+        pa.n_groups = L - 2
+        for l in range(L - 2):
+            gr = _np(prob.groups[l], np.int32)
+            self._keep.append(gr)
+            pa.groups[l] = gr.ctypes.data
+            pa.group_len[l] = gr.size
+        lv = gdsw_levels(L, overlap)
+        if stream is None and not analyze_only:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+            except Exception:
+                stream = None
+        prec = [PREC[p] if isinstance(p, str) else int(p) for p in precision]
+        prec = (prec + [prec[-1]] * 3)[:3]
+        o = gdsw_options(WEIGHT_POU if weighting == "pou" else WEIGHT_PLAIN, (C.c_int32 * 3)(*prec),
+                         PREC[phi_precision], restart, max_it, tol, slab_elems, 1 if use_graph else 0, stream)
+        self.stream = stream
+        h = C.c_void_p()
+        entry = lib.gdsw_analyze if analyze_only else lib.gdsw_setup
+        rc = entry(C.byref(m), C.byref(v), C.byref(pa), C.byref(lv), C.byref(o), C.byref(h))
+        if rc != GDSW_OK:
+            raise GdswError(rc, lib.gdsw_last_error(None).decode())
+        self.h = h
+        self._keep = None
+        si = gdsw_sizes_info()
+        lib.gdsw_sizes(h, C.byref(si))
+        self.sizes = si
+        self.n = si.n
+
+    def _check(self, rc):
+        if rc not in (GDSW_OK, GDSW_ERR_NOT_CONVERGED):
+            raise GdswError(rc, self.lib.gdsw_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gdsw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- the C ABI, one method per entry point
+    def gdsw_spmv(self, x, y):
+        return self._check(self.lib.gdsw_spmv(self.h, _ptr(x), _ptr(y)))
+
+    def gdsw_apply(self, r, z):
+        return self._check(self.lib.gdsw_apply(self.h, _ptr(r), _ptr(z)))
+
+    def gdsw_rhs_lift(self, b):
+        return self._check(self.lib.gdsw_rhs_lift(self.h, _ptr(b)))
+
+    def gdsw_solve(self, b, x):
+        info = gdsw_solve_info()
+        rc = self._check(self.lib.gdsw_solve(self.h, _ptr(b), _ptr(x), C.byref(info)))
+        return info
+
+    def gdsw_solve_host(self, b, x):
+        """b, x: numpy float64 arrays (x holds the initial guess and receives the result)."""
+        assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
+        info = gdsw_solve_info()
+        self._check(self.lib.gdsw_solve_host(self.h, b.ctypes.data, x.ctypes.data, C.byref(info)))
+        return info
+
+    def gdsw_reassemble(self, uk=None):
+        if uk is None:
+            return self._check(self.lib.gdsw_reassemble(self.h, None))
+        u = _np(uk, np.float64)
+        return self._check(self.lib.gdsw_reassemble(self.h, u.ctypes.data))
+
+    def gdsw_apply_local(self, level, r, z):
+        return self._check(self.lib.gdsw_apply_local(self.h, level, _ptr(r), _ptr(z)))
+
+    def gdsw_restrict(self, level, r, r0):
+        return self._check(self.lib.gdsw_restrict(self.h, level, _ptr(r), _ptr(r0)))
+
+    def gdsw_prolong(self, level, x0, z):
+        return self._check(self.lib.gdsw_prolong(self.h, level, _ptr(x0), _ptr(z)))
+
+    def gdsw_coarse_matrix(self, l):
+        """A_0^(l+2) as a dense host array (l = 0 .. L-2)."""
+        n = int(self.sizes.n_coarse[l])
+        out = np.zeros((n, n))
+        self._check(self.lib.gdsw_coarse_matrix(self.h, l, out.ctypes.data))
+        return out
+
+    def gdsw_matrix_csr(self):
+        import scipy.sparse as sp
+        nnz = C.c_int64()
+        self._check(self.lib.gdsw_matrix_csr(self.h, None, None, None, C.byref(nnz)))
+        rp = np.zeros(self.n + 1, np.int64)
+        col = np.zeros(nnz.value, np.int32)
+        val = np.zeros(nnz.value)
+        self._check(self.lib.gdsw_matrix_csr(self.h, rp.ctypes.data, col.ctypes.data, val.ctypes.data, C.byref(nnz)))
+        return sp.csr_matrix((val, col, rp), shape=(self.n, self.n))
+
+    def gdsw_viscosity_values(self):
+        out = np.zeros((int(self.sizes.n_elems), 27))
+        self._check(self.lib.gdsw_viscosity_values(self.h, out.ctypes.data))
+        return out
+
+    def gdsw_level_dofs(self, level):
+        N = self.sizes.n_parts[level]
+        off = np.zeros(N + 1, np.int64)
+        self._check(self.lib.gdsw_level_dofs(self.h, level, off.ctypes.data, None))
+        d = np.zeros(int(off[-1]), np.int32)
+        self._check(self.lib.gdsw_level_dofs(self.h, level, off.ctypes.data, d.ctypes.data))
+        return [d[off[i]:off[i + 1]] for i in range(N)]
+
+    def gdsw_level_entities(self, level):
+        n = C.c_int32()
+        self._check(self.lib.gdsw_level_entities(self.h, level, C.byref(n)))
+        return n.value
+
+    def gdsw_profile_enable(self, on=True):
+        return self._check(self.lib.gdsw_profile_enable(self.h, 1 if on else 0))
+
+    def gdsw_profile_reset(self):
+        return self._check(self.lib.gdsw_profile_reset(self.h))
+
+    def gdsw_profile_read(self):
+        p = gdsw_profile()
+        self._check(self.lib.gdsw_profile_read(self.h, C.byref(p)))
+        return {KERNEL_GROUPS[i]: dict(calls=p.calls[i], ms=p.ms[i], bytes=p.bytes[i]) for i in range(12)}
