@@ -845,17 +845,22 @@ static void capture_graph(gdsw_ctx* c) {
   c->d_graph_z = c->arena.alloc<double>(c->mesh.n);
   GDSW_CUDA(cudaMemsetAsync(c->d_graph_r, 0, 8 * c->mesh.n, c->stream));
   GDSW_CUDA(cudaStreamSynchronize(c->stream));
+  // capture on a private stream (the caller's stream may be the legacy default stream)
+  cudaStream_t cs;
+  GDSW_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g;
-  GDSW_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  GDSW_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   try {
-    apply_level(c, 0, c->d_graph_r, c->d_graph_z, c->stream);
+    apply_level(c, 0, c->d_graph_r, c->d_graph_z, cs);
   } catch (...) {
-    cudaStreamEndCapture(c->stream, &g);
+    cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
     throw;
   }
-  GDSW_CUDA(cudaStreamEndCapture(c->stream, &g));
+  GDSW_CUDA(cudaStreamEndCapture(cs, &g));
   GDSW_CUDA(cudaGraphInstantiate(&c->apply_graph, g, 0));
   GDSW_CUDA(cudaGraphDestroy(g));
+  GDSW_CUDA(cudaStreamDestroy(cs));
 }
 
 // ------------------------------------------------------------------ set-up driver
@@ -903,12 +908,8 @@ static void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity*
     c->est_device_bytes = int64_t(b);
     return;
   }
-  if (opt->stream) {
-    c->stream = static_cast<cudaStream_t>(opt->stream);
-  } else {
-    GDSW_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-    c->own_stream = true;
-  }
+  // NULL selects the legacy default stream, so calls order with other default-stream work
+  c->stream = static_cast<cudaStream_t>(opt->stream);
   GDSW_CUDA(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
   GDSW_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   GDSW_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));

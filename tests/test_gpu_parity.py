@@ -1,0 +1,237 @@
+"""GPU parity: every hot-path step of libgdsw.so, called through its C ABI, against the
+FP64 CPU oracle on the same seeded inputs.
+
+Tolerances (relative 2-norm unless stated):
+  * FP64 path, single steps (assembly, viscosity, SpMV, lifting, gather/local solve/
+    scatter, restriction, prolongation, Galerkin operators): <= 1e-12 -- both sides
+    compute the same sums in a different order, so only rounding differs; the local solves
+    go through explicit inverses of Schur complements whose conditioning costs a few
+    digits, which 1e-12 covers on these sizes;
+  * FP64 preconditioner apply: <= 1e-11; FP64 FGMRES solution at the same tolerance:
+    <= 1e-10 and iteration counts within +-1 (the spec bar);
+  * mixed paths (FP32 / BF16 local factors, FP32 coarse basis): solved to a tolerance tight
+    enough that the forward error against the FP64 oracle solution is <= 1e-8.
+Sizes span several 32-row GEMV tiles with ragged tails, 2-4 levels, obstacles (irregular
+subdomains), RCB partitions, one-subdomain and collapsed-level degenerate cases.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_01433_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64 = (("fp64", "fp64", "fp64"), "fp64")
+FP32 = (("fp32", "fp32", "fp32"), "fp32")
+BF16 = (("bf16", "fp32", "fp32"), "fp32")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_01433_gb300 import gdsw
+    gdsw.load()
+    return gdsw
+
+
+PROBLEMS = {
+    "box_2lvl_carreau": lambda: I.box_problem(4, 4, 4, (2, 2, 2), levels=2, form="symmetric", uk_seed=3, lam=1.0,
+                                              n=0.5, nu_inf=1e-3),
+    "cube8_newtonian": lambda: I.unit_cube(8),
+    "box_3lvl": lambda: I.box_problem(4, 4, 4, (2, 2, 2), groups=((2, 2, 1),), levels=3, form="symmetric", uk_seed=3,
+                                      lam=1.0, n=0.5, nu_inf=1e-3),
+    "box_4lvl": lambda: I.box_problem(4, 4, 2, (4, 4, 2), groups=((2, 2, 1), (2, 1, 1)), levels=4),
+    "channel16_obstacles": lambda: I.channel(16, parts=(4, 4, 4), groups=((2, 2, 2),), levels=3),
+    "die_rcb_4lvl": lambda: I.die(16, 16, 32, nparts=32, per_group=4, levels=4),
+}
+
+_cache = {}
+
+
+def oracle_for(name, weighting="pou"):
+    from oracle import fem, gdsw as og
+    key = (name, weighting)
+    if key not in _cache:
+        p = PROBLEMS[name]()
+        S = fem.assemble(p)
+        P = og.GDSW(S, p, weighting=weighting)
+        _cache[key] = (p, S, P)
+    return _cache[key]
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_operator_steps_fp64(lib, name):
+    """Section 3 Carreau viscosity, Section 2 assembly, SpMV and Dirichlet lifting."""
+    from oracle import fem
+    p, S, P = oracle_for(name)
+    ctx = lib.Context(p)
+    assert rel(ctx.gdsw_viscosity_values(), S["nu_q"]) <= 1e-14
+    Ag = ctx.gdsw_matrix_csr()
+    assert abs(Ag - S["A"]).max() <= 1e-14 * abs(S["A"]).max()
+    x = np.random.default_rng(0).standard_normal(ctx.n)
+    y = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.gdsw_spmv(dev(x), y)
+    assert rel(host(y), S["A"] @ x) <= 1e-14
+    b = torch.zeros_like(y)
+    ctx.gdsw_rhs_lift(b)
+    bo = fem.lifted_rhs(S)
+    if np.linalg.norm(bo) > 0:
+        assert rel(host(b), bo) <= 1e-13
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("weighting", ["pou", "plain"])
+def test_level_steps_fp64(lib, name, weighting):
+    """Section 2.1 / 2.2 per level: local branch sum R_i^T D_i A_i^{-1} R_i r (gather,
+    batched block-LDU solves, weighted scatter), Phi^T r, Phi x and the Galerkin A_0."""
+    p, S, P = oracle_for(name, weighting)
+    ctx = lib.Context(p, weighting=weighting)
+    rng = np.random.default_rng(1)
+    for l, lev in enumerate(P.levels):
+        r = rng.standard_normal(lev.n)
+        z = torch.zeros(lev.n, dtype=torch.float64, device="cuda")
+        ctx.gdsw_apply_local(l, dev(r), z)
+        assert rel(host(z), lev.apply_local(r, weighting)) <= 1e-12, (l, "local")
+        if lev.n0:
+            r0 = torch.zeros(lev.n0, dtype=torch.float64, device="cuda")
+            ctx.gdsw_restrict(l, dev(r), r0)
+            assert rel(host(r0), lev.Phi.T @ r) <= 1e-12, (l, "restrict")
+            x0 = rng.standard_normal(lev.n0)
+            z2 = torch.zeros(lev.n, dtype=torch.float64, device="cuda")
+            ctx.gdsw_prolong(l, dev(x0), z2)
+            assert rel(host(z2), lev.Phi @ x0) <= 1e-12, (l, "prolong")
+            assert rel(ctx.gdsw_coarse_matrix(l), P.A0[l + 1]) <= 1e-12, (l, "A0")
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_apply_and_solve_fp64(lib, name):
+    """Section 2.2 four-level equation (and 2/3-level forms) as one apply, and Section 3
+    FGMRES: solution within 1e-10 of the oracle's, iterations within +-1; applies are
+    bitwise reproducible."""
+    from oracle import fem, fgmres
+    p, S, P = oracle_for(name)
+    ctx = lib.Context(p, tol=1e-10)
+    r = np.random.default_rng(2).standard_normal(ctx.n)
+    z = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.gdsw_apply(dev(r), z)
+    za = host(z)
+    assert rel(za, P.apply(r)) <= 1e-11
+    ctx.gdsw_apply(dev(r), z)
+    assert np.array_equal(za, host(z))
+    b = fem.lifted_rhs(S) if p.rhs_seed is None else I.random_rhs(ctx.n, p.rhs_seed)
+    xo, io = fgmres.fgmres(lambda v: S["A"] @ v, b, P.apply, tol=1e-10)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.gdsw_solve(dev(b), x)
+    assert info.status == 0
+    assert abs(info.iterations - io["iterations"]) <= 1
+    assert rel(host(x), xo) <= 1e-10
+    assert info.relres <= 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["channel16_obstacles", "die_rcb_4lvl", "box_4lvl"])
+@pytest.mark.parametrize("prec", [FP32, BF16], ids=["fp32", "bf16"])
+def test_mixed_precision_solve(lib, name, prec):
+    """North-star precision pattern: FP32 / BF16 local factors (FP32 accumulation), FP32
+    coarse basis, recovered by the FP64 outer FGMRES: forward error <= 1e-8 against the
+    FP64 oracle solution."""
+    from oracle import fem, fgmres
+    p, S, P = oracle_for(name)
+    b = fem.lifted_rhs(S) if p.rhs_seed is None else I.random_rhs(S["A"].shape[0], p.rhs_seed)
+    xo, io = fgmres.fgmres(lambda v: S["A"] @ v, b, P.apply, tol=1e-13)
+    ctx = lib.Context(p, precision=prec[0], phi_precision=prec[1], tol=1e-12)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.gdsw_solve(dev(b), x)
+    assert info.status == 0
+    assert rel(host(x), xo) <= 1e-8
+    ctx.close()
+
+
+def test_poiseuille_exact_on_gpu(lib):
+    """Section 2 closed form: the GPU solve reproduces the analytic Poiseuille flow."""
+    from oracle import fem
+    p = I.poiseuille(4, parts=(2, 2, 2))
+    S = fem.assemble(p)
+    ctx = lib.Context(p, tol=1e-13)
+    b = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.gdsw_rhs_lift(b)
+    x = torch.zeros_like(b)
+    info = ctx.gdsw_solve(b, x)
+    assert info.status == 0
+    u, pr = fem.full_solution(S, host(x))
+    ue, pe = I.poiseuille_exact(p)
+    m = S["mesh"]
+    assert np.abs(u[m.active] - ue[m.active]).max() < 1e-11
+    assert np.abs(pr[m.pnodes] - pe[m.pnodes]).max() < 1e-10
+    ctx.close()
+
+
+def test_one_subdomain_and_dense_blocks(lib):
+    """Degenerate cases: one subdomain (no coarse space, B = A^{-1}, one FGMRES step);
+    one dense block per subdomain (slab thickness 0) equals the slab factorisation."""
+    import scipy.sparse.linalg as spla
+    from oracle import fem
+    p = I.box_problem(3, 3, 3, (1, 1, 1), form="symmetric", uk_seed=7, lam=1.0, n=0.5, nu_inf=1e-3)
+    S = fem.assemble(p)
+    ctx = lib.Context(p, tol=1e-10)
+    assert ctx.sizes.n_coarse[0] == 0
+    r = np.random.default_rng(3).standard_normal(ctx.n)
+    z = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.gdsw_apply(dev(r), z)
+    assert rel(host(z), spla.spsolve(S["A"].tocsc(), r)) <= 1e-12
+    x = torch.zeros_like(z)
+    info = ctx.gdsw_solve(dev(r), x)
+    assert info.iterations == 1
+    ctx.close()
+    q = PROBLEMS["cube8_newtonian"]()
+    c1 = lib.Context(q, slab_elems=1)
+    c0 = lib.Context(q, slab_elems=0)
+    r = np.random.default_rng(4).standard_normal(c1.n)
+    z1 = torch.zeros(c1.n, dtype=torch.float64, device="cuda")
+    z0 = torch.zeros_like(z1)
+    c1.gdsw_apply(dev(r), z1)
+    c0.gdsw_apply(dev(r), z0)
+    assert rel(host(z1), host(z0)) <= 1e-12
+    c1.close()
+    c0.close()
+
+
+def test_host_buffers_and_graph(lib):
+    """The host-buffer solve (copies inside the call) and the CUDA-graph apply give the
+    same result as the device-pointer path."""
+    p, S, P = oracle_for("channel16_obstacles")
+    b = I.random_rhs(S["A"].shape[0], 11)
+    ctx = lib.Context(p, tol=1e-10)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    i1 = ctx.gdsw_solve(dev(b), x)
+    xh = np.zeros(ctx.n)
+    i2 = ctx.gdsw_solve_host(b.copy(), xh)
+    assert i1.iterations == i2.iterations and np.array_equal(host(x), xh)
+    g = lib.Context(p, tol=1e-10, use_graph=True)
+    r = np.random.default_rng(5).standard_normal(ctx.n)
+    z1 = torch.zeros_like(x)
+    z2 = torch.zeros_like(x)
+    ctx.gdsw_apply(dev(r), z1)
+    g.gdsw_apply(dev(r), z2)
+    assert np.array_equal(host(z1), host(z2))
+    ctx.close()
+    g.close()
