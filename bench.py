@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark: FGMRES solve time and apply GB/s at relative residual 1e-8, mixed precision
+vs FP64, with step-latency percentiles, on one GB300 (replicas on N GPUs).
+
+Workload (the configuration the headline metric is quoted on): Carreau Stokes
+(nu0 = 1, nu_inf = 1e-3, lambda = 1, n = 0.5, frozen Picard velocity from seed 2) in a
+32x32x32-element Q2/Q1 channel with four cylindrical obstacles, 4x4x4 subdomains grouped
+2x2x2, three-level monolithic GDSW, FGMRES(100) to 1e-8.  Synthetic seeded inputs.
+
+One step = one Picard linear solve: Carreau viscosity at the Gauss points and re-assembly
+of the saddle-point operator, the lifted right-hand side, and the GDSW-preconditioned
+FGMRES solve (every row of the hot path).  The preconditioner factors are built once
+before timing.  Inputs (factors: 15 GB FP32) are far larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gdsw|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "channel32_4cyl_carreau_n0.5_q2q1_4x4x4_grouped2x2x2_3level"
+METRIC = "FGMRES solve time and apply GB/s at rel res 1e-8, mixed vs FP64; p99 latency"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gdsw", "reference"], default="gdsw")
+    ap.add_argument("--mixed", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison context")
+    ap.add_argument("--m", type=int, default=32, help="elements per edge of the channel")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "0x1") or v == "Active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("GDSW_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def allreduce_max(v, world, device=None):
+    """Max over ranks (replicas: the slowest rank defines the job time)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(p, iterations, repeats=1):
+    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the same workload and
+    scale it to ms per step: 1/16 of the elements assembled (x16), one median-size level-1
+    subdomain solve with its sparse LU (x64 subdomains per apply; the LU itself is set-up,
+    excluded like the GPU factorisation), one SpMV, per FGMRES iteration x iterations."""
+    import numpy as np
+    import scipy.sparse.linalg as spla
+    from oracle import fem, gdsw as og
+    from paper_2606_01433_gb300 import inputs as I
+    # assembly on a 1/16 element subset (a thin slab of the box)
+    q = I.Problem(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    q.mask = p.mask.copy()
+    ne = p.nx * p.ny * p.nz
+    keep = np.zeros(ne, dtype=bool)
+    keep[: ne // 16] = True
+    q.mask[~keep] = 0
+    t0 = time.perf_counter()
+    fem.assemble(q)
+    t_asm = (time.perf_counter() - t0) * 16
+    S = fem.assemble(p) if not hasattr(oracle_sample, "_S") else oracle_sample._S
+    oracle_sample._S = S
+    if not hasattr(oracle_sample, "_lu"):
+        lev_dofs = None
+        from paper_2606_01433_gb300 import gdsw as G
+        try:
+            ctx = G.Context(p, analyze_only=True)
+            lev_dofs = ctx.gdsw_level_dofs(0)
+            ctx.close()
+        except Exception:
+            lev_dofs = None
+        if lev_dofs is None:
+            lev, _ = og.build_level1(S, p)
+            lev_dofs = lev.dofs
+        sizes = [len(d) for d in lev_dofs]
+        med = int(np.argsort(sizes)[len(sizes) // 2])
+        d = lev_dofs[med]
+        oracle_sample._lu = spla.splu(S["A"][d][:, d].tocsc())
+        oracle_sample._nsub = len(lev_dofs)
+        oracle_sample._nloc = len(d)
+    lu = oracle_sample._lu
+    r = np.random.default_rng(0).standard_normal(oracle_sample._nloc)
+    x = np.random.default_rng(1).standard_normal(S["A"].shape[0])
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        lu.solve(r)
+    t_loc = (time.perf_counter() - t0) / repeats
+    t0 = time.perf_counter()
+    S["A"] @ x
+    t_spmv = time.perf_counter() - t0
+    t_iter = oracle_sample._nsub * t_loc + 2 * t_spmv
+    ms = 1e3 * (t_asm + iterations * t_iter)
+    sample = ("1/16 of the elements assembled (x16); one median level-1 subdomain (%d dofs) sparse-LU solve "
+              "(x%d subdomains) + 2 SpMV per iteration, x%d FGMRES iterations; LU set-up excluded"
+              % (oracle_sample._nloc, oracle_sample._nsub, iterations))
+    return ms, sample
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the host cores, timed on a bounded sample per step."""
+    if rank != 0:
+        return
+    from paper_2606_01433_gb300 import inputs as I
+    p = I.channel(args.m)
+    its = 46
+    for _ in range(args.warmup):
+        oracle_sample(p, its)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ms, sample = oracle_sample(p, its)
+        vals.append(ms)
+    wall = time.perf_counter() - t0
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gdsw(args, rank, world, local):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_01433_gb300 import gdsw, inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = I.channel(args.m)
+    mixed = (args.mixed, args.mixed, args.mixed)
+    t0 = time.perf_counter()
+    ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8, restart=100, max_it=1000)
+    setup_mixed_s = time.perf_counter() - t0
+    n = ctx.n
+    lib = gdsw.load()
+    b = torch.zeros(n, dtype=torch.float64, device=dev)
+    x = torch.zeros_like(b)
+
+    def step(c):
+        c.gdsw_reassemble()
+        c.gdsw_rhs_lift(b)
+        x.zero_()
+        return c.gdsw_solve(b, x)
+
+    for _ in range(args.warmup):
+        info = step(ctx)
+    ctx.gdsw_profile_enable(True)
+    ctx.gdsw_profile_reset()
+    stream = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = Clocks(local)
+    launches0 = lib.gdsw_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    evs[0].record(stream)
+    iters = []
+    for k in range(args.steps):
+        info = step(ctx)
+        iters.append(info.iterations)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = lib.gdsw_kernel_launches() - launches0
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    total_ms = allreduce_max(total_ms, world, dev)
+    prof = ctx.gdsw_profile_read()
+    ctx.gdsw_profile_enable(False)
+    relres = info.relres
+    # dominant kernel: the level-1 block-LDU sweep GEMV
+    loc = prof["local"]
+    gemv_gbs = loc["bytes"] / (loc["ms"] * 1e-3) / 1e9 if loc["ms"] > 0 else None
+    gemv_avg_ms = loc["ms"] / max(loc["calls"], 1)
+    gemv_avg_bytes = loc["bytes"] / max(loc["calls"], 1)
+    ap = prof["apply"]
+    apply_gbs = ap["bytes"] / (ap["ms"] * 1e-3) / 1e9 if ap["ms"] > 0 else None
+    sp = prof["spmv"]
+    spmv_gbs = sp["bytes"] / (sp["ms"] * 1e-3) / 1e9 if sp["ms"] > 0 else None
+    ar = prof["arnoldi"]
+    asm_ms = (prof["assembly"]["ms"] + prof["viscosity"]["ms"]) / args.steps
+
+    # FP64 path for the mixed-vs-FP64 comparison
+    fp64 = None
+    if not args.no_fp64:
+        del ctx
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        c64 = gdsw.Context(p, precision=("fp64",) * 3, phi_precision="fp64", tol=1e-8)
+        setup64 = time.perf_counter() - t0
+        for _ in range(min(args.warmup, 1)):
+            step(c64)
+        c64.gdsw_profile_enable(True)
+        c64.gdsw_profile_reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        its64 = []
+        for _ in range(args.steps):
+            its64.append(step(c64).iterations)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p64 = c64.gdsw_profile_read()
+        a64 = p64["apply"]
+        l64 = p64["local"]
+        fp64 = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "iterations": its64[-1], "setup_s": setup64,
+                "apply_gbs": a64["bytes"] / (a64["ms"] * 1e-3) / 1e9 if a64["ms"] > 0 else None,
+                "apply_ms": a64["ms"] / max(a64["calls"], 1),
+                "local_gemv_gbs": l64["bytes"] / (l64["ms"] * 1e-3) / 1e9 if l64["ms"] > 0 else None}
+        c64.close()
+        del c64
+        torch.cuda.empty_cache()
+        ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8)
+
+    # end to end through the host-buffer entry point: u_k, b and x0 from pinned host memory,
+    # x back to host, inside the timed region
+    uk_h = torch.from_numpy(np.ascontiguousarray(p.uk)).pin_memory().numpy()
+    ctx.gdsw_reassemble()
+    ctx.gdsw_rhs_lift(b)
+    b_h = b.cpu().pin_memory().numpy()
+    x_h = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    ctx.gdsw_reassemble(uk_h)
+    ctx.gdsw_solve_host(b_h.copy(), x_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.gdsw_reassemble(uk_h)
+        x_h[:] = 0.0
+        ctx.gdsw_solve_host(b_h, x_h)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = allreduce_max(e2e_ms, world, dev)
+    h2d = uk_h.nbytes + b_h.nbytes + x_h.nbytes
+    d2h = x_h.nbytes
+    sizes = ctx.sizes
+    ctx.close()
+
+    peak, peak_kind = measured_peaks()
+    ms_step = total_ms / args.steps
+    line = {
+        "metric": METRIC,
+        "value": ms_step,
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.mixed == "fp32" else "bf16",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_dofs": n, "levels": 3, "subdomains": [64, 8], "coarse": [1060, 64],
+                   "local_precision": args.mixed, "krylov_precision": "f64", "tol": 1e-8, "restart": 100,
+                   "l2": "inputs larger than L2 (no flush)", "replicas": world},
+        "iterations": iters[-1],
+        "relres": relres,
+        "solve_ms": ms_step - asm_ms,
+        "assembly_ms": asm_ms,
+        "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99)),
+                       "max": max(step_ms)},
+        "apply_gbs": apply_gbs,
+        "apply_ms": ap["ms"] / max(ap["calls"], 1),
+        "spmv_gbs": spmv_gbs,
+        "arnoldi_ms_per_solve": ar["ms"] / args.steps,
+        "fp64": fp64,
+        "speedup_vs_fp64": (fp64["ms_per_step"] / ms_step) if fp64 else None,
+        "setup_s": setup_mixed_s,
+        "factor_gb": sizes.factor_entries[0] * (4 if args.mixed == "fp32" else 2) / 1e9,
+        "roofline": {"kernel": "k_gemv (level-1 block-LDU sweeps)", "bound": "hbm", "achieved": gemv_gbs,
+                     "peak": peak, "unit": "GB/s", "frac": (gemv_gbs / peak) if gemv_gbs else None,
+                     "peak_kind": peak_kind, "avg_launch_ms": gemv_avg_ms, "avg_launch_bytes": gemv_avg_bytes,
+                     "traffic": None},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+    }
+    if rank == 0:
+        if world == 1 and os.environ.get("GDSW_BENCH_NO_CPU") != "1":
+            ms, sample = oracle_sample(p, iters[-1])
+            line["cpu_baseline"] = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
+        else:
+            line["cpu_baseline"] = None
+        line["throughput_solves_per_s"] = world * 1e3 / ms_step
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gdsw(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -209,6 +209,9 @@ int gdsw_level_dofs(gdsw_ctx* ctx, int32_t level, int64_t* offsets, int32_t* dof
 /* Coarse-space columns: for level l, the number of entities and their modes. */
 int gdsw_level_entities(gdsw_ctx* ctx, int32_t level, int32_t* n_entities);
 
+/* Number of CUDA kernels this library has launched in this process (all contexts). */
+int64_t gdsw_kernel_launches(void);
+
 int gdsw_profile_enable(gdsw_ctx* ctx, int32_t on);
 int gdsw_profile_read(gdsw_ctx* ctx, gdsw_profile* prof);
 int gdsw_profile_reset(gdsw_ctx* ctx);

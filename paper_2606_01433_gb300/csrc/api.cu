@@ -22,36 +22,12 @@ static double now_ms() {
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-// ------------------------------------------------------------------ profiling helpers
-struct ProfScope {
-  gdsw_ctx* c;
-  int group;
-  double bytes;
-  cudaStream_t s;
-  cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(gdsw_ctx* c_, int g, double by, cudaStream_t st) : c(c_), group(g), bytes(by), s(st) {
-    if (!c->prof.enabled) return;
-    a = take();
-    b = take();
-    cudaEventRecord(a, s);
-  }
-  cudaEvent_t take() {
-    if (!c->ev_pool.empty()) {
-      cudaEvent_t e = c->ev_pool.back();
-      c->ev_pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    return e;
-  }
-  ~ProfScope() {
-    if (!c->prof.enabled) return;
-    cudaEventRecord(b, s);
-    c->pending.push_back({group, a, b, bytes});
-  }
-};
+int64_t& launch_counter() {
+  static int64_t n = 0;
+  return n;
+}
 
+// ------------------------------------------------------------------ profiling helpers
 static void prof_collect(gdsw_ctx* c) {
   for (auto& p : c->pending) {
     cudaEventSynchronize(p.b);
@@ -250,9 +226,21 @@ static void add_task(std::vector<GemvTask>& tasks, std::vector<GemvTile>& tiles,
   for (int r = 0; r < t.rows; r += rpt) tiles.push_back({id, r});
 }
 
+// algorithmic bytes of the tasks [t0, t1): matrix entries read once, input read once, output
+// written (plus read when accumulated)
+static double plan_bytes(const std::vector<GemvTask>& tasks, int t0, int t1, size_t esz, size_t vsz) {
+  double b = 0;
+  for (int t = t0; t < t1; ++t) {
+    const GemvTask& q = tasks[t];
+    b += double(q.rows) * q.cols * esz + double(q.cols) * vsz + double(q.rows) * vsz * (q.base >= 0 ? 2 : 1);
+  }
+  return b;
+}
+
 static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
   std::vector<GemvTask> tasks;
   std::vector<GemvTile> tiles;
+  const size_t esz = elem_size(L.prec), vsz = L.prec == GDSW_FP64 ? 8 : 4;
   const int rpt = L.fwd.rows_per_tile;
   const int64_t nv = S.nvec;
   L.fwd.launch_task_off = {0};
@@ -295,6 +283,12 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
     L.bwd.launch_tile_off.push_back(int(tiles.size()));
     L.bwd_ld.push_back(mld);
   }
+  L.fwd_bytes.clear();
+  L.bwd_bytes.clear();
+  for (int k = 0; k < L.fwd.nlaunch(); ++k)
+    L.fwd_bytes.push_back(plan_bytes(tasks, L.fwd.launch_task_off[k], L.fwd.launch_task_off[k + 1], esz, vsz));
+  for (int k = 0; k < L.bwd.nlaunch(); ++k)
+    L.bwd_bytes.push_back(plan_bytes(tasks, L.bwd.launch_task_off[k], L.bwd.launch_task_off[k + 1], esz, vsz));
   GemvTask* dt = c->arena.upload(tasks, c->stream);
   GemvTile* dl = c->arena.upload(tiles, c->stream);
   L.fwd.d_tasks = dt;
@@ -742,33 +736,24 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
     else
       launch_gather<float>(r, L.gdof, static_cast<float*>(L.vec), nv, s);
   }
-  {
-    ProfScope ps(c, GDSW_K_LOCAL, double(L.local_bytes), s);
-    for (int k = 0; k < L.fwd.nlaunch(); ++k) {
-      if (L.prec == GDSW_FP64) {
-        double* v = static_cast<double*>(L.vec);
-        launch_gemv<double, double>(static_cast<const double*>(L.fac), v, v, v, L.fwd, k, L.fwd_ld[k], s);
-      } else if (L.prec == GDSW_FP32) {
-        float* v = static_cast<float*>(L.vec);
-        launch_gemv<float, float>(static_cast<const float*>(L.fac), v, v, v, L.fwd, k, L.fwd_ld[k], s);
-      } else {
-        float* v = static_cast<float*>(L.vec);
-        launch_gemv<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), v, v, v, L.fwd, k, L.fwd_ld[k], s);
-      }
+  // block-LDU sweeps: forward launches (S_k^{-1} y_k and the G_{k+1} update), then backward
+  // launches (W_k), every one a ragged batched GEMV over all parts of the level
+  const int group = l == 0 ? GDSW_K_LOCAL : GDSW_K_COARSE;
+  auto sweep = [&](const GemvPlan& P, int k, int ld, double bytes) {
+    ProfScope ps(c, group, bytes, s);
+    if (L.prec == GDSW_FP64) {
+      double* v = static_cast<double*>(L.vec);
+      launch_gemv<double, double>(static_cast<const double*>(L.fac), v, v, v, P, k, ld, s);
+    } else if (L.prec == GDSW_FP32) {
+      float* v = static_cast<float*>(L.vec);
+      launch_gemv<float, float>(static_cast<const float*>(L.fac), v, v, v, P, k, ld, s);
+    } else {
+      float* v = static_cast<float*>(L.vec);
+      launch_gemv<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), v, v, v, P, k, ld, s);
     }
-    for (int k = 0; k < L.bwd.nlaunch(); ++k) {
-      if (L.prec == GDSW_FP64) {
-        double* v = static_cast<double*>(L.vec);
-        launch_gemv<double, double>(static_cast<const double*>(L.fac), v, v, v, L.bwd, k, L.bwd_ld[k], s);
-      } else if (L.prec == GDSW_FP32) {
-        float* v = static_cast<float*>(L.vec);
-        launch_gemv<float, float>(static_cast<const float*>(L.fac), v, v, v, L.bwd, k, L.bwd_ld[k], s);
-      } else {
-        float* v = static_cast<float*>(L.vec);
-        launch_gemv<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), v, v, v, L.bwd, k, L.bwd_ld[k], s);
-      }
-    }
-  }
+  };
+  for (int k = 0; k < L.fwd.nlaunch(); ++k) sweep(L.fwd, k, L.fwd_ld[k], L.fwd_bytes[k]);
+  for (int k = 0; k < L.bwd.nlaunch(); ++k) sweep(L.bwd, k, L.bwd_ld[k], L.bwd_bytes[k]);
   {
     ProfScope ps(c, GDSW_K_SCATTER, double(nv) * (4 + 8 + (L.prec == GDSW_FP64 ? 8 : 4)) + 8.0 * L.n, s);
     if (L.prec == GDSW_FP64)
@@ -778,6 +763,21 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
   }
   (void)H;
   (void)gbytes;
+}
+
+// algorithmic bytes of one preconditioner apply (all levels), for the apply GB/s figure
+static double apply_bytes(const gdsw_ctx* c) {
+  double b = 0;
+  for (size_t l = 0; l < c->ld.size(); ++l) {
+    const LevelDev& L = c->ld[l];
+    const double vs = L.prec == GDSW_FP64 ? 8 : 4;
+    b += double(L.nvec) * (4 + 8 + vs) * 2 + 8.0 * L.n;                // gather + scatter
+    for (double x : L.fwd_bytes) b += x;
+    for (double x : L.bwd_bytes) b += x;
+    if (L.n0) b += 2 * (L.phi_bytes + 16.0 * L.nidofs + 16.0 * L.ngamma);  // Phi^T and Phi
+  }
+  b += 8.0 * double(c->n_coarsest) * c->ld_coarsest;
+  return b;
 }
 
 static void restrict_level(gdsw_ctx* c, int l, const double* r, double* r0, cudaStream_t s) {
@@ -836,7 +836,7 @@ void apply_precond(gdsw_ctx* c, const double* r, double* z, cudaStream_t s) {
     GDSW_CUDA(cudaMemcpyAsync(z, c->d_graph_z, sizeof(double) * c->mesh.n, cudaMemcpyDeviceToDevice, s));
     return;
   }
-  ProfScope ps(c, GDSW_K_APPLY, 0.0, s);
+  ProfScope ps(c, GDSW_K_APPLY, c->apply_bytes, s);
   apply_level(c, 0, r, z, s);
 }
 
@@ -851,8 +851,11 @@ static void capture_graph(gdsw_ctx* c) {
   cudaGraph_t g;
   GDSW_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   try {
+    c->capturing = true;
     apply_level(c, 0, c->d_graph_r, c->d_graph_z, cs);
+    c->capturing = false;
   } catch (...) {
+    c->capturing = false;
     cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
     throw;
@@ -1076,6 +1079,7 @@ static void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity*
   c->setup_ms[4] = t5 - t4;
   GDSW_CUDA(cudaStreamSynchronize(s));
   if (opt->use_graph) capture_graph(c);
+  c->apply_bytes = apply_bytes(c);
   c->setup_ms[5] = now_ms() - t0;
 }
 
@@ -1358,6 +1362,8 @@ int gdsw_level_entities(gdsw_ctx* c, int32_t level, int32_t* n_entities) {
   *n_entities = c->lh[level].cs.n_entities;
   return GDSW_OK;
 }
+
+int64_t gdsw_kernel_launches(void) { return launch_counter(); }
 
 int gdsw_profile_enable(gdsw_ctx* c, int32_t on) {
   if (!c) return GDSW_ERR_INVALID_ARG;

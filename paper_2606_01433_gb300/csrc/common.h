@@ -32,7 +32,10 @@ struct Error {
     if (!(cond)) throw ::gdsw::Error{(code), (text)};                                        \
   } while (0)
 
+// every kernel launch of the library is followed by check_launch, which also counts it
+int64_t& launch_counter();
 inline void check_launch(const char* what) {
+  ++launch_counter();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error{GDSW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
 }
@@ -226,6 +229,7 @@ struct LevelDev {
   double* zc = nullptr;         // local-branch result when the branches overlap
   // dense coarse operator of THIS level (levels >= 2), FP64 row-major
   double* A = nullptr;
+  std::vector<double> fwd_bytes, bwd_bytes;  // algorithmic bytes of each GEMV launch
   double minpiv = 0;            // smallest pivot magnitude met by the local factorisation
   double local_bytes = 0;       // algorithmic bytes of one local-solve sweep pair
   double phi_bytes = 0;         // bytes of the stored Phi_I^T blocks
@@ -237,6 +241,8 @@ struct LevelDev {
 struct gdsw_ctx {
   std::string err;
   bool host_only = false;           // created by gdsw_analyze: no device state
+  bool capturing = false;           // inside CUDA-graph capture (no profiling events)
+  double apply_bytes = 0;           // algorithmic bytes of one preconditioner apply
   int64_t est_device_bytes = 0;
   cudaStream_t stream = nullptr, stream2 = nullptr;
   bool own_stream = false;
@@ -296,3 +302,36 @@ struct gdsw_ctx {
   gdsw_sizes_info sizes{};
   double setup_ms[6] = {0};
 };
+
+namespace gdsw {
+// CUDA-event timing of one kernel group on one stream when profiling is enabled; the pair
+// is read back by gdsw_profile_read together with the group's algorithmic bytes.
+struct ProfScope {
+  gdsw_ctx* c;
+  int group;
+  double bytes;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(gdsw_ctx* c_, int g, double by, cudaStream_t st) : c(c_), group(g), bytes(by), s(st) {
+    if (!c->prof.enabled || c->capturing) return;
+    a = take();
+    b = take();
+    cudaEventRecord(a, s);
+  }
+  cudaEvent_t take() {
+    if (!c->ev_pool.empty()) {
+      cudaEvent_t e = c->ev_pool.back();
+      c->ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  ~ProfScope() {
+    if (!c->prof.enabled || c->capturing) return;
+    cudaEventRecord(b, s);
+    c->pending.push_back({group, a, b, bytes});
+  }
+};
+}  // namespace gdsw

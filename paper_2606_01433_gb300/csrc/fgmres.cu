@@ -183,15 +183,24 @@ static void cgs2(gdsw_ctx* c, int j, double* w, cudaStream_t s) {
   double* hcol = c->d_H + int64_t(j) * (c->m_alloc + 1);
   dim3 gd(RB, (nvec + DG - 1) / DG);
   const int ub = int((n + 255) / 256);
+  // four passes over the basis (two multi-dots, two multi-axpys) plus w traffic and the norm
+  ProfScope ps(c, GDSW_K_ARNOLDI, 8.0 * n * (4.0 * nvec + 7.0), s);
   for (int pass = 0; pass < 2; ++pass) {
     k_dots<<<gd, RT, 0, s>>>(c->d_V, n, nvec, w, c->d_part, ldp);
+    check_launch("k_dots");
     k_sum_parts<<<(nvec + 127) / 128, 128, 0, s>>>(c->d_part, RB, nvec, ldp, pass == 0 ? hcol : c->d_y, 0);
+    check_launch("k_sum_parts");
     k_update<<<ub, 256, nvec * sizeof(double), s>>>(c->d_V, n, nvec, pass == 0 ? hcol : c->d_y, w);
-    if (pass == 1) k_sum_parts<<<(nvec + 127) / 128, 128, 0, s>>>(c->d_part, RB, nvec, ldp, hcol, 1);
+    check_launch("k_update");
+    if (pass == 1) {
+      k_sum_parts<<<(nvec + 127) / 128, 128, 0, s>>>(c->d_part, RB, nvec, ldp, hcol, 1);
+      check_launch("k_sum_parts");
+    }
   }
   k_norm_parts<<<RB, RT, 0, s>>>(w, n, c->d_part);
+  check_launch("k_norm_parts");
   k_norm_finish<<<1, 32, 0, s>>>(c->d_part, RB, c->d_scal, 1);
-  check_launch("cgs2");
+  check_launch("k_norm_finish");
 }
 
 void fgmres_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info) {
@@ -207,7 +216,9 @@ void fgmres_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info
   GDSW_CUDA(cudaEventRecord(e0, s));
   // ||b||
   k_norm_parts<<<RB, RT, 0, s>>>(b, n, c->d_part);
+  check_launch("k_norm_parts");
   k_norm_finish<<<1, 32, 0, s>>>(c->d_part, RB, c->d_scal, 3);
+  check_launch("k_norm_finish");
   double bnorm = 0.0;
   GDSW_CUDA(cudaMemcpyAsync(&bnorm, c->d_scal + 3, 8, cudaMemcpyDeviceToHost, s));
   GDSW_CUDA(cudaStreamSynchronize(s));
@@ -223,10 +234,16 @@ void fgmres_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info
   const double tol = c->opt.tol;
   int it = 0;
   double est = 0.0, beta = 0.0;
+  const double spmv_b = c->spmv_bytes();
   auto true_residual = [&]() {
-    launch_spmv(c, x, c->d_V, b, s);  // V[0] = b - A x
+    {
+      ProfScope ps(c, GDSW_K_SPMV, spmv_b + 8.0 * n, s);
+      launch_spmv(c, x, c->d_V, b, s);  // V[0] = b - A x
+    }
     k_norm_parts<<<RB, RT, 0, s>>>(c->d_V, n, c->d_part);
+    check_launch("k_norm_parts");
     k_norm_finish<<<1, 32, 0, s>>>(c->d_part, RB, c->d_scal, 0);
+    check_launch("k_norm_finish");
     GDSW_CUDA(cudaMemcpyAsync(&beta, c->d_scal, 8, cudaMemcpyDeviceToHost, s));
     GDSW_CUDA(cudaStreamSynchronize(s));
   };
@@ -243,20 +260,26 @@ void fgmres_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info
       break;
     }
     k_scale<<<ub, 256, 0, s>>>(c->d_V, n, c->d_scal, 0, c->d_V);
+    check_launch("k_scale");
     k_cycle_start<<<(m + 1 + 127) / 128, 128, 0, s>>>(c->d_gvec, m + 1, c->d_scal);
+    check_launch("k_cycle_start");
     int jd = 0;
     for (int j = 0; j < m && it < c->opt.max_it; ++j) {
       double* vj = c->d_V + int64_t(j) * n;
       double* zj = c->d_Z + int64_t(j) * n;
       double* w = c->d_V + int64_t(j + 1) * n;
       apply_precond(c, vj, zj, s);
-      launch_spmv(c, zj, w, nullptr, s);
+      {
+        ProfScope ps(c, GDSW_K_SPMV, spmv_b, s);
+        launch_spmv(c, zj, w, nullptr, s);
+      }
       cgs2(c, j, w, s);
       k_scale<<<ub, 256, 0, s>>>(w, n, c->d_scal, 1, w);
+      check_launch("k_scale");
       k_givens<<<1, 32, 0, s>>>(c->d_H, ldh, j, c->d_cs, c->d_sn, c->d_gvec, c->d_scal, nullptr);
+      check_launch("k_givens");
       GDSW_CUDA(cudaMemcpyAsync(c->h_scal, c->d_scal + 2, 8, cudaMemcpyDeviceToHost, s));
       GDSW_CUDA(cudaStreamSynchronize(s));
-      check_launch("fgmres iteration");
       est = c->h_scal[0];
       ++it;
       jd = j + 1;
@@ -268,8 +291,9 @@ void fgmres_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info
     }
     if (status == GDSW_ERR_NAN) break;
     k_backsolve<<<1, 32, 0, s>>>(c->d_H, ldh, jd, c->d_gvec, c->d_y);
+    check_launch("k_backsolve");
     k_xupdate<<<ub, 256, jd * sizeof(double), s>>>(c->d_Z, n, jd, c->d_y, x);
-    check_launch("fgmres update");
+    check_launch("k_xupdate");
     true_residual();
   }
   GDSW_CUDA(cudaEventRecord(e1, s));

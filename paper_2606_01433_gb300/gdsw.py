@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "gdsw_viscosity_values": ([vp, dp], C.c_int),
         "gdsw_level_dofs": ([vp, i32, dp, dp], C.c_int),
         "gdsw_level_entities": ([vp, i32, C.POINTER(i32)], C.c_int),
+        "gdsw_kernel_launches": ([], i64),
         "gdsw_profile_enable": ([vp, i32], C.c_int),
         "gdsw_profile_read": ([vp, C.POINTER(gdsw_profile)], C.c_int),
         "gdsw_profile_reset": ([vp], C.c_int),
