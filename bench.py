@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--mixed", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison context")
     ap.add_argument("--m", type=int, default=32, help="elements per edge of the channel")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--prof-stride", type=int, default=8,
+                    help="CUDA-event timing of every k-th preconditioner apply inside the timed region")
     return ap.parse_args()
 
 
@@ -239,7 +243,7 @@ def run_gdsw(args, rank, world, local):
 
     for _ in range(args.warmup):
         info = step(ctx)
-    ctx.gdsw_profile_enable(True)
+    ctx.gdsw_profile_enable(args.prof_stride)
     ctx.gdsw_profile_reset()
     stream = torch.cuda.current_stream()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -248,6 +252,8 @@ def run_gdsw(args, rank, world, local):
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
+    if args.profile_region:
+        torch.cuda.profiler.start()
     evs[0].record(stream)
     iters = []
     for k in range(args.steps):
@@ -255,6 +261,8 @@ def run_gdsw(args, rank, world, local):
         iters.append(info.iterations)
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.profiler.stop()
     barrier(world)
     clk = clocks.stop()
     launches = lib.gdsw_kernel_launches() - launches0
@@ -358,7 +366,8 @@ def run_gdsw(args, rank, world, local):
         "apply_gbs": apply_gbs,
         "apply_ms": ap["ms"] / max(ap["calls"], 1),
         "spmv_gbs": spmv_gbs,
-        "arnoldi_ms_per_solve": ar["ms"] / args.steps,
+        "arnoldi_ms_per_solve": ar["ms"] / max(ar["calls"], 1) * iters[-1],
+        "spmv_ms_per_solve": sp["ms"] / max(sp["calls"], 1) * (iters[-1] + 2),
         "fp64": fp64,
         "speedup_vs_fp64": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "setup_s": setup_mixed_s,

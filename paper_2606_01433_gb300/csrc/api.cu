@@ -115,35 +115,32 @@ static void factor_slabs(const SlabSet& S, T* fac, double& minpiv, cudaStream_t 
   int64_t maxB = 1, maxC = 1;
   for (int k = 0; k < S.Kmax; ++k) {
     int64_t sb = 0, sc = 0;
-    for (int i = 0; i < S.nsub; ++i) {
+    for (int i = 0; i < S.nsub; ++i)
       if (k >= 1 && k < S.K[i]) sb += int64_t(S.m[i][k]) * S.ldG[i][k];
-      if (k + 1 < S.K[i]) sc += int64_t(S.s[i][k]) * S.ldW[i][k];
-    }
     maxB = std::max(maxB, sb);
-    maxC = std::max(maxC, sc);
+    (void)sc;
   }
   T* scrB = tmp.alloc<T>(maxB);
-  T* scrC = tmp.alloc<T>(maxC);
   minpiv = 1e300;
   try {
+    // symmetric block LDL^T: G_k = B_k S_{k-1}^{-1}, S_k = A_kk - G_k B_k^T
     for (int k = 0; k < S.Kmax; ++k) {
       if (k >= 1) {
-        std::vector<GemmTaskP> tasks;
+        std::vector<GemmTaskP> tg, tu;
         int64_t off = 0;
         for (int i = 0; i < S.nsub; ++i) {
           if (k >= S.K[i] || S.m[i][k] == 0) continue;
           int m = S.m[i][k], sp = S.s[i][k - 1];
           int64_t cnt = int64_t(m) * S.ldG[i][k];
           GDSW_CUDA(cudaMemcpyAsync(scrB + off, fac + S.fG[i][k], cnt * sizeof(T), cudaMemcpyDeviceToDevice, s));
-          GemmTaskP u{scrB + off, fac + S.fW[i][k - 1], fac + S.fS[i][k], m, m, sp, S.ldG[i][k], S.ldW[i][k - 1],
-                      S.ldS[i][k], 0, 0, -1.0, 1.0};
-          GemmTaskP g{scrB + off, fac + S.fS[i][k - 1], fac + S.fG[i][k], m, sp, sp, S.ldG[i][k], S.ldS[i][k - 1],
-                      S.ldG[i][k], 0, 0, 1.0, 0.0};
-          tasks.push_back(u);
-          tasks.push_back(g);
+          tg.push_back({scrB + off, fac + S.fS[i][k - 1], fac + S.fG[i][k], m, sp, sp, S.ldG[i][k], S.ldS[i][k - 1],
+                        S.ldG[i][k], 0, 0, 1.0, 0.0});
+          tu.push_back({fac + S.fG[i][k], scrB + off, fac + S.fS[i][k], m, m, sp, S.ldG[i][k], S.ldG[i][k],
+                        S.ldS[i][k], 0, 1, -1.0, 1.0});
           off += cnt;
         }
-        run_gemm<T>(tmp, tasks, s);
+        run_gemm<T>(tmp, tg, s);
+        run_gemm<T>(tmp, tu, s);
       }
       std::vector<InvTaskP> inv;
       for (int i = 0; i < S.nsub; ++i)
@@ -151,18 +148,6 @@ static void factor_slabs(const SlabSet& S, T* fac, double& minpiv, cudaStream_t 
       std::vector<double> mp;
       run_inverse<T>(tmp, inv, mp, s);
       for (double v : mp) minpiv = std::min(minpiv, v);
-      std::vector<GemmTaskP> wt;
-      int64_t off = 0;
-      for (int i = 0; i < S.nsub; ++i) {
-        if (k + 1 >= S.K[i] || S.m[i][k + 1] == 0) continue;
-        int sk = S.s[i][k], m1 = S.m[i][k + 1];
-        int64_t cnt = int64_t(sk) * S.ldW[i][k];
-        GDSW_CUDA(cudaMemcpyAsync(scrC + off, fac + S.fW[i][k], cnt * sizeof(T), cudaMemcpyDeviceToDevice, s));
-        wt.push_back({fac + S.fS[i][k], scrC + off, fac + S.fW[i][k], sk, m1, sk, S.ldS[i][k], S.ldW[i][k],
-                      S.ldW[i][k], 0, 0, 1.0, 0.0});
-        off += cnt;
-      }
-      run_gemm<T>(tmp, wt, s);
     }
     GDSW_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
@@ -199,8 +184,9 @@ static void sweep_multi(const SlabSet& S, const T* fac, T* R, T* W, const std::v
       for (int i = 0; i < S.nsub; ++i) {
         int k = S.K[i] - 2 - j;
         if (k < 0 || nc[i] == 0 || S.m[i][k + 1] == 0) continue;
-        b.push_back({fac + S.fW[i][k], W + toff[i] + S.soff[i][k + 1] * ldt[i], W + toff[i] + S.soff[i][k] * ldt[i],
-                     S.s[i][k], nc[i], S.m[i][k + 1], S.ldW[i][k], ldt[i], ldt[i], 0, 0, -1.0, 1.0});
+        // X_k -= G_{k+1}^T X_{k+1}[0:m_{k+1}]  (the super-diagonal block of the symmetric LDL^T)
+        b.push_back({fac + S.fG[i][k + 1], W + toff[i] + S.soff[i][k + 1] * ldt[i], W + toff[i] + S.soff[i][k] * ldt[i],
+                     S.s[i][k], nc[i], S.m[i][k + 1], S.ldG[i][k + 1], ldt[i], ldt[i], 1, 0, -1.0, 1.0});
       }
       run_gemm<T>(tmp, b, s);
     }
@@ -228,11 +214,13 @@ static void add_task(std::vector<GemvTask>& tasks, std::vector<GemvTile>& tiles,
 
 // algorithmic bytes of the tasks [t0, t1): matrix entries read once, input read once, output
 // written (plus read when accumulated)
-static double plan_bytes(const std::vector<GemvTask>& tasks, int t0, int t1, size_t esz, size_t vsz) {
+static double plan_bytes(const std::vector<GemvTask>& tasks, int t0, int t1, size_t esz, size_t vsz,
+                         bool transposed = false) {
   double b = 0;
   for (int t = t0; t < t1; ++t) {
     const GemvTask& q = tasks[t];
-    b += double(q.rows) * q.cols * esz + double(q.cols) * vsz + double(q.rows) * vsz * (q.base >= 0 ? 2 : 1);
+    double in = transposed ? q.rows : q.cols, out = transposed ? q.cols : q.rows;
+    b += double(q.rows) * q.cols * esz + in * vsz + out * vsz * (q.base >= 0 ? 2 : 1);
   }
   return b;
 }
@@ -265,30 +253,34 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
     L.fwd.launch_tile_off.push_back(int(tiles.size()));
     L.fwd_ld.push_back(mld);
   }
+  // backward: x_k = w_k - G_{k+1}^T x_{k+1}[0:m_{k+1}], transposed GEMV over 256-column tiles
+  L.bwd.transposed = true;
   L.bwd.launch_task_off = {int(tasks.size())};
   L.bwd.launch_tile_off = {int(tiles.size())};
   L.bwd_ld.clear();
   for (int j = 0; j + 1 < S.Kmax; ++j) {
-    int mld = 8;
+    int mrows = 8;
     for (int i = 0; i < S.nsub; ++i) {
       int k = S.K[i] - 2 - j;
       if (k < 0 || S.m[i][k + 1] == 0) continue;
       int64_t y = nv + S.voff[i] + S.soff[i][k];
       int64_t x = nv + S.voff[i] + S.soff[i][k + 1];
-      GemvTask t{S.fW[i][k], x, y, y, S.s[i][k], S.m[i][k + 1], S.ldW[i][k], -1.0f};
-      add_task(tasks, tiles, t, rpt);
-      mld = std::max(mld, S.ldW[i][k]);
+      GemvTask t{S.fG[i][k + 1], x, y, y, S.m[i][k + 1], S.s[i][k], S.ldG[i][k + 1], -1.0f};
+      int id = int(tasks.size());
+      tasks.push_back(t);
+      for (int c0 = 0; c0 < t.cols; c0 += 256) tiles.push_back({id, c0});
+      mrows = std::max(mrows, t.rows);
     }
     L.bwd.launch_task_off.push_back(int(tasks.size()));
     L.bwd.launch_tile_off.push_back(int(tiles.size()));
-    L.bwd_ld.push_back(mld);
+    L.bwd_ld.push_back(mrows);
   }
   L.fwd_bytes.clear();
   L.bwd_bytes.clear();
   for (int k = 0; k < L.fwd.nlaunch(); ++k)
     L.fwd_bytes.push_back(plan_bytes(tasks, L.fwd.launch_task_off[k], L.fwd.launch_task_off[k + 1], esz, vsz));
   for (int k = 0; k < L.bwd.nlaunch(); ++k)
-    L.bwd_bytes.push_back(plan_bytes(tasks, L.bwd.launch_task_off[k], L.bwd.launch_task_off[k + 1], esz, vsz));
+    L.bwd_bytes.push_back(plan_bytes(tasks, L.bwd.launch_task_off[k], L.bwd.launch_task_off[k + 1], esz, vsz, true));
   GemvTask* dt = c->arena.upload(tasks, c->stream);
   GemvTile* dl = c->arena.upload(tiles, c->stream);
   L.fwd.d_tasks = dt;
@@ -805,7 +797,7 @@ static void apply_level(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
   LevelDev& L = c->ld[l];
   const int nlev = int(c->ld.size());
   const bool coarse = L.n0 > 0;
-  const bool fork = coarse && l == 0 && c->stream2 != nullptr && !c->prof.enabled;
+  const bool fork = coarse && l == 0 && c->stream2 != nullptr;
   cudaStream_t sc = fork ? c->stream2 : s;
   if (fork) {
     GDSW_CUDA(cudaEventRecord(c->ev_fork, s));
@@ -830,7 +822,11 @@ static void apply_level(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
 }
 
 void apply_precond(gdsw_ctx* c, const double* r, double* z, cudaStream_t s) {
-  if (c->apply_graph && !c->prof.enabled) {
+  if (c->prof.enabled) {
+    c->prof_gate = (c->apply_count % c->prof_stride) == 0;
+    ++c->apply_count;
+  }
+  if (c->apply_graph && !(c->prof.enabled && c->prof_gate)) {
     GDSW_CUDA(cudaMemcpyAsync(c->d_graph_r, r, sizeof(double) * c->mesh.n, cudaMemcpyDeviceToDevice, s));
     GDSW_CUDA(cudaGraphLaunch(c->apply_graph, s));
     GDSW_CUDA(cudaMemcpyAsync(z, c->d_graph_z, sizeof(double) * c->mesh.n, cudaMemcpyDeviceToDevice, s));
@@ -947,6 +943,8 @@ static void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity*
   c->d_pnode = c->arena.upload(M.pnode, s);
   c->d_a_ptr = c->arena.upload(M.a_ptr, s);
   c->d_a_col = c->arena.upload(M.a_col, s);
+  c->d_a_diag = c->arena.upload(M.a_diag, s);
+  c->d_a_tpos = c->arena.upload(M.a_tpos, s);
   c->d_bt_ptr = c->arena.upload(M.bt_ptr, s);
   c->d_bt_col = c->arena.upload(M.bt_col, s);
   c->d_b_ptr = c->arena.upload(M.b_ptr, s);
@@ -1265,8 +1263,9 @@ int gdsw_solve_host(gdsw_ctx* c, const double* bh, double* xh, gdsw_solve_info* 
 }
 
 int gdsw_reassemble(gdsw_ctx* c, const double* uk) {
-  if (!c) return GDSW_ERR_INVALID_ARG;
+  if (!c || c->host_only) return GDSW_ERR_INVALID_ARG;
   GDSW_TRY(c, {
+    c->prof_gate = true;
     if (uk) {
       GDSW_CUDA(cudaMemcpyAsync(c->d_uk, uk, 24 * c->mesh.nnodes, cudaMemcpyHostToDevice, c->stream));
       c->has_uk = true;
@@ -1367,7 +1366,11 @@ int64_t gdsw_kernel_launches(void) { return launch_counter(); }
 
 int gdsw_profile_enable(gdsw_ctx* c, int32_t on) {
   if (!c) return GDSW_ERR_INVALID_ARG;
+  // on = 0: off; on = k >= 1: time every k-th preconditioner apply and the work after it
   c->prof.enabled = on ? 1 : 0;
+  c->prof_stride = on > 1 ? on : 1;
+  c->apply_count = 0;
+  c->prof_gate = true;
   return GDSW_OK;
 }
 

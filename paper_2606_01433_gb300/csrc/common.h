@@ -111,7 +111,9 @@ struct InvTask {
 // ------------------------------------------------------------------ host symbolic structures
 // A batch of block-tridiagonal local problems: dof lists in slab order, slab sizes, the
 // number of back-coupled dofs (those coupled to the previous slab, ordered first) and the
-// offsets of the LDU blocks Sinv_k (s_k x s_k), G_k (m_k x s_{k-1}), W_k (s_k x m_{k+1}).
+// offsets of the LDL^T blocks Sinv_k (s_k x s_k) and G_k (m_k x s_{k-1}); the
+// super-diagonal blocks of the symmetric factorisation are the transposes G_{k+1}^T, so no
+// W_k block is stored (fW = -1).
 struct SlabSet {
   int nsub = 0;
   int Kmax = 0;
@@ -176,6 +178,7 @@ struct MeshHost {
   std::vector<int32_t> bt_ptr, bt_col;   // velocity node rows x pressure cols
   std::vector<int32_t> b_ptr, b_col;     // pressure rows x velocity node cols
   std::vector<int32_t> bt2b;             // BT entry -> B entry with the same value
+  std::vector<int32_t> a_diag, a_tpos;   // position of block (I,I); position of block (J,I) for (I,J)
   std::vector<int32_t> ad_ptr, ad_col;   // velocity rows x Dirichlet velocity nodes (node ids)
   std::vector<int32_t> bd_ptr, bd_col;   // pressure rows x Dirichlet velocity nodes
   bool shares_element(int64_t a, int64_t b) const;
@@ -192,6 +195,7 @@ struct GemvPlan {
   GemvTask* d_tasks = nullptr;
   GemvTile* d_tiles = nullptr;
   int rows_per_tile = 32;
+  bool transposed = false;      // tiles are 256-column blocks of y = M^T x
   int nlaunch() const { return int(launch_task_off.size()) - 1; }
 };
 
@@ -242,6 +246,9 @@ struct gdsw_ctx {
   std::string err;
   bool host_only = false;           // created by gdsw_analyze: no device state
   bool capturing = false;           // inside CUDA-graph capture (no profiling events)
+  int prof_stride = 1;              // time every prof_stride-th apply (and the work after it)
+  int64_t apply_count = 0;
+  bool prof_gate = true;
   double apply_bytes = 0;           // algorithmic bytes of one preconditioner apply
   int64_t est_device_bytes = 0;
   cudaStream_t stream = nullptr, stream2 = nullptr;
@@ -265,6 +272,7 @@ struct gdsw_ctx {
   int32_t* d_felem = nullptr;
   int32_t *d_vnode = nullptr, *d_pnode = nullptr, *d_vidx = nullptr;
   int32_t *d_a_ptr = nullptr, *d_a_col = nullptr, *d_bt_ptr = nullptr, *d_bt_col = nullptr;
+  int32_t *d_a_diag = nullptr, *d_a_tpos = nullptr;  // diagonal block of each row, transpose map
   int32_t *d_b_ptr = nullptr, *d_b_col = nullptr, *d_bt2b = nullptr;
   int32_t *d_ad_ptr = nullptr, *d_ad_col = nullptr, *d_bd_ptr = nullptr, *d_bd_col = nullptr;
   double* d_gdir = nullptr;         // Dirichlet datum, 3 per node
@@ -312,8 +320,10 @@ struct ProfScope {
   double bytes;
   cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
+  bool on = false;
   ProfScope(gdsw_ctx* c_, int g, double by, cudaStream_t st) : c(c_), group(g), bytes(by), s(st) {
-    if (!c->prof.enabled || c->capturing) return;
+    on = c->prof.enabled && c->prof_gate && !c->capturing;
+    if (!on) return;
     a = take();
     b = take();
     cudaEventRecord(a, s);
@@ -329,7 +339,7 @@ struct ProfScope {
     return e;
   }
   ~ProfScope() {
-    if (!c->prof.enabled || c->capturing) return;
+    if (!on) return;
     cudaEventRecord(b, s);
     c->pending.push_back({group, a, b, bytes});
   }

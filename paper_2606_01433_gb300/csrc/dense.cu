@@ -111,14 +111,85 @@ __global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV
   }
 }
 
+// ------------------------------------------------------------------ ragged batched GEMV, transposed
+// y[c] = base[c] + alpha * sum_r M[r][c] x[r] for the columns [col0, col0 + 256) of a task
+// (used with the sub-diagonal blocks G of a symmetric LDL^T factorisation, whose
+// transposes are the super-diagonal blocks).  Each lane owns 8 consecutive columns and the
+// 8 warps split the rows; partial sums are combined in shared memory in a fixed order.
+__device__ __forceinline__ void load8(const float* p, float* v) {
+  load16s(p, v);
+  load16s(p + 4, v + 4);
+}
+__device__ __forceinline__ void load8(const double* p, double* v) {
+  load16s(p, v);
+  load16s(p + 2, v + 2);
+  load16s(p + 4, v + 4);
+  load16s(p + 6, v + 6);
+}
+__device__ __forceinline__ void load8(const __nv_bfloat16* p, float* v) { load16s(p, v); }
+
+template <typename TM, typename TV>
+__global__ void __launch_bounds__(256) k_gemvt(const TM* __restrict__ M, const TV* xbase, TV* ybase,
+                                               const TV* bbase, const GemvTask* __restrict__ tasks,
+                                               const GemvTile* __restrict__ tiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TV* xs = reinterpret_cast<TV*>(smem_raw);
+  __shared__ TV part[8][256 + 1];
+  const GemvTile tl = tiles[blockIdx.x];
+  const GemvTask t = tasks[tl.task];
+  for (int r = threadIdx.x; r < t.rows; r += blockDim.x) xs[r] = xbase[t.x + r];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = tl.row0 + lane * 8;  // tile column start + lane's 8 columns
+  TV acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = TV(0);
+  if (c0 < t.ld) {
+    const TM* p = M + t.mat + c0;
+    int r = warp;
+    for (; r + 8 < t.rows; r += 16) {  // two rows in flight per warp
+      TV v0[8], v1[8];
+      load8(p + int64_t(r) * t.ld, v0);
+      load8(p + int64_t(r + 8) * t.ld, v1);
+      const TV x0 = xs[r], x1 = xs[r + 8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = fma(v1[u], x1, fma(v0[u], x0, acc[u]));
+    }
+    for (; r < t.rows; r += 8) {
+      TV v0[8];
+      load8(p + int64_t(r) * t.ld, v0);
+      const TV x0 = xs[r];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = fma(v0[u], x0, acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) part[warp][lane * 8 + u] = acc[u];
+  __syncthreads();
+  const int c = tl.row0 + threadIdx.x;
+  if (c < t.cols) {
+    TV s = part[0][threadIdx.x];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) s += part[w][threadIdx.x];
+    TV v = TV(t.alpha) * s;
+    if (t.base >= 0) v += bbase[t.base + c];
+    ybase[t.y + c] = v;
+  }
+}
+
 template <typename TM, typename TV>
 void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P, int launch, int max_ld,
                  cudaStream_t s) {
   int t0 = P.launch_tile_off[launch], t1 = P.launch_tile_off[launch + 1];
   if (t1 <= t0) return;
   size_t smem = size_t(max_ld) * sizeof(TV);
-  k_gemv<TM, TV, 4><<<t1 - t0, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
-  check_launch("k_gemv");
+  if (P.transposed) {
+    k_gemvt<TM, TV><<<t1 - t0, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+    check_launch("k_gemvt");
+  } else {
+    k_gemv<TM, TV, 4><<<t1 - t0, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+    check_launch("k_gemv");
+  }
 }
 
 template void launch_gemv<double, double>(const double*, const double*, double*, const double*, const GemvPlan&,
@@ -132,6 +203,9 @@ void set_gemv_smem_limits() {
   cudaFuncSetAttribute(k_gemv<double, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_gemv<float, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_gemv<__nv_bfloat16, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemvt<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
+  cudaFuncSetAttribute(k_gemvt<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
+  cudaFuncSetAttribute(k_gemvt<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
 }
 
 // ------------------------------------------------------------------ batched GEMM (set-up)

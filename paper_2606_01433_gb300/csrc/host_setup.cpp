@@ -170,6 +170,19 @@ void build_mesh(MeshHost& M, const gdsw_mesh* m) {
   build(M.pnode, 0, M.b_ptr, M.b_col);
   build(M.vnode, 2, M.ad_ptr, M.ad_col);
   build(M.pnode, 2, M.bd_ptr, M.bd_col);
+  // symmetric velocity pattern: diagonal block of each row and the transpose of each block
+  M.a_diag.assign(M.nv, -1);
+  M.a_tpos.resize(M.a_col.size());
+  for (int64_t I = 0; I < M.nv; ++I)
+    for (int32_t blk = M.a_ptr[I]; blk < M.a_ptr[I + 1]; ++blk) {
+      int32_t J = M.a_col[blk];
+      if (J == I) M.a_diag[I] = blk;
+      auto r0 = M.a_col.begin() + M.a_ptr[J], r1 = M.a_col.begin() + M.a_ptr[J + 1];
+      auto it = std::lower_bound(r0, r1, int32_t(I));
+      GDSW_CHECK(it != r1 && *it == int32_t(I), GDSW_ERR_INVALID_ARG, "asymmetric velocity pattern");
+      M.a_tpos[blk] = int32_t(it - M.a_col.begin());
+    }
+  for (int64_t I = 0; I < M.nv; ++I) GDSW_CHECK(M.a_diag[I] >= 0, GDSW_ERR_INVALID_ARG, "missing diagonal block");
   // BT entry (I, P) has the value of B entry (P, I)
   M.bt2b.resize(M.bt_col.size());
   for (int64_t I = 0; I < M.nv; ++I)
@@ -212,11 +225,9 @@ void SlabSet::layout() {
       ldG[i].push_back(ldg);
       fG[i].push_back(nfac);
       if (k > 0) nfac += int64_t(m[i][k]) * ldg;
-      // W_k: s_k x m_{k+1}
-      int ldw = k + 1 < K[i] ? int(pad8(m[i][k + 1])) : 8;
-      ldW[i].push_back(ldw);
-      fW[i].push_back(nfac);
-      if (k + 1 < K[i]) nfac += int64_t(sk) * ldw;
+      // W_k = S_k^{-1} C_k is not stored: the operator is symmetric, so W_k = G_{k+1}^T
+      ldW[i].push_back(8);
+      fW[i].push_back(-1);
     }
   }
   nvec = voff[nsub];

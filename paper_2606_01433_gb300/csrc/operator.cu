@@ -165,18 +165,84 @@ __device__ void divergence_entry(int64_t P, int64_t J, const Geo& G, const uint8
 }
 
 // ------------------------------------------------------------------ a2: assembly
-__global__ void k_assemble_A(const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_col,
-                             const int32_t* __restrict__ vnode, int64_t nv, Geo G, const uint8_t* mask,
-                             const int32_t* felem, const double* nu, const RefTables* T, int form,
-                             double* __restrict__ val) {
-  int64_t I = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
-  int lane = threadIdx.x & 31;
+// One warp per block row I; lanes take the blocks (I, J) with J >= I (the operator is
+// symmetric: the (J, I) block is the transpose, written through the transpose map).  The
+// reference gradients live in shared memory; the element sum runs in a fixed order.
+struct SmemTables {
+  double dphi[27][27][3];
+  double w[27];
+};
+
+__global__ void __launch_bounds__(256) k_assemble_A(const int32_t* __restrict__ a_ptr,
+                                                    const int32_t* __restrict__ a_col,
+                                                    const int32_t* __restrict__ a_diag,
+                                                    const int32_t* __restrict__ a_tpos,
+                                                    const int32_t* __restrict__ vnode, int64_t nv, Geo G,
+                                                    const uint8_t* __restrict__ mask, const int32_t* __restrict__ felem,
+                                                    const double* __restrict__ nu, const RefTables* __restrict__ T,
+                                                    int form, double* __restrict__ val) {
+  __shared__ SmemTables st;
+  {
+    const double* src = &T->dphi[0][0][0];
+    double* dst = &st.dphi[0][0][0];
+    for (int e = threadIdx.x; e < 27 * 27 * 3; e += blockDim.x) dst[e] = src[e];
+    if (threadIdx.x < 27) st.w[threadIdx.x] = T->w[threadIdx.x];
+  }
+  __syncthreads();
+  const int64_t I = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
   if (I >= nv) return;
-  for (int blk = a_ptr[I] + lane; blk < a_ptr[I + 1]; blk += 32) {
+  const int64_t nodeI = vnode[I];
+  int ii, ij, ik;
+  node_ijk(nodeI, G, ii, ij, ik);
+  const double sc = 0.5 * G.h;  // (h/2)^3 * (2/h)^2
+  for (int blk = a_diag[I] + lane; blk < a_ptr[I + 1]; blk += 32) {
+    int ji, jj, jk;
+    node_ijk(vnode[a_col[blk]], G, ji, jj, jk);
     double out[9];
-    velocity_block(vnode[I], vnode[a_col[blk]], G, mask, felem, nu, T, form, out);
 #pragma unroll
-    for (int c = 0; c < 9; ++c) val[int64_t(blk) * 9 + c] = out[c];
+    for (int c = 0; c < 9; ++c) out[c] = 0.0;
+    int e0x, e0y, e0z;
+    int nxr = shared_range(ii, ji, G.nx, e0x), nyr = shared_range(ij, jj, G.ny, e0y),
+        nzr = shared_range(ik, jk, G.nz, e0z);
+    for (int cz = 0; cz < nzr; ++cz)
+      for (int cy = 0; cy < nyr; ++cy)
+        for (int cx = 0; cx < nxr; ++cx) {
+          const int ex = e0x + cx, ey = e0y + cy, ez = e0z + cz;
+          const int64_t e = ex + int64_t(G.nx) * (ey + int64_t(G.ny) * ez);
+          if (!mask[e]) continue;
+          const double* nq = nu + int64_t(felem[e]) * 27;
+          const int a = (ii - 2 * ex) + 3 * (ij - 2 * ey) + 9 * (ik - 2 * ez);
+          const int b = (ji - 2 * ex) + 3 * (jj - 2 * ey) + 9 * (jk - 2 * ez);
+          for (int q = 0; q < 27; ++q) {
+            const double* da = st.dphi[q][a];
+            const double* db = st.dphi[q][b];
+            const double f = __ldg(nq + q) * st.w[q] * sc;
+            const double g = f * (da[0] * db[0] + da[1] * db[1] + da[2] * db[2]);
+            out[0] += g;
+            out[4] += g;
+            out[8] += g;
+            if (form == GDSW_FORM_SYMMETRIC) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const double fdc = f * db[c];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) out[c * 3 + d] = fma(fdc, da[d], out[c * 3 + d]);
+              }
+            }
+          }
+        }
+    double* v = val + int64_t(blk) * 9;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) v[c] = out[c];
+    const int tb = a_tpos[blk];
+    if (tb != blk) {
+      double* w = val + int64_t(tb) * 9;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) w[d * 3 + c] = out[c * 3 + d];
+    }
   }
 }
 
@@ -324,8 +390,8 @@ void launch_assembly(gdsw_ctx* c, cudaStream_t s) {
   double* aval = c->d_val;
   double* btval = c->d_val + 9 * c->nnzb;
   double* bval = btval + 3 * c->nbt;
-  k_assemble_A<<<int((nv + 7) / 8), 256, 0, s>>>(c->d_a_ptr, c->d_a_col, c->d_vnode, nv, geo(c), c->d_mask,
-                                                 c->d_felem, c->d_nu, T, c->form, aval);
+  k_assemble_A<<<int((nv + 7) / 8), 256, 0, s>>>(c->d_a_ptr, c->d_a_col, c->d_a_diag, c->d_a_tpos, c->d_vnode, nv,
+                                                 geo(c), c->d_mask, c->d_felem, c->d_nu, T, c->form, aval);
   check_launch("k_assemble_A");
   k_assemble_B<<<int((np + 7) / 8), 256, 0, s>>>(c->d_b_ptr, c->d_b_col, c->d_pnode, c->d_vnode, np, geo(c),
                                                  c->d_mask, T, bval);

@@ -74,7 +74,8 @@ __global__ void k_extract(MatView A, SlabView S, int64_t p0, int64_t p1, int i0,
     } else if (kc == kr - 1 && r < S.m[sb + kr]) {
       fac[S.fG[sb + kr] + int64_t(r) * S.ldG[sb + kr] + c] = T(v);
     } else if (kc == kr + 1 && c < S.m[sb + kc]) {
-      fac[S.fW[sb + kr] + int64_t(r) * S.ldW[sb + kr] + c] = T(v);
+      // super-diagonal coupling: the transpose of the next slab's sub-diagonal block
+      if (S.fW[sb + kr] >= 0) fac[S.fW[sb + kr] + int64_t(r) * S.ldW[sb + kr] + c] = T(v);
     } else {
       atomicExch(err, 1);
     }

@@ -287,7 +287,9 @@ class Context:
         return n.value
 
     def gdsw_profile_enable(self, on=True):
-        return self._check(self.lib.gdsw_profile_enable(self.h, 1 if on else 0))
+        """on: False/0 = off, True/1 = time every apply, k > 1 = every k-th apply."""
+        v = (1 if on else 0) if isinstance(on, bool) else int(on)
+        return self._check(self.lib.gdsw_profile_enable(self.h, v))
 
     def gdsw_profile_reset(self):
         return self._check(self.lib.gdsw_profile_reset(self.h))
