@@ -49,6 +49,19 @@ def parse():
     return ap.parse_args()
 
 
+def gemv_traffic_ratio():
+    """DRAM bytes / algorithmic bytes of the level-1 sweep GEMV from the committed ncu summary,
+    valid only while the kernel source is the one that was profiled (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_gemv_channel32_dram.json")
+    src = os.path.join(ROOT, "paper_2606_01433_gb300", "csrc", "dense.cu")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return d["dram_over_algorithmic"] if d.get("dense_cu_sha256") == sha else None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -232,6 +245,13 @@ def run_gdsw(args, rank, world, local):
     setup_mixed_s = time.perf_counter() - t0
     n = ctx.n
     lib = gdsw.load()
+    import ctypes
+    fwd_bytes = []
+    while True:
+        d = ctypes.c_double()
+        if lib.gdsw_plan_bytes(ctx.h, 0, 0, len(fwd_bytes), ctypes.byref(d)) != 0:
+            break
+        fwd_bytes.append(d.value)
     b = torch.zeros(n, dtype=torch.float64, device=dev)
     x = torch.zeros_like(b)
 
@@ -341,6 +361,7 @@ def run_gdsw(args, rank, world, local):
 
     peak, peak_kind = measured_peaks()
     ms_step = total_ms / args.steps
+    ratio = gemv_traffic_ratio() if (args.m == 32 and args.mixed == "fp32") else None
     line = {
         "metric": METRIC,
         "value": ms_step,
@@ -375,7 +396,8 @@ def run_gdsw(args, rank, world, local):
         "roofline": {"kernel": "k_gemv (level-1 block-LDU sweeps)", "bound": "hbm", "achieved": gemv_gbs,
                      "peak": peak, "unit": "GB/s", "frac": (gemv_gbs / peak) if gemv_gbs else None,
                      "peak_kind": peak_kind, "avg_launch_ms": gemv_avg_ms, "avg_launch_bytes": gemv_avg_bytes,
-                     "traffic": None},
+                     "traffic": (ratio * gemv_avg_bytes) if ratio else None,
+                     "fwd_launch_bytes": fwd_bytes},
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

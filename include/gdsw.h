@@ -212,6 +212,11 @@ int gdsw_level_entities(gdsw_ctx* ctx, int32_t level, int32_t* n_entities);
 /* Number of CUDA kernels this library has launched in this process (all contexts). */
 int64_t gdsw_kernel_launches(void);
 
+/* Algorithmic bytes of one launch of the level-l local-solve sweeps: direction 0 = forward
+ * launches (k = 0 .. K-1), 1 = backward launches (k = 0 .. K-2), in launch order.  Used to
+ * put the DRAM traffic of a profiled launch beside the bytes the method must move. */
+int gdsw_plan_bytes(const gdsw_ctx* ctx, int32_t level, int32_t direction, int32_t k, double* bytes);
+
 int gdsw_profile_enable(gdsw_ctx* ctx, int32_t on);
 int gdsw_profile_read(gdsw_ctx* ctx, gdsw_profile* prof);
 int gdsw_profile_reset(gdsw_ctx* ctx);

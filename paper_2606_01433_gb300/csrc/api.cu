@@ -1364,6 +1364,14 @@ int gdsw_level_entities(gdsw_ctx* c, int32_t level, int32_t* n_entities) {
 
 int64_t gdsw_kernel_launches(void) { return launch_counter(); }
 
+int gdsw_plan_bytes(const gdsw_ctx* c, int32_t level, int32_t direction, int32_t k, double* bytes) {
+  if (!c || c->host_only || !bytes || level < 0 || level >= int(c->ld.size())) return GDSW_ERR_INVALID_ARG;
+  const std::vector<double>& v = direction == 0 ? c->ld[level].fwd_bytes : c->ld[level].bwd_bytes;
+  if (k < 0 || k >= int(v.size())) return GDSW_ERR_INVALID_ARG;
+  *bytes = v[k];
+  return GDSW_OK;
+}
+
 int gdsw_profile_enable(gdsw_ctx* c, int32_t on) {
   if (!c) return GDSW_ERR_INVALID_ARG;
   // on = 0: off; on = k >= 1: time every k-th preconditioner apply and the work after it

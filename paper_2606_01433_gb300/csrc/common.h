@@ -179,8 +179,8 @@ struct MeshHost {
   std::vector<int32_t> b_ptr, b_col;     // pressure rows x velocity node cols
   std::vector<int32_t> bt2b;             // BT entry -> B entry with the same value
   std::vector<int32_t> a_diag, a_tpos;   // position of block (I,I); position of block (J,I) for (I,J)
-  std::vector<int32_t> ad_ptr, ad_col;   // velocity rows x Dirichlet velocity nodes (node ids)
-  std::vector<int32_t> bd_ptr, bd_col;   // pressure rows x Dirichlet velocity nodes
+  std::vector<int32_t> ad_ptr, ad_col;   // velocity rows x Dirichlet nodes with g != 0 (node ids)
+  std::vector<int32_t> bd_ptr, bd_col;   // pressure rows x Dirichlet nodes with g != 0
   bool shares_element(int64_t a, int64_t b) const;
   void coords(int64_t node, int& i, int& j, int& k) const {
     i = int(node % NX);

@@ -78,7 +78,31 @@ __global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV
     int r = rbeg + q;
     rowp[q] = M + t.mat + int64_t(r < t.rows ? r : 0) * ld;
   }
-  for (int c = lane * V; c < ld; c += 32 * V) {
+  int c = lane * V;
+  for (; c + 32 * V < ld; c += 64 * V) {  // two column chunks per row in flight
+    TV mv0[RPW][V], mv1[RPW][V];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      if (rbeg + q < t.rows) {
+        load16s(rowp[q] + c, mv0[q]);
+        load16s(rowp[q] + c + 32 * V, mv1[q]);
+      }
+    }
+    TV xv0[V], xv1[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      xv0[u] = xs[c + u];
+      xv1[u] = xs[c + 32 * V + u];
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      if (rbeg + q < t.rows) {
+#pragma unroll
+        for (int u = 0; u < V; ++u) acc[q] = fma(mv1[q][u], xv1[u], fma(mv0[q][u], xv0[u], acc[q]));
+      }
+    }
+  }
+  if (c < ld) {
     TV xv[V];
 #pragma unroll
     for (int u = 0; u < V; ++u) xv[u] = xs[c + u];

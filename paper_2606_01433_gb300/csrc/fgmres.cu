@@ -46,14 +46,18 @@ __global__ void __launch_bounds__(RT) k_dots(const double* __restrict__ V, int64
   if (threadIdx.x < DG && t0 + threadIdx.x < nvec) part[int64_t(blockIdx.x) * ldp + t0 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// out[t] (+)= sum_b part[b * ldp + t]
+// out[t] (+)= sum_b part[b * ldp + t]: one warp per t, lane-strided partial sums and a
+// fixed butterfly (deterministic)
 __global__ void k_sum_parts(const double* __restrict__ part, int nb, int nvec, int ldp, double* __restrict__ out,
                             int accumulate) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
   if (t >= nvec) return;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[int64_t(b) * ldp + t];
-  out[t] = accumulate ? out[t] + s : s;
+  for (int b = lane; b < nb; b += 32) s += part[int64_t(b) * ldp + t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[t] = accumulate ? out[t] + s : s;
 }
 
 // w -= sum_t h[t] V[t]
@@ -99,11 +103,12 @@ __global__ void k_norm_parts(const double* __restrict__ w, int64_t n, double* __
 
 // scal[slot] = sqrt(sum of parts)
 __global__ void k_norm_finish(const double* __restrict__ part, int nb, double* __restrict__ scal, int slot) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[b];
-    scal[slot] = sqrt(s);
-  }
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) s += part[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) scal[slot] = sqrt(s);
 }
 
 // v = w / scal[slot] (0 if the norm vanished)
@@ -188,12 +193,12 @@ static void cgs2(gdsw_ctx* c, int j, double* w, cudaStream_t s) {
   for (int pass = 0; pass < 2; ++pass) {
     k_dots<<<gd, RT, 0, s>>>(c->d_V, n, nvec, w, c->d_part, ldp);
     check_launch("k_dots");
-    k_sum_parts<<<(nvec + 127) / 128, 128, 0, s>>>(c->d_part, RB, nvec, ldp, pass == 0 ? hcol : c->d_y, 0);
+    k_sum_parts<<<(nvec + 3) / 4, 128, 0, s>>>(c->d_part, RB, nvec, ldp, pass == 0 ? hcol : c->d_y, 0);
     check_launch("k_sum_parts");
     k_update<<<ub, 256, nvec * sizeof(double), s>>>(c->d_V, n, nvec, pass == 0 ? hcol : c->d_y, w);
     check_launch("k_update");
     if (pass == 1) {
-      k_sum_parts<<<(nvec + 127) / 128, 128, 0, s>>>(c->d_part, RB, nvec, ldp, hcol, 1);
+      k_sum_parts<<<(nvec + 3) / 4, 128, 0, s>>>(c->d_part, RB, nvec, ldp, hcol, 1);
       check_launch("k_sum_parts");
     }
   }

@@ -154,8 +154,10 @@ void build_mesh(MeshHost& M, const gdsw_mesh* m) {
         } else if (which == 1) {
           if (M.pidx[w] >= 0) out.push_back(M.pidx[w]);
         } else {
+          // Dirichlet neighbours with a nonzero datum (the only ones the lifting needs)
           uint8_t t = M.tags[w];
-          if (t == GDSW_TAG_WALL || t == GDSW_TAG_INFLOW) out.push_back(int32_t(w));
+          bool nz = M.g[3 * w] != 0.0 || M.g[3 * w + 1] != 0.0 || M.g[3 * w + 2] != 0.0;
+          if ((t == GDSW_TAG_WALL || t == GDSW_TAG_INFLOW) && nz) out.push_back(int32_t(w));
         }
       });
       std::sort(out.begin(), out.end());

@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
         "gdsw_level_dofs": ([vp, i32, dp, dp], C.c_int),
         "gdsw_level_entities": ([vp, i32, C.POINTER(i32)], C.c_int),
         "gdsw_kernel_launches": ([], i64),
+        "gdsw_plan_bytes": ([vp, i32, i32, i32, C.POINTER(C.c_double)], C.c_int),
         "gdsw_profile_enable": ([vp, i32], C.c_int),
         "gdsw_profile_read": ([vp, C.POINTER(gdsw_profile)], C.c_int),
         "gdsw_profile_reset": ([vp], C.c_int),
