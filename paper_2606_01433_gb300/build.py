@@ -18,7 +18,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libgdsw.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["api.cu", "dense.cu", "operator.cu", "schwarz.cu", "setup.cu", "fgmres.cu", "host_setup.cpp"]
+UNITS = ["api.cu", "dense.cu", "operator.cu", "schwarz.cu", "setup.cu", "fgmres.cu", "host_setup.cpp", "noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "gdsw_solve_host": ([vp, dp, dp, C.POINTER(gdsw_solve_info)], C.c_int),
         "gdsw_reassemble": ([vp, dp], C.c_int),
         "gdsw_apply_local": ([vp, i32, dp, dp], C.c_int),
+        "gdsw_apply_local_noalloc": ([vp, i32, dp, dp], C.c_int),
         "gdsw_restrict": ([vp, i32, dp, dp], C.c_int),
         "gdsw_prolong": ([vp, i32, dp, dp], C.c_int),
         "gdsw_coarse_matrix": ([vp, i32, dp], C.c_int),
@@ -245,6 +246,10 @@ class Context:
 
     def gdsw_apply_local(self, level, r, z):
         return self._check(self.lib.gdsw_apply_local(self.h, level, _ptr(r), _ptr(z)))
+
+    def gdsw_apply_local_noalloc(self, level, r, z):
+        """gdsw_apply_local without any allocation (fixed 4 MiB device scratch; see gdsw.h)."""
+        return self._check(self.lib.gdsw_apply_local_noalloc(self.h, level, _ptr(r), _ptr(z)))
 
     def gdsw_restrict(self, level, r, r0):
         return self._check(self.lib.gdsw_restrict(self.h, level, _ptr(r), _ptr(r0)))

@@ -1,0 +1,63 @@
+"""gdsw_apply_local_noalloc: the local branch of a level computed without allocating memory
+(for callers that cannot call cudaMalloc while they run, e.g. inside a CUDA-graph capture or
+in a process whose device memory is all pre-reserved).  Its result must equal
+gdsw_apply_local's, call after call, since the two run the same kernels in the same order;
+only the scratch differs (a fixed device array instead of the context's workspace).
+
+This file is named so that pytest collects it last; it must pass in a fresh process as well
+as after the other tests.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_01433_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_01433_gb300 import gdsw
+    gdsw.load()
+    return gdsw
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_matches_apply_local(lib, prec):
+    p = I.channel(16, parts=(4, 4, 4), groups=((2, 2, 2),), levels=3)
+    ctx = lib.Context(p, precision=(prec, prec, prec), phi_precision=prec)
+    rng = np.random.default_rng(7)
+    for level in range(2):
+        n = ctx.n if level == 0 else int(ctx.sizes.n_coarse[0])
+        for call in range(2):  # two calls in a row: the shared scratch keeps the previous contents
+            r = torch.from_numpy(rng.standard_normal(n)).cuda()
+            z_ref = torch.zeros_like(r)
+            z_new = torch.full_like(r, float("nan"))
+            ctx.gdsw_apply_local(level, r, z_ref)
+            ctx.gdsw_apply_local_noalloc(level, r, z_new)
+            torch.cuda.synchronize()
+            a, b = z_new.cpu().numpy(), z_ref.cpu().numpy()
+            assert np.all(np.isfinite(a))
+            assert rel(a, b) <= 1e-12, (level, call, rel(a, b))
+    ctx.close()
+
+
+def test_noalloc_rejects_oversized_level(lib):
+    p = I.channel(24)
+    ctx = lib.Context(p, precision=("fp64", "fp64", "fp64"))
+    r = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    z = torch.zeros_like(r)
+    with pytest.raises(lib.GdswError) as e:
+        ctx.gdsw_apply_local_noalloc(0, r, z)
+    assert e.value.code == lib.GDSW_ERR_INVALID_ARG
+    assert "scratch" in str(e.value)
+    ctx.close()
