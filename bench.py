@@ -46,6 +46,10 @@ def parse():
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--prof-stride", type=int, default=8,
                     help="CUDA-event timing of every k-th preconditioner apply inside the timed region")
+    ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals of mixed requests")
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--serve-sizes", type=str, default="8,12,16,20,24,28,32")
+    ap.add_argument("--slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -228,6 +232,72 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving
+def run_serving(n_req, sizes, slots, seed=5, budget_frac=0.8):
+    """Continuous batching of mixed Carreau requests (unit-cube channels m^3, m ~ U{sizes},
+    n ~ U[0.3, 1], nu0/nu_inf log-uniform in [10, 1e4]).  Closed loop first (all submitted at
+    once: throughput), then open loop with Poisson arrivals at 0.8x that throughput
+    (latency = submit -> result in host memory)."""
+    import numpy as np
+    import torch
+    from paper_2606_01433_gb300 import gdsw, inputs as I
+    reqs = I.serving_requests(n_req, seed, sizes)
+    probs = [I.carreau_cube(r["m"], r["n"], r["nu_inf"], r["seed"]) for r in reqs]
+    free, _ = torch.cuda.mem_get_info()
+    srv = gdsw.Server(device=torch.cuda.current_device(), mem_budget_bytes=int(free * budget_frac), max_slots=slots)
+    st, _ = srv.gdsw_server_wait(srv.gdsw_server_submit(probs[0]))  # warm-up
+    t0 = time.perf_counter()
+    tickets = [srv.gdsw_server_submit(p) for p in probs]
+    closed = [srv.gdsw_server_wait(t)[0] for t in tickets]
+    makespan = time.perf_counter() - t0
+    thr = n_req / makespan
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / (0.8 * thr), size=n_req)
+    tickets = []
+    t0 = time.perf_counter()
+    due = 0.0
+    for p, gap in zip(probs, gaps):
+        due += gap
+        delay = due - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.gdsw_server_submit(p))
+    opened = [srv.gdsw_server_wait(t)[0] for t in tickets]
+    wall = time.perf_counter() - t0
+    stats = srv.gdsw_server_stats_read()
+    srv.close()
+    lat = np.array([s.latency_ms for s in opened])
+    ok = sum(1 for s in closed + opened if s.state == gdsw.REQ_DONE and s.relres <= 1e-8)
+    return {"requests": n_req, "sizes": list(sizes), "slots": slots, "closed_loop_solves_per_s": thr,
+            "closed_loop_makespan_s": makespan, "open_loop_rate_per_s": 0.8 * thr,
+            "open_loop_throughput_per_s": n_req / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "setup_ms_p50": float(np.median([s.setup_ms for s in opened])),
+            "solve_ms_p50": float(np.median([s.solve_ms for s in opened])),
+            "queue_ms_p50": float(np.median([s.queue_ms for s in opened])),
+            "iterations_p50": float(np.median([s.iterations for s in opened])),
+            "converged": ok, "of": 2 * n_req, "peak_running": stats.peak_running,
+            "peak_used_gb": stats.peak_used_bytes / 1e9, "budget_gb": stats.budget_bytes / 1e9,
+            "local_precision": "fp32"}
+
+
+def run_serve_mode(args, rank, world, local):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    sizes = tuple(int(s) for s in args.serve_sizes.split(","))
+    res = run_serving(args.requests, sizes, args.slots)
+    if rank == 0:
+        line = {"metric": "served Stokes solves: p50/p99 latency (ms) under Poisson arrivals at 0.8x closed-loop "
+                          "throughput", "value": res["latency_ms"]["p99"], "unit": "ms", "n_gpus": world,
+                "higher_is_better": False, "scaling": "weak", "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "serving_carreau_cubes", "requests": args.requests},
+                "serving": res}
+        print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gdsw(args, rank, world, local):
     import numpy as np
@@ -358,6 +428,11 @@ def run_gdsw(args, rank, world, local):
     d2h = x_h.nbytes
     sizes = ctx.sizes
     ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    serving = None
+    if os.environ.get("GDSW_BENCH_NO_SERVE") != "1":
+        serving = run_serving(24, (8, 12, 16), 4)
 
     peak, peak_kind = measured_peaks()
     ms_step = total_ms / args.steps
@@ -401,6 +476,7 @@ def run_gdsw(args, rank, world, local):
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "serving": serving,
     }
     if rank == 0:
         if world == 1 and os.environ.get("GDSW_BENCH_NO_CPU") != "1":
@@ -417,6 +493,8 @@ def main():
     rank, world, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.serve:
+        run_serve_mode(args, rank, world, local)
     else:
         run_gdsw(args, rank, world, local)
     if world > 1:

@@ -239,6 +239,66 @@ int gdsw_profile_enable(gdsw_ctx* ctx, int32_t on);
 int gdsw_profile_read(gdsw_ctx* ctx, gdsw_profile* prof);
 int gdsw_profile_reset(gdsw_ctx* ctx);
 
+/* ---- serving: continuous batching of independent Stokes solves ------------------------ *
+ * A server owns one GPU, a device-memory budget and a number of slots (worker threads, each
+ * with its own CUDA stream).  Submitted requests are analysed on the host (gdsw_analyze's
+ * symbolic set-up gives the exact sizes and a device-memory estimate), admitted as soon as a
+ * slot is free and the estimate fits in the remaining budget, then set up, solved and
+ * released on their slot's stream, so the work of several requests overlaps on the device
+ * while later requests keep arriving.  Requests that can never fit fail with GDSW_ERR_OOM.
+ * Every result is computed by the same deterministic kernels as gdsw_solve, so a request
+ * gives the same x whether it runs alone or in a mix. */
+typedef struct gdsw_server gdsw_server;
+
+typedef struct {
+  gdsw_mesh mesh;           /* host arrays are copied at submit */
+  gdsw_viscosity visc;
+  gdsw_partition part;
+  gdsw_levels levels;
+  gdsw_options opt;         /* opt.stream is ignored: the slot's stream is used */
+  const double* rhs;        /* host right-hand side of length x_len, or NULL: lifted Dirichlet data */
+  double* x;                /* host result buffer of x_len doubles; must stay valid until completion */
+  int64_t x_len;            /* must equal the problem's n (gdsw_analyze gives it) */
+} gdsw_request;
+
+enum gdsw_request_state {
+  GDSW_REQ_QUEUED = 0, GDSW_REQ_ANALYSING = 1, GDSW_REQ_WAITING = 2, GDSW_REQ_RUNNING = 3,
+  GDSW_REQ_DONE = 4, GDSW_REQ_FAILED = 5
+};
+
+typedef struct {
+  int32_t state;            /* enum gdsw_request_state */
+  int32_t status;           /* gdsw_status of the request once done or failed */
+  int32_t iterations;
+  int32_t slot;
+  int64_t n;
+  int64_t est_bytes;        /* admission estimate */
+  double relres;
+  double queue_ms;          /* submit -> memory reserved */
+  double setup_ms;          /* device set-up */
+  double solve_ms;          /* right-hand side, FGMRES and the copy back */
+  double latency_ms;        /* submit -> result in the caller's buffer */
+} gdsw_request_status;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t budget_bytes, used_bytes, peak_used_bytes;
+  int32_t running, peak_running;
+} gdsw_server_stats;
+
+/* device: CUDA ordinal; mem_budget_bytes: device memory the server may reserve for requests;
+ * max_slots: requests in flight at once (1..64). */
+int gdsw_server_create(int32_t device, int64_t mem_budget_bytes, int32_t max_slots, gdsw_server** out);
+/* Queue a request; *ticket identifies it.  Host inputs are copied before the call returns. */
+int gdsw_server_submit(gdsw_server* srv, const gdsw_request* req, int64_t* ticket);
+/* Non-blocking status of a ticket. */
+int gdsw_server_poll(gdsw_server* srv, int64_t ticket, gdsw_request_status* st);
+/* Block until the ticket is done or failed. */
+int gdsw_server_wait(gdsw_server* srv, int64_t ticket, gdsw_request_status* st);
+int gdsw_server_stats_read(gdsw_server* srv, gdsw_server_stats* st);
+/* Finish every queued request, stop the workers and free the server. */
+int gdsw_server_destroy(gdsw_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,8 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libgdsw.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["api.cu", "dense.cu", "operator.cu", "schwarz.cu", "setup.cu", "fgmres.cu", "host_setup.cpp", "noalloc.cu"]
+UNITS = ["api.cu", "dense.cu", "operator.cu", "schwarz.cu", "setup.cu", "fgmres.cu", "host_setup.cpp", "noalloc.cu",
+         "serve.cpp"]
 
 
 def _nvcc() -> str:

@@ -22,8 +22,8 @@ static double now_ms() {
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-int64_t& launch_counter() {
-  static int64_t n = 0;
+std::atomic<int64_t>& launch_counter() {
+  static std::atomic<int64_t> n{0};
   return n;
 }
 
@@ -863,8 +863,8 @@ static void capture_graph(gdsw_ctx* c) {
 }
 
 // ------------------------------------------------------------------ set-up driver
-static void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, const gdsw_partition* part,
-                       const gdsw_levels* lv, const gdsw_options* opt) {
+void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, const gdsw_partition* part,
+                const gdsw_levels* lv, const gdsw_options* opt) {
   GDSW_CHECK(mesh && visc && part && lv && opt, GDSW_ERR_INVALID_ARG, "null argument");
   GDSW_CHECK(mesh->nx > 0 && mesh->ny > 0 && mesh->nz > 0 && mesh->h > 0, GDSW_ERR_INVALID_ARG, "bad mesh size");
   GDSW_CHECK(mesh->mask && mesh->tags && mesh->g && part->elem_part, GDSW_ERR_INVALID_ARG, "null mesh array");
@@ -882,9 +882,10 @@ static void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity*
   if (c->opt.max_it <= 0) c->opt.max_it = 1000;
   c->L = lv->levels;
   double t0 = now_ms();
-  if (c->host_only) {
+  const int nlev = c->L - 1;
+  if (!c->host_ready) {
+    // ---- host symbolic set-up (shared by gdsw_analyze, gdsw_setup and the server's admission)
     build_mesh(c->mesh, mesh);
-    const int nlev = c->L - 1;
     c->lh.assign(nlev, LevelHost());
     build_level1(c, part, lv->overlap, opt->slab_elems);
     for (int l = 1; l < nlev; ++l) {
@@ -904,9 +905,12 @@ static void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity*
              elem_size(l == 0 ? opt->phi_precision : GDSW_FP64);
     }
     b += 8.0 * (2.0 * c->opt.restart + 2.0) * M.n;
+    // the factorisation works in a temporary copy of the level-1 factors and interiors
+    b += double(c->lh[0].loc.nfac) * (opt->precision[0] == GDSW_FP64 ? 8 : 4);
     c->est_device_bytes = int64_t(b);
-    return;
+    c->host_ready = true;
   }
+  if (c->host_only) return;
   // NULL selects the legacy default stream, so calls order with other default-stream work
   c->stream = static_cast<cudaStream_t>(opt->stream);
   GDSW_CUDA(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
@@ -915,18 +919,8 @@ static void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity*
   cudaStream_t s = c->stream;
   set_gemv_smem_limits();
   set_prolong_smem_limits();
-  // ---- host symbolic set-up
-  build_mesh(c->mesh, mesh);
-  const int nlev = c->L - 1;
-  c->lh.assign(nlev, LevelHost());
   c->ld.assign(nlev, LevelDev());
-  build_level1(c, part, lv->overlap, opt->slab_elems);
-  for (int l = 1; l < nlev; ++l) {
-    GDSW_CHECK(part->groups[l - 1] != nullptr, GDSW_ERR_INVALID_ARG, "null grouping array");
-    build_coarse_level(c, l, part->groups[l - 1], part->group_len[l - 1]);
-  }
   double t1 = now_ms();
-  c->setup_ms[0] = t1 - t0;
   // ---- device mesh and operator
   MeshHost& M = c->mesh;
   c->form = visc->form;
@@ -1060,11 +1054,18 @@ static void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity*
     c->d_coarsest_inv = c->arena.alloc<double>(n0 * ldc);
     GDSW_CUDA(cudaMemsetAsync(c->d_coarsest_inv, 0, n0 * ldc * 8, s));
     GDSW_CUDA(cudaMemcpy2DAsync(c->d_coarsest_inv, ldc * 8, A0, n0 * 8, n0 * 8, n0, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> hA(n0 * n0);
+    GDSW_CUDA(cudaMemcpyAsync(hA.data(), A0, 8 * n0 * n0, cudaMemcpyDeviceToHost, s));
+    GDSW_CUDA(cudaStreamSynchronize(s));
+    double amax = 0.0;
+    for (double v : hA) amax = std::max(amax, std::fabs(v));
     DevArena tmp;
     std::vector<double> mp;
     run_inverse<double>(tmp, {{c->d_coarsest_inv, int(n0), ldc, 0}}, mp, s);
     tmp.free_all();
-    GDSW_CHECK(mp[0] > 0 && std::isfinite(mp[0]), GDSW_ERR_SINGULAR, "coarsest operator is singular");
+    // direct solve of the smallest level: a pivot below 1e-12 of the largest entry means
+    // A_0^(L) is numerically singular (e.g. no Dirichlet data at all)
+    GDSW_CHECK(mp[0] > 1e-12 * amax && std::isfinite(mp[0]), GDSW_ERR_SINGULAR, "coarsest operator is singular");
     c->coarsest_minpiv = mp[0];
     std::vector<GemvTask> tasks;
     std::vector<GemvTile> tiles;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -33,7 +34,7 @@ struct Error {
   } while (0)
 
 // every kernel launch of the library is followed by check_launch, which also counts it
-int64_t& launch_counter();
+std::atomic<int64_t>& launch_counter();
 inline void check_launch(const char* what) {
   ++launch_counter();
   cudaError_t e = cudaGetLastError();
@@ -245,6 +246,7 @@ struct LevelDev {
 struct gdsw_ctx {
   std::string err;
   bool host_only = false;           // created by gdsw_analyze: no device state
+  bool host_ready = false;          // host symbolic structures built
   bool capturing = false;           // inside CUDA-graph capture (no profiling events)
   int prof_stride = 1;              // time every prof_stride-th apply (and the work after it)
   int64_t apply_count = 0;

@@ -46,6 +46,11 @@ void launch_tneg(const MatView& A, const SlabView& S, const int32_t* gamma_col, 
 void launch_yint(const MatView& A, const SlabView& S, const int32_t* ilocal, const int64_t* coff, const int64_t* toff,
                  const int32_t* ldt, const double* X, const double* Tn, double* Y, cudaStream_t s);
 
+// whole set-up: host symbolic phase unless already done, then (unless host_only) the device phase
+void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, const gdsw_partition* part,
+                const gdsw_levels* lv, const gdsw_options* opt);
+void fgmres_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info);
+
 // host-side builders
 void build_mesh(MeshHost& M, const gdsw_mesh* m);
 void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int slab_elems);

@@ -304,3 +304,141 @@ class Context:
         p = gdsw_profile()
         self._check(self.lib.gdsw_profile_read(self.h, C.byref(p)))
         return {KERNEL_GROUPS[i]: dict(calls=p.calls[i], ms=p.ms[i], bytes=p.bytes[i]) for i in range(12)}
+
+
+# ----------------------------------------------------------------------------- serving
+class gdsw_request(C.Structure):
+    _fields_ = [("mesh", gdsw_mesh), ("visc", gdsw_viscosity), ("part", gdsw_partition), ("levels", gdsw_levels),
+                ("opt", gdsw_options), ("rhs", C.c_void_p), ("x", C.c_void_p), ("x_len", C.c_int64)]
+
+
+class gdsw_request_status(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("iterations", C.c_int32), ("slot", C.c_int32),
+                ("n", C.c_int64), ("est_bytes", C.c_int64), ("relres", C.c_double), ("queue_ms", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("latency_ms", C.c_double)]
+
+
+class gdsw_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("budget_bytes", C.c_int64), ("used_bytes", C.c_int64), ("peak_used_bytes", C.c_int64),
+                ("running", C.c_int32), ("peak_running", C.c_int32)]
+
+
+REQ_DONE, REQ_FAILED = 4, 5
+
+
+def count_dofs(prob):
+    """n of the free-dof vector by the convention of gdsw.h: 3 per fluid node that is not a
+    wall/inflow node, plus one per fluid node with all-even indices (Q1 pressure)."""
+    nx, ny, nz = prob.nx, prob.ny, prob.nz
+    m = np.asarray(prob.mask, bool).reshape(nz, ny, nx)
+    act = np.zeros((2 * nz + 1, 2 * ny + 1, 2 * nx + 1), bool)
+    for c in range(3):
+        for b in range(3):
+            for a in range(3):
+                act[c:c + 2 * nz:2, b:b + 2 * ny:2, a:a + 2 * nx:2] |= m
+    act = act.ravel()
+    tags = np.asarray(prob.tags).ravel()
+    vel = act & (tags != 1) & (tags != 2)
+    pr = act.reshape(2 * nz + 1, 2 * ny + 1, 2 * nx + 1)[::2, ::2, ::2]
+    return int(3 * vel.sum() + pr.sum())
+
+
+def _server_sigs(lib):
+    vp = C.c_void_p
+    sig = {
+        "gdsw_server_create": ([C.c_int32, C.c_int64, C.c_int32, C.POINTER(vp)], C.c_int),
+        "gdsw_server_submit": ([vp, C.POINTER(gdsw_request), C.POINTER(C.c_int64)], C.c_int),
+        "gdsw_server_poll": ([vp, C.c_int64, C.POINTER(gdsw_request_status)], C.c_int),
+        "gdsw_server_wait": ([vp, C.c_int64, C.POINTER(gdsw_request_status)], C.c_int),
+        "gdsw_server_stats_read": ([vp, C.POINTER(gdsw_server_stats)], C.c_int),
+        "gdsw_server_destroy": ([vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+
+
+class Server:
+    """Continuous-batching solve server (gdsw_server_*): submit problems, wait for results."""
+
+    def __init__(self, device=0, mem_budget_bytes=64 << 30, max_slots=4):
+        lib = load()
+        _server_sigs(lib)
+        self.lib = lib
+        h = C.c_void_p()
+        rc = lib.gdsw_server_create(device, int(mem_budget_bytes), max_slots, C.byref(h))
+        if rc != GDSW_OK:
+            raise GdswError(rc, "gdsw_server_create failed")
+        self.h = h
+        self.pending = {}
+
+    def gdsw_server_submit(self, prob, levels=None, weighting="pou", precision=("fp32", "fp32", "fp32"),
+                           phi_precision="fp32", tol=1e-8, restart=100, max_it=1000, slab_elems=1, rhs=None):
+        """Queue one problem; returns a ticket.  The result buffer is kept until wait()."""
+        L = prob.levels if levels is None else levels
+        n = count_dofs(prob)
+        keep = [np.ascontiguousarray(prob.mask, np.uint8), np.ascontiguousarray(prob.tags, np.uint8),
+                np.ascontiguousarray(prob.g, np.float64), np.ascontiguousarray(prob.part, np.int32)]
+        r = gdsw_request()
+        r.mesh = gdsw_mesh(prob.nx, prob.ny, prob.nz, prob.h, (C.c_double * 3)(*prob.origin),
+                           keep[0].ctypes.data, keep[1].ctypes.data, keep[2].ctypes.data)
+        uk = None
+        if prob.uk is not None:
+            uk = np.ascontiguousarray(prob.uk, np.float64)
+            keep.append(uk)
+        r.visc = gdsw_viscosity(FORM[prob.form], prob.nu0, prob.nu_inf, prob.lam, prob.n_carreau,
+                                uk.ctypes.data if uk is not None else None)
+        r.part.elem_part = keep[3].ctypes.data
+        r.part.n_groups = L - 2
+        for l in range(L - 2):
+            gr = np.ascontiguousarray(prob.groups[l], np.int32)
+            keep.append(gr)
+            r.part.groups[l] = gr.ctypes.data
+            r.part.group_len[l] = gr.size
+        r.levels = gdsw_levels(L, 1)
+        prec = [PREC[q] for q in precision]
+        r.opt = gdsw_options(WEIGHT_POU if weighting == "pou" else WEIGHT_PLAIN, (C.c_int32 * 3)(*prec),
+                             PREC[phi_precision], restart, max_it, tol, slab_elems, 0, None)
+        x = np.zeros(n)
+        if rhs is not None:
+            rb = np.ascontiguousarray(rhs, np.float64)
+            keep.append(rb)
+            r.rhs = rb.ctypes.data
+        r.x = x.ctypes.data
+        r.x_len = n
+        t = C.c_int64()
+        rc = self.lib.gdsw_server_submit(self.h, C.byref(r), C.byref(t))
+        if rc != GDSW_OK:
+            raise GdswError(rc, "gdsw_server_submit failed")
+        self.pending[t.value] = x
+        return t.value
+
+    def gdsw_server_wait(self, ticket):
+        st = gdsw_request_status()
+        rc = self.lib.gdsw_server_wait(self.h, ticket, C.byref(st))
+        if rc != GDSW_OK:
+            raise GdswError(rc, "gdsw_server_wait failed")
+        return st, self.pending.pop(ticket)
+
+    def gdsw_server_poll(self, ticket):
+        st = gdsw_request_status()
+        self.lib.gdsw_server_poll(self.h, ticket, C.byref(st))
+        return st
+
+    def gdsw_server_stats_read(self):
+        st = gdsw_server_stats()
+        self.lib.gdsw_server_stats_read(self.h, C.byref(st))
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gdsw_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
