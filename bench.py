@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "channel32_4cyl_carreau_n0.5_q2q1_4x4x4_grouped2x2x2_3level"
+DIE_WORKLOAD = "die64x64x128_sdf_carreau_n0.4_q2q1_rcb512_64_8_4level"
 METRIC = "FGMRES solve time and apply GB/s at rel res 1e-8, mixed vs FP64; p99 latency"
 
 
@@ -42,6 +43,8 @@ def parse():
     ap.add_argument("--mixed", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison context")
     ap.add_argument("--m", type=int, default=32, help="elements per edge of the channel")
+    ap.add_argument("--workload", choices=["channel", "die"], default="channel",
+                    help="channel: 32^3 Carreau channel (3 levels); die: 64x64x128 die-like channel (4 levels)")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--prof-stride", type=int, default=8,
@@ -308,8 +311,14 @@ def run_gdsw(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p = I.channel(args.m)
-    mixed = (args.mixed, args.mixed, args.mixed)
+    if args.workload == "die":
+        p = I.die()
+        mixed = (args.mixed, "fp32", "fp32")
+        wname = DIE_WORKLOAD
+    else:
+        p = I.channel(args.m)
+        mixed = (args.mixed, args.mixed, args.mixed)
+        wname = WORKLOAD if args.m == 32 else WORKLOAD.replace("channel32", "channel%d" % args.m)
     t0 = time.perf_counter()
     ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8, restart=100, max_it=1000)
     setup_mixed_s = time.perf_counter() - t0
@@ -436,7 +445,7 @@ def run_gdsw(args, rank, world, local):
 
     peak, peak_kind = measured_peaks()
     ms_step = total_ms / args.steps
-    ratio = gemv_traffic_ratio() if (args.m == 32 and args.mixed == "fp32") else None
+    ratio = gemv_traffic_ratio() if (args.workload == "channel" and args.m == 32 and args.mixed == "fp32") else None
     line = {
         "metric": METRIC,
         "value": ms_step,
@@ -450,7 +459,9 @@ def run_gdsw(args, rank, world, local):
         "vs_baseline": None,
         "dtype": "f32" if args.mixed == "fp32" else "bf16",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_dofs": n, "levels": 3, "subdomains": [64, 8], "coarse": [1060, 64],
+        "config": {"workload": wname, "n_dofs": n, "levels": int(sizes.levels),
+                   "subdomains": [int(v) for v in list(sizes.n_parts)[:sizes.levels - 1]],
+                   "coarse": [int(v) for v in list(sizes.n_coarse)[:sizes.levels - 1]],
                    "local_precision": args.mixed, "krylov_precision": "f64", "tol": 1e-8, "restart": 100,
                    "l2": "inputs larger than L2 (no flush)", "replicas": world},
         "iterations": iters[-1],
@@ -467,6 +478,8 @@ def run_gdsw(args, rank, world, local):
         "fp64": fp64,
         "speedup_vs_fp64": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "setup_s": setup_mixed_s,
+        "setup_breakdown_ms": dict(zip(["host_symbolic", "viscosity_assembly", "level1_factors", "phi_and_A0",
+                                        "coarse_levels", "total"], [float(v) for v in sizes.setup_ms])),
         "factor_gb": sizes.factor_entries[0] * (4 if args.mixed == "fp32" else 2) / 1e9,
         "roofline": {"kernel": "k_gemv (level-1 block-LDU sweeps)", "bound": "hbm", "achieved": gemv_gbs,
                      "peak": peak, "unit": "GB/s", "frac": (gemv_gbs / peak) if gemv_gbs else None,

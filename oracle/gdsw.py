@@ -117,6 +117,36 @@ def _coarse_columns(entity_modes):
     return col, c, nodes
 
 
+def overlapping_dofs(sys_, prob, overlap=1):
+    """Free dofs of every overlapping subdomain Omega_i' (Section 2.1; overlap reading in the
+    module header): index sets only, no factorisation."""
+    mesh = sys_["mesh"]
+    ne = mesh.elems.size
+    sub = prob.part[mesh.elems].astype(np.int64)
+    N = int(sub.max()) + 1
+    nn = prob.n_nodes
+    NE = sp.csr_matrix((np.ones(27 * ne), (mesh.enodes.ravel(), np.repeat(np.arange(ne), 27))), shape=(nn, ne))
+    NE.data[:] = 1.0
+    ES = sp.csr_matrix((np.ones(ne), (np.arange(ne), sub)), shape=(ne, N))
+    deg = np.asarray(NE.sum(axis=1)).ravel()
+    EO = ES.copy()
+    for _ in range(overlap):
+        EO = (NE.T @ (NE @ EO)).tocsr()
+        EO.data[:] = 1.0
+    cntc = (NE @ EO).tocsc()
+    vnode_dof = np.where(mesh.vindex >= 0, 3 * mesh.vindex, -1)
+    pnode_dof = np.where(mesh.pindex >= 0, mesh.nu + mesh.pindex, -1)
+    out = []
+    for i in range(N):
+        col = cntc[:, i]
+        nodes = col.indices[col.data == deg[col.indices]]
+        v = vnode_dof[nodes]
+        v = v[v >= 0]
+        pp = pnode_dof[nodes]
+        out.append(np.sort(np.concatenate([(v[:, None] + np.arange(3)[None, :]).ravel(), pp[pp >= 0]])))
+    return out
+
+
 def build_level1(sys_, prob, overlap=1, dense_local=False):
     """First level from the mesh and the element partition (Section 2.1)."""
     mesh = sys_["mesh"]

@@ -43,6 +43,7 @@ def test_symbolic_setup_matches_oracle(lib, name, make):
     assert ctx.sizes.n == S["A"].shape[0]
     assert ctx.sizes.n_u == mesh.nu and ctx.sizes.n_p == mesh.np_
     P = og.GDSW(S, p)
+    assert all(np.array_equal(a, b) for a, b in zip(og.overlapping_dofs(S, p), P.levels[0].dofs))
     for l, lev in enumerate(P.levels):
         mine = ctx.gdsw_level_dofs(l)
         assert len(mine) == len(lev.dofs)
