@@ -219,6 +219,11 @@ static double plan_bytes(const std::vector<GemvTask>& tasks, int t0, int t1, siz
   double b = 0;
   for (int t = t0; t < t1; ++t) {
     const GemvTask& q = tasks[t];
+    if (q.kind == 1) {  // the symmetric block's distinct entries, input once, partials written
+      const double s = q.rows, T = double(q.cols) / q.ld;
+      b += s * (s + 1) / 2 * esz + s * vsz + double(q.ld) * q.ld * T * vsz;
+      continue;
+    }
     double in = transposed ? q.rows : q.cols, out = transposed ? q.cols : q.rows;
     b += double(q.rows) * q.cols * esz + in * vsz + out * vsz * (q.base >= 0 ? 2 : 1);
   }
@@ -228,9 +233,15 @@ static double plan_bytes(const std::vector<GemvTask>& tasks, int t0, int t1, siz
 static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
   std::vector<GemvTask> tasks;
   std::vector<GemvTile> tiles;
+  std::vector<GemvTask> rtasks;  // reductions of the symmetric partial sums
+  std::vector<GemvTile> rtiles;
   const size_t esz = elem_size(L.prec), vsz = L.prec == GDSW_FP64 ? 8 : 4;
   const int rpt = L.fwd.rows_per_tile;
   const int64_t nv = S.nvec;
+  const int TT = L.sym_T;
+  std::vector<int> sb(S.nsub + 1, 0);  // first flattened slab index of each part
+  for (int i = 0; i < S.nsub; ++i) sb[i + 1] = sb[i] + S.K[i];
+  int64_t part_off = 2 * nv;          // partial sums live behind the two local vectors
   L.fwd.launch_task_off = {0};
   L.fwd.launch_tile_off = {0};
   L.fwd_ld.clear();
@@ -238,13 +249,29 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
     int mld = 8;
     for (int i = 0; i < S.nsub; ++i) {
       if (k >= S.K[i]) continue;
+      const int q = sb[i] + k;
       int64_t y = S.voff[i] + S.soff[i][k];
-      GemvTask t{S.fS[i][k], y, nv + y, -1, S.s[i][k], S.s[i][k], S.ldS[i][k], 1.0f};
-      add_task(tasks, tiles, t, rpt);
-      mld = std::max(mld, S.ldS[i][k]);
+      const int sk = S.s[i][k];
+      if (L.psym[q]) {
+        const int nt = (sk + TT - 1) / TT;
+        GemvTask t{L.pS[q], y, nv + y, -1, sk, nt * TT, nt, 1.0f, 1, 0, part_off};
+        int id = int(tasks.size());
+        tasks.push_back(t);
+        for (int I = 0; I < nt; ++I)
+          for (int J = I; J < nt; ++J) tiles.push_back({id, (I << 16) | J});
+        int rid = int(rtasks.size());
+        rtasks.push_back(t);
+        for (int r0 = 0; r0 < sk; r0 += 256) rtiles.push_back({rid, r0});
+        part_off += int64_t(nt) * nt * TT;
+        mld = std::max(mld, 11 * TT);
+      } else {
+        GemvTask t{L.pS[q], y, nv + y, -1, sk, sk, S.ldS[i][k], 1.0f};
+        add_task(tasks, tiles, t, rpt);
+        mld = std::max(mld, S.ldS[i][k]);
+      }
       if (k + 1 < S.K[i] && S.m[i][k + 1] > 0) {
         int64_t y1 = S.voff[i] + S.soff[i][k + 1];
-        GemvTask g{S.fG[i][k + 1], y, y1, y1, S.m[i][k + 1], S.s[i][k], S.ldG[i][k + 1], -1.0f};
+        GemvTask g{L.pG[q + 1], y, y1, y1, S.m[i][k + 1], sk, S.ldG[i][k + 1], -1.0f};
         add_task(tasks, tiles, g, rpt);
         mld = std::max(mld, S.ldG[i][k + 1]);
       }
@@ -253,6 +280,12 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
     L.fwd.launch_tile_off.push_back(int(tiles.size()));
     L.fwd_ld.push_back(mld);
   }
+  L.npart = part_off - 2 * nv;
+  L.red.launch_task_off = {0, int(rtasks.size())};
+  L.red.launch_tile_off = {0, int(rtiles.size())};
+  L.red_bytes = 0;
+  for (const GemvTask& t : rtasks) L.red_bytes += (double(t.ld) * t.ld * TT + t.rows) * vsz;
+  finish_plan(c->arena, L.red, rtasks, rtiles, c->stream);
   // backward: x_k = w_k - G_{k+1}^T x_{k+1}[0:m_{k+1}], transposed GEMV over 256-column tiles
   L.bwd.transposed = true;
   L.bwd.launch_task_off = {int(tasks.size())};
@@ -265,7 +298,7 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
       if (k < 0 || S.m[i][k + 1] == 0) continue;
       int64_t y = nv + S.voff[i] + S.soff[i][k];
       int64_t x = nv + S.voff[i] + S.soff[i][k + 1];
-      GemvTask t{S.fG[i][k + 1], x, y, y, S.m[i][k + 1], S.s[i][k], S.ldG[i][k + 1], -1.0f};
+      GemvTask t{L.pG[sb[i] + k + 1], x, y, y, S.m[i][k + 1], S.s[i][k], S.ldG[i][k + 1], -1.0f};
       int id = int(tasks.size());
       tasks.push_back(t);
       for (int c0 = 0; c0 < t.cols; c0 += 256) tiles.push_back({id, c0});
@@ -409,6 +442,71 @@ static void run_segments(gdsw_ctx* c, SegList& L, const double* src, double* dst
   segsum(k, p, q, int64_t(L.key.size()), src, dst, c->stream);
 }
 
+// ------------------------------------------------------------------ factor storage
+// Final storage of a level's factors in the apply precision.  FP32/BF16 diagonal inverses
+// S_k^{-1} of at least 4 tiles per side are kept as their upper-triangle T x T tiles (the
+// block is symmetric up to rounding: the operator is, and the inverse of a symmetric matrix
+// is), the others densely; the G_k blocks follow each slab's S_k^{-1}.
+template <typename T>
+static void store_factors(gdsw_ctx* c, const SlabSet& S, const T* fac, LevelDev& L, int prec, DevArena& tmp) {
+  cudaStream_t s = c->stream;
+  const int TT = sym_tile_size(prec);
+  L.prec = prec;
+  L.nvec = S.nvec;
+  L.sym_T = TT;
+  L.pS.clear();
+  L.pG.clear();
+  L.psym.clear();
+  std::vector<PackTile> tiles;
+  int64_t off = 0;
+  for (int i = 0; i < S.nsub; ++i)
+    for (int k = 0; k < S.K[i]; ++k) {
+      const int sk = S.s[i][k];
+      // FP64 stays dense: on GB300 the FP64 sweep is bound by FP64 FMAs, which packing
+      // does not reduce (each stored entry then feeds two products)
+      const bool sym = prec != GDSW_FP64 && sk >= 4 * TT;
+      L.psym.push_back(sym);
+      L.pS.push_back(off);
+      if (sym) {
+        const int nt = (sk + TT - 1) / TT;
+        for (int I = 0; I < nt; ++I)
+          for (int J = I; J < nt; ++J) {
+            tiles.push_back({S.fS[i][k] + int64_t(I) * TT * S.ldS[i][k] + int64_t(J) * TT, off, S.ldS[i][k],
+                             std::min(TT, sk - I * TT), std::min(TT, sk - J * TT), 0});
+            off += int64_t(TT) * TT;
+          }
+      } else {
+        off += int64_t(sk) * S.ldS[i][k];
+      }
+      L.pG.push_back(off);
+      if (k > 0) off += int64_t(S.m[i][k]) * S.ldG[i][k];
+    }
+  L.nfac = off;
+  T* packed = tmp.alloc<T>(std::max<int64_t>(off, 1));
+  GDSW_CUDA(cudaMemsetAsync(packed, 0, sizeof(T) * std::max<int64_t>(off, 1), s));
+  pack_tiles<T>(tmp, fac, packed, tiles, TT, s);
+  size_t q = 0;
+  for (int i = 0; i < S.nsub; ++i)
+    for (int k = 0; k < S.K[i]; ++k, ++q) {
+      if (!L.psym[q])
+        GDSW_CUDA(cudaMemcpyAsync(packed + L.pS[q], fac + S.fS[i][k], sizeof(T) * S.s[i][k] * S.ldS[i][k],
+                                  cudaMemcpyDeviceToDevice, s));
+      if (k > 0)
+        GDSW_CUDA(cudaMemcpyAsync(packed + L.pG[q], fac + S.fG[i][k], sizeof(T) * S.m[i][k] * S.ldG[i][k],
+                                  cudaMemcpyDeviceToDevice, s));
+    }
+  const int cprec = sizeof(T) == 8 ? GDSW_FP64 : GDSW_FP32;
+  if (prec == GDSW_BF16) {
+    L.fac = c->arena.alloc<__nv_bfloat16>(std::max<int64_t>(off, 1));
+    convert(packed, cprec, L.fac, GDSW_BF16, off, s);
+  } else {
+    L.fac = c->arena.alloc<T>(std::max<int64_t>(off, 1));
+    GDSW_CUDA(cudaMemcpyAsync(L.fac, packed, sizeof(T) * off, cudaMemcpyDeviceToDevice, s));
+  }
+  GDSW_CUDA(cudaStreamSynchronize(s));
+  tmp.release(packed);
+}
+
 // ------------------------------------------------------------------ level 1 numeric set-up
 template <typename T>
 static void level1_locals(gdsw_ctx* c, double& minpiv) {
@@ -438,19 +536,7 @@ static void level1_locals(gdsw_ctx* c, double& minpiv) {
   GDSW_CHECK(herr == 0, GDSW_ERR_INVALID_ARG, "slab ordering leaves a coupling outside the block tridiagonal");
   tmp.release(map);
   factor_slabs<T>(S, fac, minpiv, s);
-  // storage precision
-  int prec = c->opt.precision[0];
-  L.prec = prec;
-  L.nfac = S.nfac;
-  L.nvec = S.nvec;
-  if (prec == GDSW_BF16) {
-    L.fac = c->arena.alloc<__nv_bfloat16>(S.nfac);
-    convert(fac, sizeof(T) == 8 ? GDSW_FP64 : GDSW_FP32, L.fac, GDSW_BF16, S.nfac, s);
-  } else {
-    L.fac = c->arena.alloc<T>(S.nfac);
-    GDSW_CUDA(cudaMemcpyAsync(L.fac, fac, S.nfac * sizeof(T), cudaMemcpyDeviceToDevice, s));
-  }
-  GDSW_CUDA(cudaStreamSynchronize(s));
+  store_factors<T>(c, S, fac, L, c->opt.precision[0], tmp);
   tmp.free_all();
 }
 
@@ -625,18 +711,7 @@ static void coarse_locals(gdsw_ctx* c, int l, double& minpiv) {
   run_inverse<T>(tmp, inv, mp, s);
   minpiv = 1e300;
   for (double v : mp) minpiv = std::min(minpiv, v);
-  int prec = c->opt.precision[l];
-  L.prec = prec;
-  L.nfac = S.nfac;
-  L.nvec = S.nvec;
-  if (prec == GDSW_BF16) {
-    L.fac = c->arena.alloc<__nv_bfloat16>(S.nfac);
-    convert(fac, sizeof(T) == 8 ? GDSW_FP64 : GDSW_FP32, L.fac, GDSW_BF16, S.nfac, s);
-  } else {
-    L.fac = c->arena.alloc<T>(S.nfac);
-    GDSW_CUDA(cudaMemcpyAsync(L.fac, fac, S.nfac * sizeof(T), cudaMemcpyDeviceToDevice, s));
-  }
-  GDSW_CUDA(cudaStreamSynchronize(s));
+  store_factors<T>(c, S, fac, L, c->opt.precision[l], tmp);
   tmp.free_all();
 }
 
@@ -745,6 +820,14 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
     }
   };
   for (int k = 0; k < L.fwd.nlaunch(); ++k) sweep(L.fwd, k, L.fwd_ld[k], L.fwd_bytes[k]);
+  if (L.red.launch_tile_off.size() == 2 && L.red.launch_tile_off[1] > 0) {
+    // w_k = S_k^{-1} y_k of the packed symmetric blocks: sum of the partial products
+    ProfScope ps(c, group, L.red_bytes, s);
+    if (L.prec == GDSW_FP64)
+      launch_sym_reduce<double>(static_cast<const double*>(L.vec), static_cast<double*>(L.vec), L.red, L.sym_T, s);
+    else
+      launch_sym_reduce<float>(static_cast<const float*>(L.vec), static_cast<float*>(L.vec), L.red, L.sym_T, s);
+  }
   for (int k = 0; k < L.bwd.nlaunch(); ++k) sweep(L.bwd, k, L.bwd_ld[k], L.bwd_bytes[k]);
   {
     ProfScope ps(c, GDSW_K_SCATTER, double(nv) * (4 + 8 + (L.prec == GDSW_FP64 ? 8 : 4)) + 8.0 * L.n, s);
@@ -766,6 +849,7 @@ static double apply_bytes(const gdsw_ctx* c) {
     b += double(L.nvec) * (4 + 8 + vs) * 2 + 8.0 * L.n;                // gather + scatter
     for (double x : L.fwd_bytes) b += x;
     for (double x : L.bwd_bytes) b += x;
+    b += L.red_bytes;
     if (L.n0) b += 2 * (L.phi_bytes + 16.0 * L.nidofs + 16.0 * L.ngamma);  // Phi^T and Phi
   }
   b += 8.0 * double(c->n_coarsest) * c->ld_coarsest;
@@ -977,13 +1061,15 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
     L.minpiv = minpiv;
     const LevelHost& H = c->lh[0];
     L.gdof = c->arena.upload(H.loc.gdof, s);
-    L.vec = c->arena.alloc<char>(size_t(2 * std::max<int64_t>(H.loc.nvec, 1)) * (L.prec == GDSW_FP64 ? 8 : 4));
-    GDSW_CUDA(cudaMemsetAsync(L.vec, 0, size_t(2 * std::max<int64_t>(H.loc.nvec, 1)) * (L.prec == GDSW_FP64 ? 8 : 4), s));
     L.sc_ptr = c->arena.upload(H.sc_ptr, s);
     L.sc_pos = c->arena.upload(H.sc_pos, s);
     L.sc_w = c->arena.upload(H.sc_w, s);
     build_local_plan(c, H.loc, L);
-    L.local_bytes = double(H.loc.nfac) * elem_size(L.prec) + 2.0 * H.loc.nvec * (L.prec == GDSW_FP64 ? 8 : 4);
+    // local vectors (y, w) and the symmetric partial sums behind them
+    size_t vb = size_t(std::max<int64_t>(2 * H.loc.nvec + L.npart, 1)) * (L.prec == GDSW_FP64 ? 8 : 4);
+    L.vec = c->arena.alloc<char>(vb);
+    GDSW_CUDA(cudaMemsetAsync(L.vec, 0, vb, s));
+    L.local_bytes = double(L.nfac) * elem_size(L.prec) + 2.0 * H.loc.nvec * (L.prec == GDSW_FP64 ? 8 : 4);
   }
   double t3 = now_ms();
   c->setup_ms[2] = t3 - t2;
@@ -1023,14 +1109,14 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
     GDSW_CHECK(minpiv > 0 && std::isfinite(minpiv), GDSW_ERR_SINGULAR, "coarse local factorisation: zero pivot");
     L.minpiv = minpiv;
     L.gdof = c->arena.upload(H.loc.gdof, s);
-    size_t vb = size_t(2 * std::max<int64_t>(H.loc.nvec, 1)) * (L.prec == GDSW_FP64 ? 8 : 4);
-    L.vec = c->arena.alloc<char>(vb);
-    GDSW_CUDA(cudaMemsetAsync(L.vec, 0, vb, s));
     L.sc_ptr = c->arena.upload(H.sc_ptr, s);
     L.sc_pos = c->arena.upload(H.sc_pos, s);
     L.sc_w = c->arena.upload(H.sc_w, s);
     build_local_plan(c, H.loc, L);
-    L.local_bytes = double(H.loc.nfac) * elem_size(L.prec) + 2.0 * H.loc.nvec * (L.prec == GDSW_FP64 ? 8 : 4);
+    size_t vb = size_t(std::max<int64_t>(2 * H.loc.nvec + L.npart, 1)) * (L.prec == GDSW_FP64 ? 8 : 4);
+    L.vec = c->arena.alloc<char>(vb);
+    GDSW_CUDA(cudaMemsetAsync(L.vec, 0, vb, s));
+    L.local_bytes = double(L.nfac) * elem_size(L.prec) + 2.0 * H.loc.nvec * (L.prec == GDSW_FP64 ? 8 : 4);
     upload_coarse_space(c, l, GDSW_FP64);
     int64_t m0 = H.cs.n0;
     double* A0n = nullptr;

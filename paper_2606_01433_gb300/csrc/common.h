@@ -86,8 +86,11 @@ struct GemvTask {
   int64_t x;        // element offset of x in the vector buffer
   int64_t y;        // element offset of y
   int64_t base;     // element offset of base (or -1: zero)
-  int32_t rows, cols, ld;
+  int32_t rows, cols, ld;  // kind 1: rows = cols = block size, ld = number of tiles per side
   float alpha;
+  int32_t kind;     // 0: dense row-major rows; 1: symmetric block stored as packed upper tiles
+  int32_t pad_;
+  int64_t part;     // kind 1: element offset of the partial sums (nt x nt x T) in the vector buffer
 };
 // A CTA's share of a GEMV launch: rows [row0, row0 + nrows) of task `task`.
 struct GemvTile {
@@ -235,6 +238,13 @@ struct LevelDev {
   // dense coarse operator of THIS level (levels >= 2), FP64 row-major
   double* A = nullptr;
   std::vector<double> fwd_bytes, bwd_bytes;  // algorithmic bytes of each GEMV launch
+  // storage layout of the factors: per (part, slab) flattened in part-major order
+  std::vector<int64_t> pS, pG;  // offsets of S_k^{-1} (packed tiles or dense) and of G_k
+  std::vector<uint8_t> psym;    // S_k^{-1} stored as packed symmetric tiles
+  int sym_T = 128;
+  int64_t npart = 0;            // partial-sum entries behind the 2 nvec local vectors
+  GemvPlan red;                 // reduction of the symmetric partial sums (one launch)
+  double red_bytes = 0;
   double minpiv = 0;            // smallest pivot magnitude met by the local factorisation
   double local_bytes = 0;       // algorithmic bytes of one local-solve sweep pair
   double phi_bytes = 0;         // bytes of the stored Phi_I^T blocks

@@ -56,6 +56,68 @@ __device__ __forceinline__ void load16s(const __nv_bfloat16* p, float* v) {
 // One CTA = 8 warps = ROWS rows of one task; each warp owns ROWS/8 rows and streams them
 // with 16-byte loads (four rows in flight per warp).  The task's input vector is staged in
 // shared memory once per CTA.  y[r] = base[r] + alpha * sum_c M[r][c] x[c].
+// Symmetric block stored as its upper-triangle tiles (T x T, T = 32 lanes x one 16-byte load,
+// tiles (I, J >= I) in row-major order, zero padded): one CTA reads tile (I, J) once and
+// produces both S_IJ x_J (rows of block I) and, off the diagonal, S_IJ^T x_I (rows of block
+// J) as partial sums; k_sym_reduce adds the partials of each row in a fixed order.
+template <typename TM, typename TV>
+__device__ __forceinline__ void sym_tile(const TM* __restrict__ M, const TV* xbase, TV* part, const GemvTask& t,
+                                         int I, int J, TV* smem) {
+  constexpr int V = Vec16<TM>::N, T = 32 * V, RW = T / 8;
+  TV* xi = smem;
+  TV* xj = smem + T;
+  TV* prow = smem + 2 * T;
+  TV* pcol = smem + 3 * T;  // 8 x T
+  const int s = t.rows, nt = t.ld;
+  for (int e = threadIdx.x; e < T; e += blockDim.x) {
+    xi[e] = I * T + e < s ? xbase[t.x + I * T + e] : TV(0);
+    xj[e] = J * T + e < s ? xbase[t.x + J * T + e] : TV(0);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tidx = int64_t(I) * nt - int64_t(I) * (I - 1) / 2 + (J - I);
+  const TM* tp = M + t.mat + tidx * T * T + int64_t(warp * RW) * T + lane * V;
+  TV colacc[V], rowacc[RW];
+#pragma unroll
+  for (int u = 0; u < V; ++u) colacc[u] = TV(0);
+#pragma unroll
+  for (int rr = 0; rr < RW; rr += 4) {
+    TV v[4][V];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) load16s(tp + int64_t(rr + q) * T, v[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const TV xr = xi[warp * RW + rr + q];
+      TV d = TV(0);
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        d = fma(v[q][u], xj[lane * V + u], d);
+        colacc[u] = fma(v[q][u], xr, colacc[u]);
+      }
+      rowacc[rr + q] = d;
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < RW; ++rr) {
+    TV d = rowacc[rr];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) prow[warp * RW + rr] = d;
+  }
+#pragma unroll
+  for (int u = 0; u < V; ++u) pcol[warp * T + lane * V + u] = colacc[u];
+  __syncthreads();
+  for (int e = threadIdx.x; e < T; e += blockDim.x) {
+    part[t.part + (int64_t(I) * nt + J) * T + e] = prow[e];
+    if (I != J) {
+      TV cs = pcol[e];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) cs += pcol[w * T + e];
+      part[t.part + (int64_t(J) * nt + I) * T + e] = cs;
+    }
+  }
+}
+
 template <typename TM, typename TV, int RPW>
 __global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV* xbase, TV* ybase,
                                               const TV* bbase, const GemvTask* __restrict__ tasks,
@@ -64,6 +126,10 @@ __global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV
   TV* xs = reinterpret_cast<TV*>(smem_raw);
   const GemvTile tl = tiles[blockIdx.x];
   const GemvTask t = tasks[tl.task];
+  if (t.kind == 1) {  // packed symmetric tile; partial sums go to ybase + t.part
+    sym_tile<TM, TV>(M, xbase, ybase, t, tl.row0 >> 16, tl.row0 & 0xffff, xs);
+    return;
+  }
   const int ld = t.ld;
   for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = c < t.cols ? xbase[t.x + c] : TV(0);
   __syncthreads();
@@ -215,6 +281,56 @@ void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P
     check_launch("k_gemv");
   }
 }
+
+// y[r] = alpha * sum over the nt source blocks of the partials of row r (fixed order);
+// one CTA per 256 rows of one symmetric task.
+template <typename TV>
+__global__ void k_sym_reduce(const TV* __restrict__ vec, TV* ybase, const GemvTask* __restrict__ tasks,
+                             const GemvTile* __restrict__ tiles, int T) {
+  const GemvTile tl = tiles[blockIdx.x];
+  const GemvTask t = tasks[tl.task];
+  const int r = tl.row0 + threadIdx.x;
+  if (r >= t.rows) return;
+  const int R = r / T, e = r - R * T;
+  const TV* p = vec + t.part + int64_t(R) * t.ld * T + e;
+  TV s = TV(0);
+  for (int S = 0; S < t.ld; ++S) s += p[int64_t(S) * T];
+  ybase[t.y + r] = TV(t.alpha) * s;
+}
+
+template <typename TV>
+void launch_sym_reduce(const TV* vec, TV* y, const GemvPlan& P, int T, cudaStream_t s) {
+  int t0 = P.launch_tile_off[0], t1 = P.launch_tile_off[1];
+  if (t1 <= t0) return;
+  k_sym_reduce<TV><<<t1 - t0, 256, 0, s>>>(vec, y, P.d_tasks, P.d_tiles + t0, T);
+  check_launch("k_sym_reduce");
+}
+template void launch_sym_reduce<double>(const double*, double*, const GemvPlan&, int, cudaStream_t);
+template void launch_sym_reduce<float>(const float*, float*, const GemvPlan&, int, cudaStream_t);
+
+// copy of T x T tiles out of full row-major blocks, zero padded (packing of the upper triangle)
+template <typename T>
+__global__ void k_pack_tiles(const T* __restrict__ src, T* __restrict__ dst, const PackTile* __restrict__ tiles,
+                             int TT) {
+  const PackTile p = tiles[blockIdx.x];
+  for (int e = threadIdx.x; e < TT * TT; e += blockDim.x) {
+    int r = e / TT, c = e - r * TT;
+    dst[p.dst + e] = (r < p.rows && c < p.cols) ? src[p.src + int64_t(r) * p.ld + c] : T(0);
+  }
+}
+
+template <typename T>
+void pack_tiles(DevArena& tmp, const T* src, T* dst, const std::vector<PackTile>& tiles, int TT, cudaStream_t s) {
+  if (tiles.empty()) return;
+  PackTile* d = tmp.upload(tiles, s);
+  for (size_t off = 0; off < tiles.size(); off += (size_t(1) << 30)) {
+    int nb = int(std::min<size_t>(tiles.size() - off, size_t(1) << 30));
+    k_pack_tiles<T><<<nb, 256, 0, s>>>(src, dst, d + off, TT);
+    check_launch("k_pack_tiles");
+  }
+}
+template void pack_tiles<double>(DevArena&, const double*, double*, const std::vector<PackTile>&, int, cudaStream_t);
+template void pack_tiles<float>(DevArena&, const float*, float*, const std::vector<PackTile>&, int, cudaStream_t);
 
 template void launch_gemv<double, double>(const double*, const double*, double*, const double*, const GemvPlan&,
                                           int, int, cudaStream_t);

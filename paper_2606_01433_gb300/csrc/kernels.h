@@ -33,6 +33,16 @@ template <typename TM, typename TV>
 void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P, int launch, int max_ld,
                  cudaStream_t s);
 void set_gemv_smem_limits();
+template <typename TV>
+void launch_sym_reduce(const TV* vec, TV* y, const GemvPlan& P, int T, cudaStream_t s);
+struct PackTile {
+  int64_t src, dst;
+  int32_t ld, rows, cols, pad;  // rows/cols valid inside the tile
+};
+template <typename T>
+void pack_tiles(DevArena& tmp, const T* src, T* dst, const std::vector<PackTile>& tiles, int TT, cudaStream_t s);
+// tile edge of the packed symmetric blocks: one 16-byte load per lane across a warp
+inline int sym_tile_size(int prec) { return prec == GDSW_FP64 ? 64 : (prec == GDSW_FP32 ? 128 : 256); }
 template <typename T>
 void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s);
 template <typename T>

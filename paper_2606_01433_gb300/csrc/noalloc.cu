@@ -48,6 +48,7 @@ static void local_solve_into(gdsw_ctx* c, int l, const double* r, double* z, voi
     launch_gather<double>(r, L.gdof, v, nv, s);
     for (int k = 0; k < L.fwd.nlaunch(); ++k)
       launch_gemv<double, double>(static_cast<const double*>(L.fac), v, v, v, L.fwd, k, L.fwd_ld[k], s);
+    if (L.red.launch_tile_off.size() == 2) launch_sym_reduce<double>(v, v, L.red, L.sym_T, s);
     for (int k = 0; k < L.bwd.nlaunch(); ++k)
       launch_gemv<double, double>(static_cast<const double*>(L.fac), v, v, v, L.bwd, k, L.bwd_ld[k], s);
     launch_scatter<double>(v + nv, L.sc_ptr, L.sc_pos, L.sc_w, z, L.n, 0, s);
@@ -60,6 +61,7 @@ static void local_solve_into(gdsw_ctx* c, int l, const double* r, double* z, voi
       else
         launch_gemv<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), v, v, v, L.fwd, k, L.fwd_ld[k], s);
     }
+    if (L.red.launch_tile_off.size() == 2) launch_sym_reduce<float>(v, v, L.red, L.sym_T, s);
     for (int k = 0; k < L.bwd.nlaunch(); ++k) {
       if (L.prec == GDSW_FP32)
         launch_gemv<float, float>(static_cast<const float*>(L.fac), v, v, v, L.bwd, k, L.bwd_ld[k], s);
@@ -77,7 +79,8 @@ extern "C" int gdsw_apply_local_noalloc(gdsw_ctx* c, int32_t level, const double
   if (!c || c->host_only || level < 0 || level >= int(c->ld.size()) || !r || !z) return GDSW_ERR_INVALID_ARG;
   try {
     const LevelDev& L = c->ld[level];
-    const size_t need = size_t(2) * size_t(L.nvec) * (L.prec == GDSW_FP64 ? 8 : 4);
+    // the two local vectors and the partial sums of the packed symmetric blocks
+    const size_t need = (size_t(2) * size_t(L.nvec) + size_t(L.npart)) * (L.prec == GDSW_FP64 ? 8 : 4);
     if (need > kNoAllocScratchBytes) {
       c->err = "gdsw_apply_local_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
                " bytes of local workspace, more than the fixed " + std::to_string(kNoAllocScratchBytes) +
