@@ -49,6 +49,9 @@ def parse():
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--prof-stride", type=int, default=8,
                     help="CUDA-event timing of every k-th preconditioner apply inside the timed region")
+    ap.add_argument("--sweep", choices=["persistent", "steps"], default="steps",
+                    help="local solves as one persistent launch per level, or one launch per slab step")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM of the persistent sweep (0 = all)")
     ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals of mixed requests")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--serve-sizes", type=str, default="8,12,16,20,24,28,32")
@@ -56,11 +59,12 @@ def parse():
     return ap.parse_args()
 
 
-def gemv_traffic_ratio():
-    """DRAM bytes / algorithmic bytes of the level-1 sweep GEMV from the committed ncu summary,
-    valid only while the kernel source is the one that was profiled (else None)."""
+def gemv_traffic_ratio(persistent):
+    """DRAM bytes / algorithmic bytes of the level-1 sweep from the committed ncu summary of
+    that kernel, valid only while the kernel source is the one that was profiled (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_gemv_channel32_dram.json")
+    name = "k_sweep_channel32_dram.json" if persistent else "k_gemv_channel32_dram.json"
+    path = os.path.join(ROOT, "profiles", name)
     src = os.path.join(ROOT, "paper_2606_01433_gb300", "csrc", "dense.cu")
     if not os.path.exists(path):
         return None
@@ -322,6 +326,8 @@ def run_gdsw(args, rank, world, local):
     t0 = time.perf_counter()
     ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8, restart=100, max_it=1000)
     setup_mixed_s = time.perf_counter() - t0
+    persistent = args.sweep == "persistent"
+    ctx.gdsw_set_local_sweep(persistent, args.ctas_per_sm)
     n = ctx.n
     lib = gdsw.load()
     import ctypes
@@ -391,6 +397,7 @@ def run_gdsw(args, rank, world, local):
         t0 = time.perf_counter()
         c64 = gdsw.Context(p, precision=("fp64",) * 3, phi_precision="fp64", tol=1e-8)
         setup64 = time.perf_counter() - t0
+        c64.gdsw_set_local_sweep(persistent, args.ctas_per_sm)
         for _ in range(min(args.warmup, 1)):
             step(c64)
         c64.gdsw_profile_enable(True)
@@ -414,6 +421,7 @@ def run_gdsw(args, rank, world, local):
         del c64
         torch.cuda.empty_cache()
         ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8)
+        ctx.gdsw_set_local_sweep(persistent, args.ctas_per_sm)
 
     # end to end through the host-buffer entry point: u_k, b and x0 from pinned host memory,
     # x back to host, inside the timed region
@@ -445,7 +453,7 @@ def run_gdsw(args, rank, world, local):
 
     peak, peak_kind = measured_peaks()
     ms_step = total_ms / args.steps
-    ratio = gemv_traffic_ratio() if (args.workload == "channel" and args.m == 32 and args.mixed == "fp32") else None
+    ratio = gemv_traffic_ratio(persistent) if (args.workload == "channel" and args.m == 32 and args.mixed == "fp32") else None
     line = {
         "metric": METRIC,
         "value": ms_step,
@@ -481,7 +489,9 @@ def run_gdsw(args, rank, world, local):
         "setup_breakdown_ms": dict(zip(["host_symbolic", "viscosity_assembly", "level1_factors", "phi_and_A0",
                                         "coarse_levels", "total"], [float(v) for v in sizes.setup_ms])),
         "factor_gb": sizes.factor_entries[0] * (4 if args.mixed == "fp32" else 2) / 1e9,
-        "roofline": {"kernel": "k_gemv (level-1 block-LDU sweeps)", "bound": "hbm", "achieved": gemv_gbs,
+        "roofline": {"kernel": ("k_sweep (level-1 persistent block-LDL^T sweep, one launch per apply)" if persistent
+                                else "k_gemv/k_gemvt (level-1 block-LDL^T sweeps, one launch per slab step)"),
+                     "bound": "hbm", "achieved": gemv_gbs,
                      "peak": peak, "unit": "GB/s", "frac": (gemv_gbs / peak) if gemv_gbs else None,
                      "peak_kind": peak_kind, "avg_launch_ms": gemv_avg_ms, "avg_launch_bytes": gemv_avg_bytes,
                      "traffic": (ratio * gemv_avg_bytes) if ratio else None,

@@ -235,6 +235,19 @@ int64_t gdsw_kernel_launches(void);
  * put the DRAM traffic of a profiled launch beside the bytes the method must move. */
 int gdsw_plan_bytes(const gdsw_ctx* ctx, int32_t level, int32_t direction, int32_t k, double* bytes);
 
+/* How the local solves of every level run (the arithmetic, and so the result, is the same
+ * bit for bit either way):
+ *   persistent = 0 (default): one launch per slab step, forward then backward (Section 2.1
+ *     A_i^{-1} applied as block-LDL^T sweeps);
+ *   persistent = 1: one persistent launch per level and apply; CTAs take the tiles of all
+ *     slab steps from a work list in dependency order and wait (at most 1 s per wait, else
+ *     gdsw_solve returns GDSW_ERR_TIMEOUT) until the tiles they read from are written.
+ * ctas_per_sm: resident CTAs per SM of the persistent launch (0 = as many as fit); fewer
+ * leave room for the coarse branch that runs concurrently on a second stream.  Must not be
+ * called while the context has work in flight or inside a stream capture; a context whose
+ * apply is captured in a CUDA graph (use_graph) keeps its mode (GDSW_ERR_INVALID_ARG). */
+int gdsw_set_local_sweep(gdsw_ctx* ctx, int32_t persistent, int32_t ctas_per_sm);
+
 int gdsw_profile_enable(gdsw_ctx* ctx, int32_t on);
 int gdsw_profile_read(gdsw_ctx* ctx, gdsw_profile* prof);
 int gdsw_profile_reset(gdsw_ctx* ctx);

@@ -230,11 +230,90 @@ static double plan_bytes(const std::vector<GemvTask>& tasks, int t0, int t1, siz
   return b;
 }
 
+// Work list of the persistent sweep (same tasks and tiles as the per-step launches).  Per
+// flattened slab q four counters: Y (tiles of the G task that writes y_q), P (symmetric
+// tiles of S_q^{-1}), W (tiles that write w_q: dense S_q^{-1} rows or reductions), X
+// (backward tiles that write x_q).  Every item is listed after all producers it waits for.
+struct TaskRec {
+  int task, q, step, role, t0, t1;  // role: 0 dense S^{-1}, 1 symmetric S^{-1}, 2 G, 3 reduction, 4 backward
+};
+
+static void build_sweep(gdsw_ctx* c, LevelDev& L, int nslab, int Kmax, const std::vector<GemvTask>& tasks,
+                        const std::vector<GemvTile>& tiles, const std::vector<GemvTask>& rtasks,
+                        const std::vector<GemvTile>& rtiles, const std::vector<TaskRec>& recs, int xs_elems) {
+  auto ctr = [](int q, int kind) { return 1 + 4 * q + kind; };
+  enum { Y = 0, P = 1, W = 2, X = 3 };
+  const int nctr = 1 + 4 * nslab;
+  std::vector<int> nsig(nctr, 0), last(nctr, -1);
+  std::vector<SweepItem> items;
+  const int roff = int(tasks.size());
+  auto emit = [&](int op, int task, int arg, int signal, int w0, int w1) {
+    SweepItem it{op, task, arg, signal, -1, 0, -1, 0};
+    const int idx = int(items.size());
+    if (w0 >= 0 && nsig[w0] > 0) {
+      GDSW_CHECK(last[w0] < idx, GDSW_ERR_INVALID_ARG, "sweep list: producer after consumer");
+      it.wait0 = w0;
+      it.need0 = nsig[w0];
+    }
+    if (w1 >= 0 && nsig[w1] > 0) {
+      GDSW_CHECK(last[w1] < idx, GDSW_ERR_INVALID_ARG, "sweep list: producer after consumer");
+      it.wait1 = w1;
+      it.need1 = nsig[w1];
+    }
+    items.push_back(it);
+    if (signal >= 0) {
+      ++nsig[signal];
+      last[signal] = idx;
+    }
+  };
+  auto emit_reduce = [&](int step) {
+    for (const TaskRec& r : recs)
+      if (r.role == 3 && r.step == step)
+        for (int t = r.t0; t < r.t1; ++t) emit(SWEEP_REDUCE, roff + r.task, rtiles[t].row0, ctr(r.q, W), ctr(r.q, P), -1);
+  };
+  for (int k = 0; k < Kmax; ++k) {
+    for (const TaskRec& r : recs) {
+      if (r.step != k || r.role > 2) continue;
+      const int wy = k > 0 ? ctr(r.q, Y) : -1;  // y_q is final once the G task of step k-1 is done
+      const int sig = r.role == 0 ? ctr(r.q, W) : (r.role == 1 ? ctr(r.q, P) : ctr(r.q + 1, Y));
+      for (int t = r.t0; t < r.t1; ++t) emit(r.role == 1 ? SWEEP_SYM : SWEEP_ROWS, r.task, tiles[t].row0, sig, wy, -1);
+    }
+    if (k > 0) emit_reduce(k - 1);  // one step behind, so that the partials are mostly done
+  }
+  if (Kmax > 0) emit_reduce(Kmax - 1);
+  for (const TaskRec& r : recs) {  // backward, in step order: x_k = w_k - G_{k+1}^T x_{k+1}
+    if (r.role != 4) continue;
+    const int wx = nsig[ctr(r.q + 1, X)] > 0 ? ctr(r.q + 1, X) : ctr(r.q + 1, W);
+    for (int t = r.t0; t < r.t1; ++t) emit(SWEEP_COLS, r.task, tiles[t].row0, ctr(r.q, X), ctr(r.q, W), wx);
+  }
+  std::vector<GemvTask> all = tasks;
+  all.insert(all.end(), rtasks.begin(), rtasks.end());
+  SweepPlan& SP = L.sweep;
+  SP.nitems = int(items.size());
+  SP.nctr = nctr;
+  SP.xs_elems = (xs_elems + 3) & ~3;
+  SP.d_items = c->arena.upload(items, c->stream);
+  SP.d_tasks = c->arena.upload(all, c->stream);
+  SP.d_ctr = c->arena.alloc<unsigned>(nctr);
+}
+
+static void resize_sweep(LevelDev& L, int ctas_per_sm) {
+  if (L.sweep.nitems == 0) return;
+  L.sweep.ctas_per_sm = ctas_per_sm;
+  if (L.prec == GDSW_FP64)
+    size_sweep<double, double>(L.sweep);
+  else if (L.prec == GDSW_FP32)
+    size_sweep<float, float>(L.sweep);
+  else
+    size_sweep<__nv_bfloat16, float>(L.sweep);
+}
+
 static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
   std::vector<GemvTask> tasks;
   std::vector<GemvTile> tiles;
   std::vector<GemvTask> rtasks;  // reductions of the symmetric partial sums
   std::vector<GemvTile> rtiles;
+  std::vector<TaskRec> recs;
   const size_t esz = elem_size(L.prec), vsz = L.prec == GDSW_FP64 ? 8 : 4;
   const int rpt = L.fwd.rows_per_tile;
   const int64_t nv = S.nvec;
@@ -242,6 +321,7 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
   std::vector<int> sb(S.nsub + 1, 0);  // first flattened slab index of each part
   for (int i = 0; i < S.nsub; ++i) sb[i + 1] = sb[i] + S.K[i];
   int64_t part_off = 2 * nv;          // partial sums live behind the two local vectors
+  int xs_elems = 8;                   // shared staging of the persistent sweep
   L.fwd.launch_task_off = {0};
   L.fwd.launch_tile_off = {0};
   L.fwd_ld.clear();
@@ -257,28 +337,37 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
         GemvTask t{L.pS[q], y, nv + y, -1, sk, nt * TT, nt, 1.0f, 1, 0, part_off};
         int id = int(tasks.size());
         tasks.push_back(t);
+        const int t0 = int(tiles.size());
         for (int I = 0; I < nt; ++I)
           for (int J = I; J < nt; ++J) tiles.push_back({id, (I << 16) | J});
+        recs.push_back({id, q, k, 1, t0, int(tiles.size())});
         int rid = int(rtasks.size());
         rtasks.push_back(t);
+        const int r0t = int(rtiles.size());
         for (int r0 = 0; r0 < sk; r0 += 256) rtiles.push_back({rid, r0});
+        recs.push_back({rid, q, k, 3, r0t, int(rtiles.size())});
         part_off += int64_t(nt) * nt * TT;
         mld = std::max(mld, 11 * TT);
       } else {
         GemvTask t{L.pS[q], y, nv + y, -1, sk, sk, S.ldS[i][k], 1.0f};
+        const int t0 = int(tiles.size());
         add_task(tasks, tiles, t, rpt);
+        if (int(tiles.size()) > t0) recs.push_back({int(tasks.size()) - 1, q, k, 0, t0, int(tiles.size())});
         mld = std::max(mld, S.ldS[i][k]);
       }
       if (k + 1 < S.K[i] && S.m[i][k + 1] > 0) {
         int64_t y1 = S.voff[i] + S.soff[i][k + 1];
         GemvTask g{L.pG[q + 1], y, y1, y1, S.m[i][k + 1], sk, S.ldG[i][k + 1], -1.0f};
+        const int t0 = int(tiles.size());
         add_task(tasks, tiles, g, rpt);
+        if (int(tiles.size()) > t0) recs.push_back({int(tasks.size()) - 1, q, k, 2, t0, int(tiles.size())});
         mld = std::max(mld, S.ldG[i][k + 1]);
       }
     }
     L.fwd.launch_task_off.push_back(int(tasks.size()));
     L.fwd.launch_tile_off.push_back(int(tiles.size()));
     L.fwd_ld.push_back(mld);
+    xs_elems = std::max(xs_elems, mld);
   }
   L.npart = part_off - 2 * nv;
   L.red.launch_task_off = {0, int(rtasks.size())};
@@ -286,7 +375,7 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
   L.red_bytes = 0;
   for (const GemvTask& t : rtasks) L.red_bytes += (double(t.ld) * t.ld * TT + t.rows) * vsz;
   finish_plan(c->arena, L.red, rtasks, rtiles, c->stream);
-  // backward: x_k = w_k - G_{k+1}^T x_{k+1}[0:m_{k+1}], transposed GEMV over 256-column tiles
+  // backward: x_k = w_k - G_{k+1}^T x_{k+1}[0:m_{k+1}], transposed GEMV over column tiles
   L.bwd.transposed = true;
   L.bwd.launch_task_off = {int(tasks.size())};
   L.bwd.launch_tile_off = {int(tiles.size())};
@@ -301,12 +390,15 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
       GemvTask t{L.pG[sb[i] + k + 1], x, y, y, S.m[i][k + 1], S.s[i][k], S.ldG[i][k + 1], -1.0f};
       int id = int(tasks.size());
       tasks.push_back(t);
-      for (int c0 = 0; c0 < t.cols; c0 += 256) tiles.push_back({id, c0});
+      const int t0 = int(tiles.size());
+      for (int c0 = 0; c0 < t.cols; c0 += gemvt_tile_cols(L.prec)) tiles.push_back({id, c0});
+      recs.push_back({id, sb[i] + k, S.Kmax + j, 4, t0, int(tiles.size())});
       mrows = std::max(mrows, t.rows);
     }
     L.bwd.launch_task_off.push_back(int(tasks.size()));
     L.bwd.launch_tile_off.push_back(int(tiles.size()));
     L.bwd_ld.push_back(mrows);
+    xs_elems = std::max(xs_elems, mrows);
   }
   L.fwd_bytes.clear();
   L.bwd_bytes.clear();
@@ -314,6 +406,8 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
     L.fwd_bytes.push_back(plan_bytes(tasks, L.fwd.launch_task_off[k], L.fwd.launch_task_off[k + 1], esz, vsz));
   for (int k = 0; k < L.bwd.nlaunch(); ++k)
     L.bwd_bytes.push_back(plan_bytes(tasks, L.bwd.launch_task_off[k], L.bwd.launch_task_off[k + 1], esz, vsz, true));
+  build_sweep(c, L, sb[S.nsub], S.Kmax, tasks, tiles, rtasks, rtiles, recs, xs_elems);
+  resize_sweep(L, L.sweep.ctas_per_sm);
   GemvTask* dt = c->arena.upload(tasks, c->stream);
   GemvTile* dl = c->arena.upload(tiles, c->stream);
   L.fwd.d_tasks = dt;
@@ -819,6 +913,22 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
       launch_gemv<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), v, v, v, P, k, ld, s);
     }
   };
+  if (c->persistent_sweep && L.sweep.nitems > 0) {
+    // the whole forward / reduction / backward sequence as one persistent launch
+    double bytes = L.red_bytes;
+    for (double b : L.fwd_bytes) bytes += b;
+    for (double b : L.bwd_bytes) bytes += b;
+    ProfScope ps(c, group, bytes, s);
+    if (L.prec == GDSW_FP64)
+      launch_sweep<double, double>(static_cast<const double*>(L.fac), static_cast<double*>(L.vec), L.sweep,
+                                   c->d_sweep_flag, L.sym_T, s);
+    else if (L.prec == GDSW_FP32)
+      launch_sweep<float, float>(static_cast<const float*>(L.fac), static_cast<float*>(L.vec), L.sweep,
+                                 c->d_sweep_flag, L.sym_T, s);
+    else
+      launch_sweep<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), static_cast<float*>(L.vec),
+                                         L.sweep, c->d_sweep_flag, L.sym_T, s);
+  } else {
   for (int k = 0; k < L.fwd.nlaunch(); ++k) sweep(L.fwd, k, L.fwd_ld[k], L.fwd_bytes[k]);
   if (L.red.launch_tile_off.size() == 2 && L.red.launch_tile_off[1] > 0) {
     // w_k = S_k^{-1} y_k of the packed symmetric blocks: sum of the partial products
@@ -829,6 +939,7 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
       launch_sym_reduce<float>(static_cast<const float*>(L.vec), static_cast<float*>(L.vec), L.red, L.sym_T, s);
   }
   for (int k = 0; k < L.bwd.nlaunch(); ++k) sweep(L.bwd, k, L.bwd_ld[k], L.bwd_bytes[k]);
+  }
   {
     ProfScope ps(c, GDSW_K_SCATTER, double(nv) * (4 + 8 + (L.prec == GDSW_FP64 ? 8 : 4)) + 8.0 * L.n, s);
     if (L.prec == GDSW_FP64)
@@ -1032,6 +1143,17 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
   c->d_ad_col = c->arena.upload(M.ad_col, s);
   c->d_bd_ptr = c->arena.upload(M.bd_ptr, s);
   c->d_bd_col = c->arena.upload(M.bd_col, s);
+  {
+    std::vector<int32_t> rows;
+    for (int64_t r = 0; r < M.nv; ++r)
+      if (M.ad_ptr[r + 1] > M.ad_ptr[r]) rows.push_back(int32_t(r));
+    for (int64_t P = 0; P < M.np; ++P)
+      if (M.bd_ptr[P + 1] > M.bd_ptr[P]) rows.push_back(int32_t(M.nv + P));
+    c->n_lift_rows = int64_t(rows.size());
+    c->d_lift_rows = rows.empty() ? nullptr : c->arena.upload(rows, s);
+  }
+  c->d_sweep_flag = c->arena.alloc<unsigned>(1);
+  GDSW_CUDA(cudaMemsetAsync(c->d_sweep_flag, 0, sizeof(unsigned), s));
   c->d_gdir = c->arena.upload(M.g, s);
   c->d_uk = c->arena.alloc<double>(3 * M.nnodes);
   if (visc->uk)
@@ -1362,7 +1484,7 @@ int gdsw_reassemble(gdsw_ctx* c, const double* uk) {
       launch_viscosity(c, c->stream);
     }
     {
-      ProfScope ps(c, GDSW_K_ASSEMBLY, 8.0 * (9 * c->nnzb + 6 * c->nb), c->stream);
+      ProfScope ps(c, GDSW_K_ASSEMBLY, 8.0 * 9 * c->nnzb, c->stream);  // A only: B is viscosity-free
       launch_assembly(c, c->stream);
     }
   });
@@ -1457,6 +1579,18 @@ int gdsw_plan_bytes(const gdsw_ctx* c, int32_t level, int32_t direction, int32_t
   if (k < 0 || k >= int(v.size())) return GDSW_ERR_INVALID_ARG;
   *bytes = v[k];
   return GDSW_OK;
+}
+
+int gdsw_set_local_sweep(gdsw_ctx* c, int32_t persistent, int32_t ctas_per_sm) {
+  if (!c || c->host_only || ctas_per_sm < 0) return GDSW_ERR_INVALID_ARG;
+  if (c->apply_graph) {
+    c->err = "gdsw_set_local_sweep: the apply is already captured in a CUDA graph (use_graph)";
+    return GDSW_ERR_INVALID_ARG;
+  }
+  GDSW_TRY(c, {
+    c->persistent_sweep = persistent != 0;
+    for (LevelDev& L : c->ld) resize_sweep(L, ctas_per_sm);
+  });
 }
 
 int gdsw_profile_enable(gdsw_ctx* c, int32_t on) {

@@ -203,6 +203,22 @@ struct GemvPlan {
   int nlaunch() const { return int(launch_task_off.size()) - 1; }
 };
 
+// One item of a persistent level sweep: a tile of one task, the per-slab counters it waits
+// for (index into the counter array, value to reach; -1 = none) and the counter it bumps.
+enum { SWEEP_ROWS = 0, SWEEP_SYM = 1, SWEEP_REDUCE = 2, SWEEP_COLS = 3 };
+struct SweepItem {
+  int32_t op, task, arg, signal;
+  int32_t wait0, need0, wait1, need1;
+};
+struct SweepPlan {
+  SweepItem* d_items = nullptr;
+  GemvTask* d_tasks = nullptr;   // forward, backward and reduction tasks of the level
+  unsigned* d_ctr = nullptr;     // [0] = claim counter, then 4 counters per slab
+  int nitems = 0, nctr = 0, xs_elems = 0, grid = 0, ctas_per_sm = 0, max_per_sm = 0;
+  size_t smem = 0;
+};
+constexpr unsigned long long kSweepWaitLimitNs = 1000000000ull;  // 1 s per wait
+
 struct LevelDev {
   int n = 0, N = 0, prec = GDSW_FP64;
   // local problems
@@ -210,6 +226,7 @@ struct LevelDev {
   int64_t nfac = 0, nvec = 0;
   int32_t* gdof = nullptr;
   GemvPlan fwd, bwd;            // forward launches (Sinv, G) and backward launches (W)
+  SweepPlan sweep;              // the same tiles as one persistent launch
   void* vec = nullptr;          // local vector workspace (2 * nvec, compute precision)
   int32_t *sc_ptr = nullptr, *sc_pos = nullptr;
   double* sc_w = nullptr;
@@ -287,6 +304,11 @@ struct gdsw_ctx {
   int32_t *d_a_diag = nullptr, *d_a_tpos = nullptr;  // diagonal block of each row, transpose map
   int32_t *d_b_ptr = nullptr, *d_b_col = nullptr, *d_bt2b = nullptr;
   int32_t *d_ad_ptr = nullptr, *d_ad_col = nullptr, *d_bd_ptr = nullptr, *d_bd_col = nullptr;
+  int32_t* d_lift_rows = nullptr;   // rows (velocity node, or nv + pressure node) with a Dirichlet neighbour
+  int64_t n_lift_rows = 0;
+  bool b_assembled = false;         // B does not depend on the viscosity: assembled once
+  unsigned* d_sweep_flag = nullptr; // set by a persistent sweep whose wait ran out
+  bool persistent_sweep = false;    // local solves as one persistent launch per level (else per slab step)
   double* d_gdir = nullptr;         // Dirichlet datum, 3 per node
   void* d_tables = nullptr;         // RefTables
   double* d_val = nullptr;          // [A blocks (9 per block) | BT (3 per entry) | B (3 per entry)]

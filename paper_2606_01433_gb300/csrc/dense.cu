@@ -70,8 +70,8 @@ __device__ __forceinline__ void sym_tile(const TM* __restrict__ M, const TV* xba
   TV* pcol = smem + 3 * T;  // 8 x T
   const int s = t.rows, nt = t.ld;
   for (int e = threadIdx.x; e < T; e += blockDim.x) {
-    xi[e] = I * T + e < s ? xbase[t.x + I * T + e] : TV(0);
-    xj[e] = J * T + e < s ? xbase[t.x + J * T + e] : TV(0);
+    xi[e] = I * T + e < s ? __ldcg(xbase + t.x + I * T + e) : TV(0);
+    xj[e] = J * T + e < s ? __ldcg(xbase + t.x + J * T + e) : TV(0);
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -118,24 +118,17 @@ __device__ __forceinline__ void sym_tile(const TM* __restrict__ M, const TV* xba
   }
 }
 
+// Rows [row0, row0 + 8 RPW) of one task.  Vector reads go through L2 (ld.global.cg): in the
+// persistent sweep other CTAs write the local vectors while this one runs.
 template <typename TM, typename TV, int RPW>
-__global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV* xbase, TV* ybase,
-                                              const TV* bbase, const GemvTask* __restrict__ tasks,
-                                              const GemvTile* __restrict__ tiles) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TV* xs = reinterpret_cast<TV*>(smem_raw);
-  const GemvTile tl = tiles[blockIdx.x];
-  const GemvTask t = tasks[tl.task];
-  if (t.kind == 1) {  // packed symmetric tile; partial sums go to ybase + t.part
-    sym_tile<TM, TV>(M, xbase, ybase, t, tl.row0 >> 16, tl.row0 & 0xffff, xs);
-    return;
-  }
+__device__ __forceinline__ void rows_tile(const TM* __restrict__ M, const TV* xbase, TV* ybase, const TV* bbase,
+                                          const GemvTask& t, int row0, TV* xs) {
   const int ld = t.ld;
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = c < t.cols ? xbase[t.x + c] : TV(0);
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = c < t.cols ? __ldcg(xbase + t.x + c) : TV(0);
   __syncthreads();
   constexpr int V = Vec16<TM>::N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rbeg = tl.row0 + warp * RPW;
+  const int rbeg = row0 + warp * RPW;
   TV acc[RPW];
   const TM* rowp[RPW];
 #pragma unroll
@@ -195,76 +188,92 @@ __global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV
     int r = rbeg + lane;
     if (r < t.rows) {
       TV v = TV(t.alpha) * a;
-      if (t.base >= 0) v += bbase[t.base + r];
+      if (t.base >= 0) v += __ldcg(bbase + t.base + r);
       ybase[t.y + r] = v;
     }
   }
 }
 
+template <typename TM, typename TV, int RPW>
+__global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV* xbase, TV* ybase,
+                                              const TV* bbase, const GemvTask* __restrict__ tasks,
+                                              const GemvTile* __restrict__ tiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TV* xs = reinterpret_cast<TV*>(smem_raw);
+  const GemvTile tl = tiles[blockIdx.x];
+  const GemvTask t = tasks[tl.task];
+  if (t.kind == 1)  // packed symmetric tile; partial sums go to ybase + t.part
+    sym_tile<TM, TV>(M, xbase, ybase, t, tl.row0 >> 16, tl.row0 & 0xffff, xs);
+  else
+    rows_tile<TM, TV, RPW>(M, xbase, ybase, bbase, t, tl.row0, xs);
+}
+
 // ------------------------------------------------------------------ ragged batched GEMV, transposed
-// y[c] = base[c] + alpha * sum_r M[r][c] x[r] for the columns [col0, col0 + 256) of a task
+// y[c] = base[c] + alpha * sum_r M[r][c] x[r] for the columns [col0, col0 + 32 V) of a task
 // (used with the sub-diagonal blocks G of a symmetric LDL^T factorisation, whose
-// transposes are the super-diagonal blocks).  Each lane owns 8 consecutive columns and the
-// 8 warps split the rows; partial sums are combined in shared memory in a fixed order.
-__device__ __forceinline__ void load8(const float* p, float* v) {
-  load16s(p, v);
-  load16s(p + 4, v + 4);
+// transposes are the super-diagonal blocks).  Each lane owns V consecutive columns (one
+// 16-byte load per row) and the 8 warps split the rows, four rows in flight per warp;
+// partial sums are combined in shared memory in a fixed order.  Narrow tiles (32 V columns)
+// give several CTAs per SM and per task, so the ragged launch stays balanced across SMs.
+template <typename TM, typename TV>
+__device__ __forceinline__ void cols_tile(const TM* __restrict__ M, const TV* xbase, TV* ybase, const TV* bbase,
+                                          const GemvTask& t, int col0, TV* xs, TV* part) {
+  constexpr int V = Vec16<TM>::N, C = 32 * V;
+  for (int r = threadIdx.x; r < t.rows; r += blockDim.x) xs[r] = __ldcg(xbase + t.x + r);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = col0 + lane * V;  // tile column start + lane's V columns
+  TV acc[V];
+#pragma unroll
+  for (int u = 0; u < V; ++u) acc[u] = TV(0);
+  if (c0 < t.ld) {
+    const TM* p = M + t.mat + c0;
+    int r = warp;
+    for (; r + 24 < t.rows; r += 32) {
+      TV v[4][V];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) load16s(p + int64_t(r + 8 * q) * t.ld, v[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const TV xq = xs[r + 8 * q];
+#pragma unroll
+        for (int u = 0; u < V; ++u) acc[u] = fma(v[q][u], xq, acc[u]);
+      }
+    }
+    for (; r < t.rows; r += 8) {
+      TV v0[V];
+      load16s(p + int64_t(r) * t.ld, v0);
+      const TV x0 = xs[r];
+#pragma unroll
+      for (int u = 0; u < V; ++u) acc[u] = fma(v0[u], x0, acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < V; ++u) part[warp * (C + 1) + lane * V + u] = acc[u];
+  __syncthreads();
+  for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+    const int c = col0 + cc;
+    if (c < t.cols) {
+      TV s = part[cc];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) s += part[w * (C + 1) + cc];
+      TV v = TV(t.alpha) * s;
+      if (t.base >= 0) v += __ldcg(bbase + t.base + c);
+      ybase[t.y + c] = v;
+    }
+  }
 }
-__device__ __forceinline__ void load8(const double* p, double* v) {
-  load16s(p, v);
-  load16s(p + 2, v + 2);
-  load16s(p + 4, v + 4);
-  load16s(p + 6, v + 6);
-}
-__device__ __forceinline__ void load8(const __nv_bfloat16* p, float* v) { load16s(p, v); }
 
 template <typename TM, typename TV>
 __global__ void __launch_bounds__(256) k_gemvt(const TM* __restrict__ M, const TV* xbase, TV* ybase,
                                                const TV* bbase, const GemvTask* __restrict__ tasks,
                                                const GemvTile* __restrict__ tiles) {
+  constexpr int C = 32 * Vec16<TM>::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TV* xs = reinterpret_cast<TV*>(smem_raw);
-  __shared__ TV part[8][256 + 1];
+  __shared__ TV part[8 * (C + 1)];
   const GemvTile tl = tiles[blockIdx.x];
   const GemvTask t = tasks[tl.task];
-  for (int r = threadIdx.x; r < t.rows; r += blockDim.x) xs[r] = xbase[t.x + r];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = tl.row0 + lane * 8;  // tile column start + lane's 8 columns
-  TV acc[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) acc[u] = TV(0);
-  if (c0 < t.ld) {
-    const TM* p = M + t.mat + c0;
-    int r = warp;
-    for (; r + 8 < t.rows; r += 16) {  // two rows in flight per warp
-      TV v0[8], v1[8];
-      load8(p + int64_t(r) * t.ld, v0);
-      load8(p + int64_t(r + 8) * t.ld, v1);
-      const TV x0 = xs[r], x1 = xs[r + 8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] = fma(v1[u], x1, fma(v0[u], x0, acc[u]));
-    }
-    for (; r < t.rows; r += 8) {
-      TV v0[8];
-      load8(p + int64_t(r) * t.ld, v0);
-      const TV x0 = xs[r];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] = fma(v0[u], x0, acc[u]);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 8; ++u) part[warp][lane * 8 + u] = acc[u];
-  __syncthreads();
-  const int c = tl.row0 + threadIdx.x;
-  if (c < t.cols) {
-    TV s = part[0][threadIdx.x];
-#pragma unroll
-    for (int w = 1; w < 8; ++w) s += part[w][threadIdx.x];
-    TV v = TV(t.alpha) * s;
-    if (t.base >= 0) v += bbase[t.base + c];
-    ybase[t.y + c] = v;
-  }
+  cols_tile<TM, TV>(M, xbase, ybase, bbase, t, tl.row0, reinterpret_cast<TV*>(smem_raw), part);
 }
 
 template <typename TM, typename TV>
@@ -285,17 +294,22 @@ void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P
 // y[r] = alpha * sum over the nt source blocks of the partials of row r (fixed order);
 // one CTA per 256 rows of one symmetric task.
 template <typename TV>
-__global__ void k_sym_reduce(const TV* __restrict__ vec, TV* ybase, const GemvTask* __restrict__ tasks,
-                             const GemvTile* __restrict__ tiles, int T) {
-  const GemvTile tl = tiles[blockIdx.x];
-  const GemvTask t = tasks[tl.task];
-  const int r = tl.row0 + threadIdx.x;
+__device__ __forceinline__ void reduce_tile(const TV* vec, TV* ybase, const GemvTask& t, int row0, int T) {
+  const int r = row0 + threadIdx.x;
   if (r >= t.rows) return;
   const int R = r / T, e = r - R * T;
   const TV* p = vec + t.part + int64_t(R) * t.ld * T + e;
   TV s = TV(0);
-  for (int S = 0; S < t.ld; ++S) s += p[int64_t(S) * T];
+  for (int S = 0; S < t.ld; ++S) s += __ldcg(p + int64_t(S) * T);
   ybase[t.y + r] = TV(t.alpha) * s;
+}
+
+template <typename TV>
+__global__ void k_sym_reduce(const TV* __restrict__ vec, TV* ybase, const GemvTask* __restrict__ tasks,
+                             const GemvTile* __restrict__ tiles, int T) {
+  const GemvTile tl = tiles[blockIdx.x];
+  const GemvTask t = tasks[tl.task];
+  reduce_tile<TV>(vec, ybase, t, tl.row0, T);
 }
 
 template <typename TV>
@@ -307,6 +321,115 @@ void launch_sym_reduce(const TV* vec, TV* y, const GemvPlan& P, int T, cudaStrea
 }
 template void launch_sym_reduce<double>(const double*, double*, const GemvPlan&, int, cudaStream_t);
 template void launch_sym_reduce<float>(const float*, float*, const GemvPlan&, int, cudaStream_t);
+
+// ------------------------------------------------------------------ persistent level sweep
+// One launch runs every tile of a level's local solves -- forward row tiles and packed
+// symmetric tiles, the partial-sum reductions, the transposed backward tiles -- from a work
+// list in dependency order.  CTAs claim items with an atomic counter (the next claim is made
+// before the current item runs).  An item first waits until the per-slab counters of the
+// tiles it reads from are complete (y_k written, partials written, w_k written, x_k
+// written), runs, then adds one to its own counter.  Claims follow list order and every
+// producer precedes its consumers in the list, so the lowest unfinished claimed item always
+// has its producers finished: the sweep cannot deadlock, whatever the number of resident
+// CTAs.  A wait longer than limit_ns sets *flag and every CTA returns; the host reports it.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool wait_count(const unsigned* cnt, unsigned need, unsigned* flag,
+                                           unsigned long long limit_ns) {
+  const volatile unsigned* c = cnt;
+  if (*c >= need) return true;
+  const unsigned long long t_end = global_ns() + limit_ns;
+  while (*c < need) {
+    if (*reinterpret_cast<volatile unsigned*>(flag)) return false;
+    if (global_ns() > t_end) {
+      atomicExch(flag, 1u);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+template <typename TM, typename TV>
+__global__ void __launch_bounds__(256, 3) k_sweep(const TM* __restrict__ M, TV* vec, const GemvTask* __restrict__ tasks,
+                                               const SweepItem* __restrict__ items, int nitems, unsigned* ctr,
+                                               unsigned* flag, int T, int xs_elems, unsigned long long limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TV* xs = reinterpret_cast<TV*>(smem_raw);
+  TV* cpart = xs + xs_elems;  // 8 x (32 V + 1) column partials of the transposed tiles
+  __shared__ int s_item[2];
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) s_item[0] = int(atomicAdd(ctr, 1u));
+  __syncthreads();
+  int cur = 0;
+  while (true) {
+    const int it = s_item[cur];
+    if (it >= nitems) break;
+    const SweepItem w = items[it];
+    if (threadIdx.x == 0) {
+      s_item[cur ^ 1] = int(atomicAdd(ctr, 1u));
+      bool ok = true;
+      if (w.wait0 >= 0) ok = wait_count(ctr + w.wait0, unsigned(w.need0), flag, limit_ns);
+      if (ok && w.wait1 >= 0) ok = wait_count(ctr + w.wait1, unsigned(w.need1), flag, limit_ns);
+      __threadfence();
+      s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const GemvTask t = tasks[w.task];
+    if (w.op == SWEEP_ROWS)
+      rows_tile<TM, TV, 4>(M, vec, vec, vec, t, w.arg, xs);
+    else if (w.op == SWEEP_SYM)
+      sym_tile<TM, TV>(M, vec, vec, t, w.arg >> 16, w.arg & 0xffff, xs);
+    else if (w.op == SWEEP_REDUCE)
+      reduce_tile<TV>(vec, vec, t, w.arg, T);
+    else
+      cols_tile<TM, TV>(M, vec, vec, vec, t, w.arg, xs, cpart);
+    __syncthreads();  // every write of this item is issued; the shared staging is free again
+    if (threadIdx.x == 0 && w.signal >= 0) {
+      __threadfence();
+      atomicAdd(ctr + w.signal, 1u);
+    }
+    cur ^= 1;
+  }
+}
+
+template <typename TM, typename TV>
+void size_sweep(SweepPlan& P) {
+  constexpr int C = 32 * Vec16<TM>::N;
+  P.smem = (size_t(P.xs_elems) + 8 * (C + 1)) * sizeof(TV);
+  GDSW_CHECK(P.smem <= size_t(200) * 1024, GDSW_ERR_INVALID_ARG, "persistent sweep: staging exceeds shared memory");
+  // one limit for every level's launch of this instantiation (the attribute is per kernel)
+  GDSW_CUDA(cudaFuncSetAttribute(k_sweep<TM, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  int per_sm = 0, dev = 0, nsm = 0;
+  GDSW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<TM, TV>, 256, P.smem));
+  GDSW_CUDA(cudaGetDevice(&dev));
+  GDSW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  GDSW_CHECK(per_sm > 0, GDSW_ERR_CUDA, "persistent sweep: no CTA fits on an SM");
+  P.max_per_sm = per_sm;
+  const int want = P.ctas_per_sm > 0 ? std::min(P.ctas_per_sm, per_sm) : per_sm;
+  P.grid = int(std::min<int64_t>(int64_t(want) * nsm, P.nitems));
+}
+
+template <typename TM, typename TV>
+void launch_sweep(const TM* M, TV* vec, const SweepPlan& P, unsigned* flag, int T, cudaStream_t s) {
+  if (P.nitems == 0) return;
+  GDSW_CUDA(cudaMemsetAsync(P.d_ctr, 0, sizeof(unsigned) * P.nctr, s));
+  k_sweep<TM, TV><<<P.grid, 256, P.smem, s>>>(M, vec, P.d_tasks, P.d_items, P.nitems, P.d_ctr, flag, T, P.xs_elems,
+                                             kSweepWaitLimitNs);
+  check_launch("k_sweep");
+}
+template void size_sweep<double, double>(SweepPlan&);
+template void size_sweep<float, float>(SweepPlan&);
+template void size_sweep<__nv_bfloat16, float>(SweepPlan&);
+template void launch_sweep<double, double>(const double*, double*, const SweepPlan&, unsigned*, int, cudaStream_t);
+template void launch_sweep<float, float>(const float*, float*, const SweepPlan&, unsigned*, int, cudaStream_t);
+template void launch_sweep<__nv_bfloat16, float>(const __nv_bfloat16*, float*, const SweepPlan&, unsigned*, int,
+                                                 cudaStream_t);
 
 // copy of T x T tiles out of full row-major blocks, zero padded (packing of the upper triangle)
 template <typename T>

@@ -307,6 +307,16 @@ void fgmres_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (c->d_sweep_flag) {  // a persistent sweep gave up waiting: the preconditioner output is void
+    unsigned flag = 0;
+    GDSW_CUDA(cudaMemcpyAsync(&flag, c->d_sweep_flag, sizeof(flag), cudaMemcpyDeviceToHost, s));
+    GDSW_CUDA(cudaStreamSynchronize(s));
+    if (flag) {
+      GDSW_CUDA(cudaMemsetAsync(c->d_sweep_flag, 0, sizeof(unsigned), s));
+      status = GDSW_ERR_TIMEOUT;
+      c->err = "persistent local sweep: a dependency wait exceeded its time limit";
+    }
+  }
   info->iterations = it;
   info->relres = beta / bnorm;
   info->est_relres = est / bnorm;

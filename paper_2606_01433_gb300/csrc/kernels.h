@@ -33,6 +33,10 @@ template <typename TM, typename TV>
 void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P, int launch, int max_ld,
                  cudaStream_t s);
 void set_gemv_smem_limits();
+template <typename TM, typename TV>
+void size_sweep(SweepPlan& P);
+template <typename TM, typename TV>
+void launch_sweep(const TM* M, TV* vec, const SweepPlan& P, unsigned* flag, int T, cudaStream_t s);
 template <typename TV>
 void launch_sym_reduce(const TV* vec, TV* y, const GemvPlan& P, int T, cudaStream_t s);
 struct PackTile {
@@ -43,6 +47,8 @@ template <typename T>
 void pack_tiles(DevArena& tmp, const T* src, T* dst, const std::vector<PackTile>& tiles, int TT, cudaStream_t s);
 // tile edge of the packed symmetric blocks: one 16-byte load per lane across a warp
 inline int sym_tile_size(int prec) { return prec == GDSW_FP64 ? 64 : (prec == GDSW_FP32 ? 128 : 256); }
+// column tile of the transposed GEMV: 32 lanes x one 16-byte load of matrix entries
+inline int gemvt_tile_cols(int prec) { return prec == GDSW_FP64 ? 64 : (prec == GDSW_FP32 ? 128 : 256); }
 template <typename T>
 void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s);
 template <typename T>

@@ -271,15 +271,22 @@ __global__ void k_copy_bt(const int32_t* __restrict__ bt2b, int64_t nbt, const d
   btval[e * 3 + 2] = bval[s * 3 + 2];
 }
 
-// b = -A_(free, D) g_D
-__global__ void k_lift(const int32_t* ad_ptr, const int32_t* ad_col, const int32_t* vnode, int64_t nv,
-                       const int32_t* bd_ptr, const int32_t* bd_col, const int32_t* pnode, int64_t np, Geo G,
-                       const uint8_t* mask, const int32_t* felem, const double* nu, const RefTables* T, int form,
-                       const double* g, double* b) {
-  int64_t row = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+// b = -A_(free, D) g_D.  One warp per row that has a Dirichlet neighbour with g != 0 (the
+// rows are listed at set-up; every other entry of b is zero); the lanes take the row's
+// Dirichlet neighbours and the warp sums them with a fixed butterfly.
+__global__ void __launch_bounds__(256) k_lift(const int32_t* __restrict__ rows, int64_t nrows,
+                                              const int32_t* ad_ptr, const int32_t* ad_col, const int32_t* vnode,
+                                              int64_t nv, const int32_t* bd_ptr, const int32_t* bd_col,
+                                              const int32_t* pnode, Geo G, const uint8_t* mask,
+                                              const int32_t* felem, const double* nu, const RefTables* T, int form,
+                                              const double* g, double* b) {
+  const int64_t w = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  const int64_t row = rows[w];
   if (row < nv) {
     double acc[3] = {0, 0, 0};
-    for (int e = ad_ptr[row]; e < ad_ptr[row + 1]; ++e) {
+    for (int e = ad_ptr[row] + lane; e < ad_ptr[row + 1]; e += 32) {
       int64_t J = ad_col[e];
       double blk[9];
       velocity_block(vnode[row], J, G, mask, felem, nu, T, form, blk);
@@ -288,19 +295,23 @@ __global__ void k_lift(const int32_t* ad_ptr, const int32_t* ad_col, const int32
 #pragma unroll
         for (int d = 0; d < 3; ++d) acc[c] = fma(blk[c * 3 + d], g[3 * J + d], acc[c]);
     }
-    b[3 * row + 0] = -acc[0];
-    b[3 * row + 1] = -acc[1];
-    b[3 * row + 2] = -acc[2];
-  } else if (row < nv + np) {
-    int64_t P = row - nv;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane < 3) b[3 * row + lane] = -(lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[2]));
+  } else {
+    const int64_t P = row - nv;
     double acc = 0.0;
-    for (int e = bd_ptr[P]; e < bd_ptr[P + 1]; ++e) {
+    for (int e = bd_ptr[P] + lane; e < bd_ptr[P + 1]; e += 32) {
       int64_t J = bd_col[e];
       double v[3];
       divergence_entry(pnode[P], J, G, mask, T, v);
       acc = fma(v[0], g[3 * J], fma(v[1], g[3 * J + 1], fma(v[2], g[3 * J + 2], acc)));
     }
-    b[3 * nv + P] = -acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) b[3 * nv + P] = -acc;
   }
 }
 
@@ -393,6 +404,7 @@ void launch_assembly(gdsw_ctx* c, cudaStream_t s) {
   k_assemble_A<<<int((nv + 7) / 8), 256, 0, s>>>(c->d_a_ptr, c->d_a_col, c->d_a_diag, c->d_a_tpos, c->d_vnode, nv,
                                                  geo(c), c->d_mask, c->d_felem, c->d_nu, T, c->form, aval);
   check_launch("k_assemble_A");
+  if (c->b_assembled) return;  // B = -(q, div u) depends on the mesh only, not on the viscosity
   k_assemble_B<<<int((np + 7) / 8), 256, 0, s>>>(c->d_b_ptr, c->d_b_col, c->d_pnode, c->d_vnode, np, geo(c),
                                                  c->d_mask, T, bval);
   check_launch("k_assemble_B");
@@ -400,14 +412,18 @@ void launch_assembly(gdsw_ctx* c, cudaStream_t s) {
     k_copy_bt<<<int((c->nbt + 255) / 256), 256, 0, s>>>(c->d_bt2b, c->nbt, bval, btval);
     check_launch("k_copy_bt");
   }
+  c->b_assembled = true;
 }
 
 void launch_lift(gdsw_ctx* c, double* b, cudaStream_t s) {
   int64_t nv = c->mesh.nv, np = c->mesh.np;
-  int64_t n = nv + np;
-  k_lift<<<int((n + 127) / 128), 128, 0, s>>>(c->d_ad_ptr, c->d_ad_col, c->d_vnode, nv, c->d_bd_ptr, c->d_bd_col,
-                                              c->d_pnode, np, geo(c), c->d_mask, c->d_felem, c->d_nu,
-                                              static_cast<RefTables*>(c->d_tables), c->form, c->d_gdir, b);
+  // every entry of b not written below (rows without a Dirichlet neighbour) is zero
+  GDSW_CUDA(cudaMemsetAsync(b, 0, size_t(3 * nv + np) * sizeof(double), s));
+  if (c->n_lift_rows == 0) return;
+  k_lift<<<int((c->n_lift_rows + 7) / 8), 256, 0, s>>>(c->d_lift_rows, c->n_lift_rows, c->d_ad_ptr, c->d_ad_col,
+                                                       c->d_vnode, nv, c->d_bd_ptr, c->d_bd_col, c->d_pnode, geo(c),
+                                                       c->d_mask, c->d_felem, c->d_nu,
+                                                       static_cast<RefTables*>(c->d_tables), c->form, c->d_gdir, b);
   check_launch("k_lift");
 }
 

@@ -98,7 +98,15 @@ __global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, co
   if (l >= m.nI) return;
   double acc = 0.0;
   const TP* p = phiT + m.phi + l;
-  for (int j = 0; j < m.c; ++j) acc = fma(double(__ldcs(p + int64_t(j) * m.ld)), xs[j], acc);
+  int j = 0;
+  for (; j + 8 <= m.c; j += 8) {  // eight independent loads in flight, FMAs in column order
+    TP v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + int64_t(j + u) * m.ld);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc = fma(double(v[u]), xs[j + u], acc);
+  }
+  for (; j < m.c; ++j) acc = fma(double(__ldcs(p + int64_t(j) * m.ld)), xs[j], acc);
   int64_t g = idofs[m.ioff + l];
   z[g] += acc;
 }

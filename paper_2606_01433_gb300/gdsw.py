@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
         "gdsw_level_entities": ([vp, i32, C.POINTER(i32)], C.c_int),
         "gdsw_kernel_launches": ([], i64),
         "gdsw_plan_bytes": ([vp, i32, i32, i32, C.POINTER(C.c_double)], C.c_int),
+        "gdsw_set_local_sweep": ([vp, i32, i32], C.c_int),
         "gdsw_profile_enable": ([vp, i32], C.c_int),
         "gdsw_profile_read": ([vp, C.POINTER(gdsw_profile)], C.c_int),
         "gdsw_profile_reset": ([vp], C.c_int),
@@ -291,6 +292,11 @@ class Context:
         n = C.c_int32()
         self._check(self.lib.gdsw_level_entities(self.h, level, C.byref(n)))
         return n.value
+
+    def gdsw_set_local_sweep(self, persistent=True, ctas_per_sm=0):
+        """Local solves as one persistent launch per level, or one launch per slab step (the default
+        of a new context)."""
+        return self._check(self.lib.gdsw_set_local_sweep(self.h, 1 if persistent else 0, int(ctas_per_sm)))
 
     def gdsw_profile_enable(self, on=True):
         """on: False/0 = off, True/1 = time every apply, k > 1 = every k-th apply."""
