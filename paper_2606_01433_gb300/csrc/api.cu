@@ -1092,6 +1092,8 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
     const MeshHost& M = c->mesh;
     double b = 8.0 * (9.0 * M.a_col.size() + 3.0 * M.bt_col.size() + 3.0 * M.b_col.size());
     b += 4.0 * (M.a_col.size() + M.bt_col.size() + M.b_col.size() + 4.0 * M.n) + 8.0 * 27 * M.fluid.size();
+    b += 4.0 * (M.asm_uoff.size() + M.asm_unit.size() + M.asm_cta.size());
+    b += 80.0 * M.sell_acol.size() + 32.0 * M.sell_bcol.size() + 4.0 * M.sell_row.size();
     for (int l = 0; l < nlev; ++l) {
       const LevelHost& H = c->lh[l];
       b += double(H.loc.nfac) * elem_size(opt->precision[l]) + 16.0 * H.loc.nvec + 16.0 * H.loc.nvec;
@@ -1134,6 +1136,19 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
   c->d_a_col = c->arena.upload(M.a_col, s);
   c->d_a_diag = c->arena.upload(M.a_diag, s);
   c->d_a_tpos = c->arena.upload(M.a_tpos, s);
+  c->d_asm_cta = c->arena.upload(M.asm_cta, s);
+  c->d_asm_uoff = c->arena.upload(M.asm_uoff, s);
+  c->d_asm_unit = c->arena.upload(M.asm_unit, s);
+  c->n_sell_slices = int64_t(M.sell_aoff.size()) - 1;
+  c->d_sell_row = c->arena.upload(M.sell_row, s);
+  c->d_sell_aoff = c->arena.upload(M.sell_aoff, s);
+  c->d_sell_boff = c->arena.upload(M.sell_boff, s);
+  c->d_sell_acol = c->arena.upload(M.sell_acol, s);
+  c->d_sell_asrc = c->arena.upload(M.sell_asrc, s);
+  c->d_sell_bcol = c->arena.upload(M.sell_bcol, s);
+  c->d_sell_bsrc = c->arena.upload(M.sell_bsrc, s);
+  c->d_sell_aval = c->arena.alloc<double>(9 * M.sell_acol.size());
+  c->d_sell_btval = c->arena.alloc<double>(3 * M.sell_bcol.size());
   c->d_bt_ptr = c->arena.upload(M.bt_ptr, s);
   c->d_bt_col = c->arena.upload(M.bt_col, s);
   c->d_b_ptr = c->arena.upload(M.b_ptr, s);

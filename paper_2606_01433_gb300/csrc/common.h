@@ -185,6 +185,19 @@ struct MeshHost {
   std::vector<int32_t> a_diag, a_tpos;   // position of block (I,I); position of block (J,I) for (I,J)
   std::vector<int32_t> ad_ptr, ad_col;   // velocity rows x Dirichlet nodes with g != 0 (node ids)
   std::vector<int32_t> bd_ptr, bd_col;   // pressure rows x Dirichlet nodes with g != 0
+  // assembly work units: one (upper block (I, J >= I), shared fluid element) pair each, listed
+  // block by block (elements in increasing index); packed fluid element << 10 | a << 5 | b
+  // with a, b the local Q2 node numbers of I and J in that element
+  std::vector<int32_t> asm_uoff;         // per block: first unit (lower blocks own none), nnzb + 1
+  std::vector<uint32_t> asm_unit;
+  std::vector<int32_t> asm_cta;          // first block of each assembly CTA (<= 256 units), + nnzb
+  // sliced copy of the velocity rows for the SpMV (32 rows per slice, rows sorted by length
+  // inside windows of 1024 rows so that a slice's rows have near-equal lengths): slot
+  // j * 32 + lane of slice s holds the j-th block (or B^T entry) of the slice's lane-th row
+  std::vector<int32_t> sell_row;         // nslices * 32: velocity row or -1
+  std::vector<int64_t> sell_aoff, sell_boff;  // nslices + 1: first block / B^T slot of each slice
+  std::vector<int32_t> sell_acol, sell_asrc;  // per block slot: column node, source block (-1: pad)
+  std::vector<int32_t> sell_bcol, sell_bsrc;  // per B^T slot: pressure column, source entry (-1: pad)
   bool shares_element(int64_t a, int64_t b) const;
   void coords(int64_t node, int& i, int& j, int& k) const {
     i = int(node % NX);
@@ -302,6 +315,13 @@ struct gdsw_ctx {
   int32_t *d_vnode = nullptr, *d_pnode = nullptr, *d_vidx = nullptr;
   int32_t *d_a_ptr = nullptr, *d_a_col = nullptr, *d_bt_ptr = nullptr, *d_bt_col = nullptr;
   int32_t *d_a_diag = nullptr, *d_a_tpos = nullptr;  // diagonal block of each row, transpose map
+  int32_t *d_asm_cta = nullptr, *d_asm_uoff = nullptr;  // assembly work units (see MeshHost)
+  uint32_t* d_asm_unit = nullptr;
+  int32_t *d_sell_row = nullptr, *d_sell_acol = nullptr, *d_sell_asrc = nullptr;  // sliced SpMV copy
+  int32_t *d_sell_bcol = nullptr, *d_sell_bsrc = nullptr;
+  int64_t *d_sell_aoff = nullptr, *d_sell_boff = nullptr;
+  double *d_sell_aval = nullptr, *d_sell_btval = nullptr;
+  int64_t n_sell_slices = 0;
   int32_t *d_b_ptr = nullptr, *d_b_col = nullptr, *d_bt2b = nullptr;
   int32_t *d_ad_ptr = nullptr, *d_ad_col = nullptr, *d_bd_ptr = nullptr, *d_bd_col = nullptr;
   int32_t* d_lift_rows = nullptr;   // rows (velocity node, or nv + pressure node) with a Dirichlet neighbour

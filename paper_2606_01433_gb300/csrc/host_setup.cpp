@@ -91,6 +91,60 @@ static void for_neighbors(const MeshHost& M, int64_t node, F f) {
 }
 
 // ------------------------------------------------------------------ mesh and patterns
+// Sliced layout of the velocity rows for the SpMV: on GB300 an FP64 warp instruction costs
+// the same with 1 or 32 active lanes, so each lane takes one whole row and the rows of a warp
+// are made to have (nearly) the same number of blocks.
+static void build_sell(MeshHost& M) {
+  const int64_t nv = M.nv;
+  const int64_t W = 1024;
+  std::vector<int32_t> order(nv);
+  for (int64_t r = 0; r < nv; ++r) order[r] = int32_t(r);
+  auto alen = [&](int32_t r) { return M.a_ptr[r + 1] - M.a_ptr[r]; };
+  auto blen = [&](int32_t r) { return M.bt_ptr[r + 1] - M.bt_ptr[r]; };
+  for (int64_t w0 = 0; w0 < nv; w0 += W) {
+    auto b = order.begin() + w0, e = order.begin() + std::min(nv, w0 + W);
+    std::sort(b, e, [&](int32_t x, int32_t y) {
+      if (alen(x) != alen(y)) return alen(x) > alen(y);
+      if (blen(x) != blen(y)) return blen(x) > blen(y);
+      return x < y;
+    });
+  }
+  const int64_t ns = (nv + 31) / 32;
+  M.sell_row.assign(ns * 32, -1);
+  M.sell_aoff.assign(ns + 1, 0);
+  M.sell_boff.assign(ns + 1, 0);
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    int la = 0, lb = 0;
+    for (int l = 0; l < 32 && sl * 32 + l < nv; ++l) {
+      const int32_t r = order[sl * 32 + l];
+      M.sell_row[sl * 32 + l] = r;
+      la = std::max(la, alen(r));
+      lb = std::max(lb, blen(r));
+    }
+    M.sell_aoff[sl + 1] = M.sell_aoff[sl] + int64_t(la) * 32;
+    M.sell_boff[sl + 1] = M.sell_boff[sl] + int64_t(lb) * 32;
+  }
+  M.sell_acol.assign(M.sell_aoff[ns], 0);
+  M.sell_asrc.assign(M.sell_aoff[ns], -1);
+  M.sell_bcol.assign(M.sell_boff[ns], 0);
+  M.sell_bsrc.assign(M.sell_boff[ns], -1);
+  for (int64_t sl = 0; sl < ns; ++sl)
+    for (int l = 0; l < 32; ++l) {
+      const int32_t r = M.sell_row[sl * 32 + l];
+      if (r < 0) continue;
+      for (int j = 0; j < alen(r); ++j) {
+        const int64_t slot = M.sell_aoff[sl] + int64_t(j) * 32 + l;
+        M.sell_acol[slot] = M.a_col[M.a_ptr[r] + j];
+        M.sell_asrc[slot] = M.a_ptr[r] + j;
+      }
+      for (int j = 0; j < blen(r); ++j) {
+        const int64_t slot = M.sell_boff[sl] + int64_t(j) * 32 + l;
+        M.sell_bcol[slot] = M.bt_col[M.bt_ptr[r] + j];
+        M.sell_bsrc[slot] = M.bt_ptr[r] + j;
+      }
+    }
+}
+
 void build_mesh(MeshHost& M, const gdsw_mesh* m) {
   M.nx = m->nx; M.ny = m->ny; M.nz = m->nz;
   M.h = m->h;
@@ -185,6 +239,51 @@ void build_mesh(MeshHost& M, const gdsw_mesh* m) {
       M.a_tpos[blk] = int32_t(it - M.a_col.begin());
     }
   for (int64_t I = 0; I < M.nv; ++I) GDSW_CHECK(M.a_diag[I] >= 0, GDSW_ERR_INVALID_ARG, "missing diagonal block");
+  // assembly units: for each upper block, the fluid elements holding both nodes
+  GDSW_CHECK(int64_t(M.fluid.size()) < (int64_t(1) << 22), GDSW_ERR_INVALID_ARG,
+             "too many fluid elements for the packed assembly units");
+  const int64_t nnzb = int64_t(M.a_col.size());
+  std::vector<int32_t> ucount(nnzb, 0);
+  auto units_of = [&](int64_t I, int32_t blk, uint32_t* out) {
+    int ii[3], jj[3];
+    M.coords(M.vnode[I], ii[0], ii[1], ii[2]);
+    M.coords(M.vnode[M.a_col[blk]], jj[0], jj[1], jj[2]);
+    const int nn[3] = {M.nx, M.ny, M.nz};
+    int e0[3], e1[3];
+    for (int d = 0; d < 3; ++d) {
+      const int lo = std::max(ii[d], jj[d]), hi = std::min(ii[d], jj[d]);
+      e0[d] = lo < 2 ? 0 : (lo - 1) / 2;
+      e1[d] = std::min(nn[d] - 1, hi / 2);
+    }
+    int cnt = 0;
+    for (int ez = e0[2]; ez <= e1[2]; ++ez)
+      for (int ey = e0[1]; ey <= e1[1]; ++ey)
+        for (int ex = e0[0]; ex <= e1[0]; ++ex) {
+          const int64_t e = ex + int64_t(M.nx) * (ey + int64_t(M.ny) * ez);
+          if (!M.mask[e]) continue;
+          if (out) {
+            const uint32_t a = uint32_t((ii[0] - 2 * ex) + 3 * (ii[1] - 2 * ey) + 9 * (ii[2] - 2 * ez));
+            const uint32_t b = uint32_t((jj[0] - 2 * ex) + 3 * (jj[1] - 2 * ey) + 9 * (jj[2] - 2 * ez));
+            out[cnt] = (uint32_t(M.felem[e]) << 10) | (a << 5) | b;
+          }
+          ++cnt;
+        }
+    return cnt;
+  };
+  parallel_for(M.nv, [&](int64_t I) {
+    for (int32_t blk = M.a_diag[I]; blk < M.a_ptr[I + 1]; ++blk) ucount[blk] = units_of(I, blk, nullptr);
+  });
+  M.asm_uoff.assign(nnzb + 1, 0);
+  for (int64_t q = 0; q < nnzb; ++q) M.asm_uoff[q + 1] = M.asm_uoff[q] + ucount[q];
+  GDSW_CHECK(int64_t(M.asm_uoff[nnzb]) < (int64_t(1) << 31), GDSW_ERR_INVALID_ARG, "too many assembly units");
+  M.asm_unit.resize(M.asm_uoff[nnzb]);
+  parallel_for(M.nv, [&](int64_t I) {
+    for (int32_t blk = M.a_diag[I]; blk < M.a_ptr[I + 1]; ++blk) units_of(I, blk, M.asm_unit.data() + M.asm_uoff[blk]);
+  });
+  M.asm_cta.assign(1, 0);
+  for (int64_t q = 0; q < nnzb; ++q)
+    if (M.asm_uoff[q + 1] - M.asm_uoff[M.asm_cta.back()] > 256) M.asm_cta.push_back(int32_t(q));
+  M.asm_cta.push_back(int32_t(nnzb));
   // BT entry (I, P) has the value of B entry (P, I)
   M.bt2b.resize(M.bt_col.size());
   for (int64_t I = 0; I < M.nv; ++I)
@@ -195,6 +294,7 @@ void build_mesh(MeshHost& M, const gdsw_mesh* m) {
       GDSW_CHECK(it != b1 && *it == int32_t(I), GDSW_ERR_INVALID_ARG, "asymmetric B pattern");
       M.bt2b[e] = int32_t(it - M.b_col.begin());
     }
+  build_sell(M);
 }
 
 // ------------------------------------------------------------------ slab layout

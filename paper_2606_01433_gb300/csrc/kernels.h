@@ -60,6 +60,7 @@ void launch_viscosity(gdsw_ctx* c, cudaStream_t s);
 void launch_assembly(gdsw_ctx* c, cudaStream_t s);
 void launch_lift(gdsw_ctx* c, double* b, cudaStream_t s);
 void launch_spmv(gdsw_ctx* c, const double* x, double* y, const double* b, cudaStream_t s);
+void launch_sell_fill(gdsw_ctx* c, bool with_bt, cudaStream_t s);
 void upload_tables(gdsw_ctx* c, cudaStream_t s);
 
 // schwarz.cu

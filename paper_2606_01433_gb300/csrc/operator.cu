@@ -165,83 +165,99 @@ __device__ void divergence_entry(int64_t P, int64_t J, const Geo& G, const uint8
 }
 
 // ------------------------------------------------------------------ a2: assembly
-// One warp per block row I; lanes take the blocks (I, J) with J >= I (the operator is
-// symmetric: the (J, I) block is the transpose, written through the transpose map).  The
-// reference gradients live in shared memory; the element sum runs in a fixed order.
+// On GB300 a warp-wide FP64 instruction holds the FP64 pipe for the same time whether 1 or 32
+// lanes are active, so the assembly is organised for uniform lanes: one thread per work unit
+// (an upper block (I, J >= I) and one fluid element holding both nodes), each unit exactly 27
+// Gauss points.  Per unit the thread accumulates
+//   O[c][d] = sum_q f_q dphi_b,c(q) dphi_a,d(q),   f_q = nu_q w_q (h/2)^3 (2/h)^2,
+// and the element's contribution to the block is tr(O) I + O for the symmetric form 2 nu D:D
+// (Section 3) and tr(O) I for the gradient form nu grad:grad (Section 2).  A CTA holds the
+// units of whole blocks (at most 256); each block sums its units' O in element order in
+// shared memory, then writes itself and, off the diagonal, its transpose (operator symmetric).
 struct SmemTables {
   double dphi[27][27][3];
-  double w[27];
+  double wsc[27];
 };
 
-__global__ void __launch_bounds__(256) k_assemble_A(const int32_t* __restrict__ a_ptr,
-                                                    const int32_t* __restrict__ a_col,
-                                                    const int32_t* __restrict__ a_diag,
+__global__ void __launch_bounds__(256) k_assemble_A(const int32_t* __restrict__ asm_cta,
+                                                    const int32_t* __restrict__ asm_uoff,
+                                                    const uint32_t* __restrict__ asm_unit,
                                                     const int32_t* __restrict__ a_tpos,
-                                                    const int32_t* __restrict__ vnode, int64_t nv, Geo G,
-                                                    const uint8_t* __restrict__ mask, const int32_t* __restrict__ felem,
                                                     const double* __restrict__ nu, const RefTables* __restrict__ T,
-                                                    int form, double* __restrict__ val) {
+                                                    double sc, int form, double* __restrict__ val) {
   __shared__ SmemTables st;
+  __shared__ double part[256][9];
   {
     const double* src = &T->dphi[0][0][0];
     double* dst = &st.dphi[0][0][0];
     for (int e = threadIdx.x; e < 27 * 27 * 3; e += blockDim.x) dst[e] = src[e];
-    if (threadIdx.x < 27) st.w[threadIdx.x] = T->w[threadIdx.x];
+    if (threadIdx.x < 27) st.wsc[threadIdx.x] = T->w[threadIdx.x] * sc;
   }
   __syncthreads();
-  const int64_t I = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (I >= nv) return;
-  const int64_t nodeI = vnode[I];
-  int ii, ij, ik;
-  node_ijk(nodeI, G, ii, ij, ik);
-  const double sc = 0.5 * G.h;  // (h/2)^3 * (2/h)^2
-  for (int blk = a_diag[I] + lane; blk < a_ptr[I + 1]; blk += 32) {
-    int ji, jj, jk;
-    node_ijk(vnode[a_col[blk]], G, ji, jj, jk);
+  const int blk0 = asm_cta[blockIdx.x], blk1 = asm_cta[blockIdx.x + 1];
+  const int u0 = asm_uoff[blk0], u1 = asm_uoff[blk1];
+  const int u = u0 + int(threadIdx.x);
+  double O[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) O[c] = 0.0;
+  if (u < u1) {
+    const uint32_t w = asm_unit[u];
+    const int fe = int(w >> 10), a = int((w >> 5) & 31u), b = int(w & 31u);
+    const double* nq = nu + int64_t(fe) * 27;
+    if (form == GDSW_FORM_SYMMETRIC) {
+      for (int q = 0; q < 27; ++q) {
+        const double f = __ldg(nq + q) * st.wsc[q];
+        const double* da = st.dphi[q][a];
+        const double* db = st.dphi[q][b];
+        const double fa0 = f * da[0], fa1 = f * da[1], fa2 = f * da[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double dbc = db[c];
+          O[c * 3 + 0] = fma(dbc, fa0, O[c * 3 + 0]);
+          O[c * 3 + 1] = fma(dbc, fa1, O[c * 3 + 1]);
+          O[c * 3 + 2] = fma(dbc, fa2, O[c * 3 + 2]);
+        }
+      }
+    } else {  // only the trace is needed
+      for (int q = 0; q < 27; ++q) {
+        const double f = __ldg(nq + q) * st.wsc[q];
+        const double* da = st.dphi[q][a];
+        const double* db = st.dphi[q][b];
+        O[0] = fma(f * da[0], db[0], O[0]);
+        O[4] = fma(f * da[1], db[1], O[4]);
+        O[8] = fma(f * da[2], db[2], O[8]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) part[threadIdx.x][c] = O[c];
+  __syncthreads();
+  for (int blk = blk0 + int(threadIdx.x); blk < blk1; blk += blockDim.x) {
+    const int v0 = asm_uoff[blk], v1 = asm_uoff[blk + 1];
+    if (v1 == v0) continue;  // a lower block: written as the transpose of its upper partner
+    double S[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) S[c] = part[v0 - u0][c];
+    for (int v = v0 + 1; v < v1; ++v)
+#pragma unroll
+      for (int c = 0; c < 9; ++c) S[c] += part[v - u0][c];
+    const double tr = S[0] + S[4] + S[8];
     double out[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) out[c] = 0.0;
-    int e0x, e0y, e0z;
-    int nxr = shared_range(ii, ji, G.nx, e0x), nyr = shared_range(ij, jj, G.ny, e0y),
-        nzr = shared_range(ik, jk, G.nz, e0z);
-    for (int cz = 0; cz < nzr; ++cz)
-      for (int cy = 0; cy < nyr; ++cy)
-        for (int cx = 0; cx < nxr; ++cx) {
-          const int ex = e0x + cx, ey = e0y + cy, ez = e0z + cz;
-          const int64_t e = ex + int64_t(G.nx) * (ey + int64_t(G.ny) * ez);
-          if (!mask[e]) continue;
-          const double* nq = nu + int64_t(felem[e]) * 27;
-          const int a = (ii - 2 * ex) + 3 * (ij - 2 * ey) + 9 * (ik - 2 * ez);
-          const int b = (ji - 2 * ex) + 3 * (jj - 2 * ey) + 9 * (jk - 2 * ez);
-          for (int q = 0; q < 27; ++q) {
-            const double* da = st.dphi[q][a];
-            const double* db = st.dphi[q][b];
-            const double f = __ldg(nq + q) * st.w[q] * sc;
-            const double g = f * (da[0] * db[0] + da[1] * db[1] + da[2] * db[2]);
-            out[0] += g;
-            out[4] += g;
-            out[8] += g;
-            if (form == GDSW_FORM_SYMMETRIC) {
+    for (int c = 0; c < 9; ++c) out[c] = form == GDSW_FORM_SYMMETRIC ? S[c] : 0.0;
+    out[0] += tr;
+    out[4] += tr;
+    out[8] += tr;
+    double* vp = val + int64_t(blk) * 9;
 #pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const double fdc = f * db[c];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) out[c * 3 + d] = fma(fdc, da[d], out[c * 3 + d]);
-              }
-            }
-          }
-        }
-    double* v = val + int64_t(blk) * 9;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) v[c] = out[c];
+    for (int c = 0; c < 9; ++c) vp[c] = out[c];
     const int tb = a_tpos[blk];
     if (tb != blk) {
-      double* w = val + int64_t(tb) * 9;
+      double* wp = val + int64_t(tb) * 9;
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) w[d * 3 + c] = out[c * 3 + d];
+        for (int d = 0; d < 3; ++d) wp[d * 3 + c] = out[c * 3 + d];
     }
   }
 }
@@ -316,45 +332,73 @@ __global__ void __launch_bounds__(256) k_lift(const int32_t* __restrict__ rows, 
 }
 
 // ------------------------------------------------------------------ a3: SpMV
-// Velocity rows: one warp per node row; lanes 3g+c (g < 10) own output component c and
-// walk the row's blocks g, g+10, ...  Pressure rows: one warp per row streaming the
-// contiguous 3-vectors.  FP64 throughout; y = A x or y = b - A x.
-__global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_col,
-                                              const double* __restrict__ aval, const int32_t* __restrict__ bt_ptr,
-                                              const int32_t* __restrict__ bt_col, const double* __restrict__ btval,
+// Velocity rows from the sliced copy: one warp per slice of 32 rows, lane = row, every lane
+// running the same number of blocks (the slice's longest row; shorter rows are zero padded),
+// so each FP64 warp instruction has all 32 lanes busy.  Slot group g (32 slots, one per lane)
+// keeps its 3x3 blocks component-major: value m of lane l at g * 288 + m * 32 + l (B^T: at
+// g * 96 + m * 32 + l), so every value load is one coalesced 256-byte access.
+// Pressure rows: one warp per row streaming the contiguous 3-vectors of B.  FP64 throughout;
+// y = A x or y = b - A x.
+__global__ void k_sell_fill(const int32_t* __restrict__ src, int64_t nslots, int m, const double* __restrict__ from,
+                            double* __restrict__ to) {
+  const int64_t slot = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (slot >= nslots) return;
+  const int64_t g = slot >> 5;
+  const int lane = int(slot & 31);
+  const int32_t e = src[slot];
+  for (int c = 0; c < m; ++c) to[g * (32 * m) + c * 32 + lane] = e >= 0 ? from[int64_t(e) * m + c] : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ sell_row, const int64_t* __restrict__ aoff,
+                                              const int32_t* __restrict__ acol, const double* __restrict__ aval,
+                                              const int64_t* __restrict__ boff, const int32_t* __restrict__ bcol,
+                                              const double* __restrict__ btval, int64_t nslices,
                                               const int32_t* __restrict__ b_ptr, const int32_t* __restrict__ b_col,
                                               const double* __restrict__ bval, int64_t nv, int64_t np,
                                               const double* __restrict__ x, double* __restrict__ y,
                                               const double* __restrict__ rhs) {
-  __shared__ double red[8][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row = blockIdx.x * int64_t(8) + warp;
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
   const int64_t nu = 3 * nv;
-  if (row < nv) {
-    const int g = lane / 3, c = lane - 3 * g;
-    double acc = 0.0;
-    if (lane < 30) {
-      const int b0 = a_ptr[row], b1 = a_ptr[row + 1];
-      for (int blk = b0 + g; blk < b1; blk += 10) {
-        const double* v = aval + int64_t(blk) * 9 + c * 3;
-        const double* xj = x + 3 * int64_t(__ldg(a_col + blk));
-        acc = fma(__ldcs(v + 0), __ldg(xj + 0), acc);
-        acc = fma(__ldcs(v + 1), __ldg(xj + 1), acc);
-        acc = fma(__ldcs(v + 2), __ldg(xj + 2), acc);
+  if (wid < nslices) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    const int64_t g0 = aoff[wid] >> 5, g1 = aoff[wid + 1] >> 5;
+    for (int64_t g = g0; g < g1; ++g) {
+      const int64_t j = __ldg(acol + g * 32 + lane);
+      const double x0 = __ldg(x + 3 * j), x1 = __ldg(x + 3 * j + 1), x2 = __ldg(x + 3 * j + 2);
+      const double* v = aval + g * 288 + lane;
+      a0 = fma(__ldcs(v + 0), x0, a0);
+      a0 = fma(__ldcs(v + 32), x1, a0);
+      a0 = fma(__ldcs(v + 64), x2, a0);
+      a1 = fma(__ldcs(v + 96), x0, a1);
+      a1 = fma(__ldcs(v + 128), x1, a1);
+      a1 = fma(__ldcs(v + 160), x2, a1);
+      a2 = fma(__ldcs(v + 192), x0, a2);
+      a2 = fma(__ldcs(v + 224), x1, a2);
+      a2 = fma(__ldcs(v + 256), x2, a2);
+    }
+    const int64_t h0 = boff[wid] >> 5, h1 = boff[wid + 1] >> 5;
+    for (int64_t g = h0; g < h1; ++g) {
+      const double xp = __ldg(x + nu + __ldg(bcol + g * 32 + lane));
+      const double* v = btval + g * 96 + lane;
+      a0 = fma(__ldcs(v + 0), xp, a0);
+      a1 = fma(__ldcs(v + 32), xp, a1);
+      a2 = fma(__ldcs(v + 64), xp, a2);
+    }
+    const int32_t row = sell_row[wid * 32 + lane];
+    if (row >= 0) {
+      const int64_t o = 3 * int64_t(row);
+      if (rhs) {
+        a0 = rhs[o] - a0;
+        a1 = rhs[o + 1] - a1;
+        a2 = rhs[o + 2] - a2;
       }
-      const int e0 = bt_ptr[row], e1 = bt_ptr[row + 1];
-      for (int e = e0 + g; e < e1; e += 10) acc = fma(__ldcs(btval + int64_t(e) * 3 + c), __ldg(x + nu + bt_col[e]), acc);
+      y[o] = a0;
+      y[o + 1] = a1;
+      y[o + 2] = a2;
     }
-    red[warp][lane] = acc;
-    __syncwarp();
-    if (lane < 3) {
-      double s = 0.0;
-      for (int q = lane; q < 30; q += 3) s += red[warp][q];
-      double out = rhs ? rhs[3 * row + lane] - s : s;
-      y[3 * row + lane] = out;
-    }
-  } else if (row < nv + np) {
-    const int64_t P = row - nv;
+  } else if (wid < nslices + np) {
+    const int64_t P = wid - nslices;
     const int64_t f0 = int64_t(b_ptr[P]) * 3, f1 = int64_t(b_ptr[P + 1]) * 3;
     double acc = 0.0;
     for (int64_t f = f0 + lane; f < f1; f += 32) {
@@ -397,14 +441,19 @@ void launch_viscosity(gdsw_ctx* c, cudaStream_t s) {
 
 void launch_assembly(gdsw_ctx* c, cudaStream_t s) {
   const auto* T = static_cast<RefTables*>(c->d_tables);
-  int64_t nv = c->mesh.nv, np = c->mesh.np;
+  const int64_t np = c->mesh.np;
   double* aval = c->d_val;
   double* btval = c->d_val + 9 * c->nnzb;
   double* bval = btval + 3 * c->nbt;
-  k_assemble_A<<<int((nv + 7) / 8), 256, 0, s>>>(c->d_a_ptr, c->d_a_col, c->d_a_diag, c->d_a_tpos, c->d_vnode, nv,
-                                                 geo(c), c->d_mask, c->d_felem, c->d_nu, T, c->form, aval);
+  const int ncta = int(c->mesh.asm_cta.size()) - 1;
+  if (ncta > 0)
+    k_assemble_A<<<ncta, 256, 0, s>>>(c->d_asm_cta, c->d_asm_uoff, c->d_asm_unit, c->d_a_tpos, c->d_nu, T,
+                                      0.5 * c->mesh.h, c->form, aval);
   check_launch("k_assemble_A");
-  if (c->b_assembled) return;  // B = -(q, div u) depends on the mesh only, not on the viscosity
+  if (c->b_assembled) {  // B = -(q, div u) depends on the mesh only, not on the viscosity
+    launch_sell_fill(c, false, s);
+    return;
+  }
   k_assemble_B<<<int((np + 7) / 8), 256, 0, s>>>(c->d_b_ptr, c->d_b_col, c->d_pnode, c->d_vnode, np, geo(c),
                                                  c->d_mask, T, bval);
   check_launch("k_assemble_B");
@@ -412,6 +461,7 @@ void launch_assembly(gdsw_ctx* c, cudaStream_t s) {
     k_copy_bt<<<int((c->nbt + 255) / 256), 256, 0, s>>>(c->d_bt2b, c->nbt, bval, btval);
     check_launch("k_copy_bt");
   }
+  launch_sell_fill(c, true, s);
   c->b_assembled = true;
 }
 
@@ -428,14 +478,29 @@ void launch_lift(gdsw_ctx* c, double* b, cudaStream_t s) {
 }
 
 void launch_spmv(gdsw_ctx* c, const double* x, double* y, const double* rhs, cudaStream_t s) {
-  int64_t nv = c->mesh.nv, np = c->mesh.np;
-  const double* aval = c->d_val;
-  const double* btval = c->d_val + 9 * c->nnzb;
-  const double* bval = btval + 3 * c->nbt;
-  int64_t rows = nv + np;
-  k_spmv<<<int((rows + 7) / 8), 256, 0, s>>>(c->d_a_ptr, c->d_a_col, aval, c->d_bt_ptr, c->d_bt_col, btval, c->d_b_ptr,
-                                             c->d_b_col, bval, nv, np, x, y, rhs);
+  const int64_t nv = c->mesh.nv, np = c->mesh.np;
+  const double* bval = c->d_val + 9 * c->nnzb + 3 * c->nbt;
+  const int64_t ns = c->n_sell_slices;
+  const int64_t warps = ns + np;
+  k_spmv<<<int((warps + 7) / 8), 256, 0, s>>>(c->d_sell_row, c->d_sell_aoff, c->d_sell_acol, c->d_sell_aval,
+                                              c->d_sell_boff, c->d_sell_bcol, c->d_sell_btval, ns, c->d_b_ptr,
+                                              c->d_b_col, bval, nv, np, x, y, rhs);
   check_launch("k_spmv");
+}
+
+// refresh the sliced copy of A (after every assembly) and of B^T (once B is assembled)
+void launch_sell_fill(gdsw_ctx* c, bool with_bt, cudaStream_t s) {
+  const MeshHost& M = c->mesh;
+  const int64_t na = int64_t(M.sell_acol.size()), nb = int64_t(M.sell_bcol.size());
+  if (na > 0) {
+    k_sell_fill<<<int((na + 255) / 256), 256, 0, s>>>(c->d_sell_asrc, na, 9, c->d_val, c->d_sell_aval);
+    check_launch("k_sell_fill");
+  }
+  if (with_bt && nb > 0) {
+    k_sell_fill<<<int((nb + 255) / 256), 256, 0, s>>>(c->d_sell_bsrc, nb, 3, c->d_val + 9 * c->nnzb,
+                                                      c->d_sell_btval);
+    check_launch("k_sell_fill");
+  }
 }
 
 }  // namespace gdsw
