@@ -529,27 +529,145 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTaskP* __restrict__ task
   }
 }
 
+// ------------------------------------------------------------------ FP32 GEMM tiles
+// 128 x 128 outputs per CTA of 256 threads, 8 x 8 per thread (rows ty*4 + {0..3} and
+// 64 + ty*4 + {0..3}, columns likewise with tx), K in steps of 16 staged transposed in
+// shared memory; the next step's global loads are held in registers while the current
+// step is multiplied (one barrier per step).  op(A)(r, k) = ta ? A[k*lda + r] : A[r*lda + k],
+// op(B)(k, c) = tb ? B[c*ldb + k] : B[k*ldb + c].
+struct GemmOp {
+  const float* p;
+  int ld, trans;
+};
+
+__device__ __forceinline__ void gemm_fetch(const GemmOp& A, const GemmOp& B, int M, int N, int K, int m0, int n0,
+                                           int k0, float (&ra)[8], float (&rb)[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int e = threadIdx.x + 256 * i;
+    int m, k;
+    if (A.trans) { k = e >> 7; m = e & 127; } else { m = e >> 4; k = e & 15; }
+    const int gm = m0 + m, gk = k0 + k;
+    ra[i] = (gm < M && gk < K) ? (A.trans ? A.p[int64_t(gk) * A.ld + gm] : A.p[int64_t(gm) * A.ld + gk]) : 0.f;
+    int c, kk;
+    if (B.trans) { c = e >> 4; kk = e & 15; } else { kk = e >> 7; c = e & 127; }
+    const int gc = n0 + c, gk2 = k0 + kk;
+    rb[i] = (gc < N && gk2 < K) ? (B.trans ? B.p[int64_t(gc) * B.ld + gk2] : B.p[int64_t(gk2) * B.ld + gc]) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void gemm_stash(const GemmOp& A, const GemmOp& B, const float (&ra)[8],
+                                           const float (&rb)[8], float (*As)[132], float (*Bs)[132]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int e = threadIdx.x + 256 * i;
+    if (A.trans) As[e >> 7][e & 127] = ra[i]; else As[e & 15][e >> 4] = ra[i];
+    if (B.trans) Bs[e & 15][e >> 4] = rb[i]; else Bs[e >> 7][e & 127] = rb[i];
+  }
+}
+
+// acc = op(A)[m0:, :K] op(B)[:K, n0:] for the CTA's 128 x 128 tile
+__device__ __forceinline__ void gemm_tile_f32(const GemmOp& A, const GemmOp& B, int M, int N, int K, int m0, int n0,
+                                              float (*As)[16][132], float (*Bs)[16][132], float (&acc)[8][8]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  float ra[8], rb[8];
+  gemm_fetch(A, B, M, N, K, m0, n0, 0, ra, rb);
+  gemm_stash(A, B, ra, rb, As[0], Bs[0]);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const bool more = k0 + 16 < K;
+    if (more) gemm_fetch(A, B, M, N, K, m0, n0, k0 + 16, ra, rb);
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) gemm_stash(A, B, ra, rb, As[buf ^ 1], Bs[buf ^ 1]);
+    __syncthreads();
+    buf ^= 1;
+  }
+}
+
+__device__ __forceinline__ int gemm_row(int i) { return i < 4 ? (threadIdx.x >> 4) * 4 + i : 64 + (threadIdx.x >> 4) * 4 + i - 4; }
+__device__ __forceinline__ int gemm_col(int j) { return j < 4 ? (threadIdx.x & 15) * 4 + j : 64 + (threadIdx.x & 15) * 4 + j - 4; }
+
+__global__ void __launch_bounds__(256, 2) k_gemm_f32(const GemmTaskP* __restrict__ tasks,
+                                                  const int32_t* __restrict__ tile_task,
+                                                  const int32_t* __restrict__ tile_id) {
+  __shared__ __align__(16) float As[2][16][132];
+  __shared__ __align__(16) float Bs[2][16][132];
+  const GemmTaskP t = tasks[tile_task[blockIdx.x]];
+  const int tiles_n = (t.N + 127) / 128;
+  const int m0 = (tile_id[blockIdx.x] / tiles_n) * 128, n0 = (tile_id[blockIdx.x] % tiles_n) * 128;
+  const GemmOp A{static_cast<const float*>(t.a), t.lda, t.ta};
+  const GemmOp B{static_cast<const float*>(t.b), t.ldb, t.tb};
+  float acc[8][8];
+  gemm_tile_f32(A, B, t.M, t.N, t.K, m0, n0, As, Bs, acc);
+  float* C = static_cast<float*>(t.c);
+  const float alpha = float(t.alpha), beta = float(t.beta);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + gemm_row(i);
+    if (gm >= t.M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + gemm_col(j);
+      if (gn >= t.N) continue;
+      float* cp = C + int64_t(gm) * t.ldc + gn;
+      float v = alpha * acc[i][j];
+      if (beta != 0.f) v = fmaf(beta, *cp, v);
+      *cp = v;
+    }
+  }
+}
+
 template <typename T>
 void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s) {
   if (tasks.empty()) return;
-  std::vector<int32_t> tt, ti;
+  std::vector<int32_t> tt, ti, bt, bi;  // 64-tiles (k_gemm), 128-tiles (k_gemm_f32)
   for (size_t q = 0; q < tasks.size(); ++q) {
     const auto& t = tasks[q];
     if (t.M <= 0 || t.N <= 0) continue;
+    if (sizeof(T) == 4 && t.M >= 96 && t.N >= 96) {
+      int nt = ((t.M + 127) / 128) * ((t.N + 127) / 128);
+      for (int i = 0; i < nt; ++i) {
+        bt.push_back(int32_t(q));
+        bi.push_back(i);
+      }
+      continue;
+    }
     int nt = ((t.M + 63) / 64) * ((t.N + 63) / 64);
     for (int i = 0; i < nt; ++i) {
       tt.push_back(int32_t(q));
       ti.push_back(i);
     }
   }
-  if (tt.empty()) return;
+  if (tt.empty() && bt.empty()) return;
   GemmTaskP* d_t = tmp.upload(tasks, s);
-  int32_t* d_tt = tmp.upload(tt, s);
-  int32_t* d_ti = tmp.upload(ti, s);
-  for (size_t off = 0; off < tt.size(); off += 1 << 30) {
-    int nb = int(std::min<size_t>(tt.size() - off, size_t(1) << 30));
-    k_gemm<T><<<nb, 256, 0, s>>>(d_t, d_tt + off, d_ti + off);
+  if (!tt.empty()) {
+    int32_t* d_tt = tmp.upload(tt, s);
+    int32_t* d_ti = tmp.upload(ti, s);
+    k_gemm<T><<<int(tt.size()), 256, 0, s>>>(d_t, d_tt, d_ti);
     check_launch("k_gemm");
+  }
+  if (!bt.empty()) {
+    int32_t* d_bt = tmp.upload(bt, s);
+    int32_t* d_bi = tmp.upload(bi, s);
+    k_gemm_f32<<<int(bt.size()), 256, 0, s>>>(d_t, d_bt, d_bi);
+    check_launch("k_gemm_f32");
   }
 }
 template void run_gemm<double>(DevArena&, const std::vector<GemmTaskP>&, cudaStream_t);
@@ -625,6 +743,114 @@ __global__ void __launch_bounds__(256) k_gj_panel(const InvTaskP* tasks, int kb,
       T l = pr[j] / d;
       pr[j] = l;
       for (int c = j + 1; c < w; ++c) pr[c] -= l * prow[c];
+    }
+    __syncthreads();
+  }
+}
+
+// Pivot choice for one panel, faster form: 1024 threads; the first RS rows of the panel copy
+// live in shared memory (row stride NB + 1), the rest in the global scratch; the column
+// maximum is found with warp shuffles (largest magnitude, smallest row on ties -- the same
+// pivots as the tree reduction above), and the rank-1 elimination runs one warp per row,
+// lane = column.  Only the pivot rows are used afterwards.
+template <typename T>
+__device__ __forceinline__ T& panel_at(T* Ps, T* Pg, int RS, int r, int c) {
+  return r < RS ? Ps[r * (GJ_NB + 1) + c] : Pg[int64_t(r) * GJ_NB + c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gj_panel_fast(const InvTaskP* tasks, int kb, T* scratch, int64_t scr_stride,
+                                                       int32_t* piv, int64_t piv_stride, double* minpiv, int RS) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ps = reinterpret_cast<T*>(smem_raw);
+  __shared__ double wv[32];
+  __shared__ int wi[32];
+  __shared__ int s_p;
+  __shared__ T prow[GJ_NB];
+  const InvTaskP t = tasks[blockIdx.x];
+  if (kb >= t.n) return;
+  const T* A = static_cast<const T*>(t.a);
+  const int w = min(GJ_NB, t.n - kb), rows = t.n - kb;
+  T* Pg = scratch + int64_t(t.id) * scr_stride;
+  int32_t* pv = piv + int64_t(t.id) * piv_stride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < rows * w; e += blockDim.x) {
+    const int r = e / w, c = e - r * w;
+    panel_at(Ps, Pg, RS, r, c) = A[int64_t(kb + r) * t.ld + kb + c];
+  }
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    double best = -1.0;
+    int bi = rows;
+    for (int r = j + threadIdx.x; r < rows; r += blockDim.x) {
+      const double a = fabs(double(panel_at(Ps, Pg, RS, r, j)));
+      if (a > best) { best = a; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { wv[warp] = best; wi[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      const int nw = int(blockDim.x >> 5);
+      double b = lane < nw ? wv[lane] : -2.0;
+      int i = lane < nw ? wi[lane] : rows;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, b, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ob > b || (ob == b && oi < i)) { b = ob; i = oi; }
+      }
+      if (lane == 0) {
+        s_p = i;
+        pv[kb + j] = kb + i;
+        if (b < minpiv[t.id]) minpiv[t.id] = b;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j && threadIdx.x < w) {
+      T& x = panel_at(Ps, Pg, RS, j, threadIdx.x);
+      T& y = panel_at(Ps, Pg, RS, p, threadIdx.x);
+      const T tmp = x;
+      x = y;
+      y = tmp;
+    }
+    __syncthreads();
+    if (threadIdx.x < w) prow[threadIdx.x] = panel_at(Ps, Pg, RS, j, threadIdx.x);
+    __syncthreads();
+    T d = prow[j];
+    if (d == T(0)) d = T(1);  // singular: recorded through minpiv, keep the numbers finite
+    const int nw = int(blockDim.x >> 5);
+    const T pl = lane < w ? prow[lane] : T(0);
+    int r = j + 1 + warp;
+    for (; r + 3 * nw < rows; r += 4 * nw) {  // four rows of this warp in flight
+      T l[4], v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        l[q] = panel_at(Ps, Pg, RS, r + q * nw, j);
+        v[q] = lane < w ? panel_at(Ps, Pg, RS, r + q * nw, lane) : T(0);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T lq = l[q] / d;
+        if (lane == j)
+          panel_at(Ps, Pg, RS, r + q * nw, j) = lq;
+        else if (lane > j && lane < w)
+          panel_at(Ps, Pg, RS, r + q * nw, lane) = v[q] - lq * pl;
+      }
+    }
+    for (; r < rows; r += nw) {
+      const T l = panel_at(Ps, Pg, RS, r, j) / d;
+      __syncwarp();
+      if (lane == j)
+        panel_at(Ps, Pg, RS, r, j) = l;
+      else if (lane > j && lane < w)
+        panel_at(Ps, Pg, RS, r, lane) -= l * pl;
     }
     __syncthreads();
   }
@@ -706,7 +932,7 @@ __global__ void k_gj_fe(const InvTaskP* tasks, int kb, const T* dinv, T* Fp, T* 
     T s = T(0);
 #pragma unroll
     for (int q = 0; q < GJ_NB; ++q) s = fma(Di[r * GJ_NB + q], col[q], s);
-    F[int64_t(r) * t.n + idx] = s;
+    F[int64_t(r) * t.ld + idx] = s;
   }
   // row idx of E
 #pragma unroll
@@ -735,7 +961,7 @@ __global__ void __launch_bounds__(256) k_gj_update(const InvTaskP* tasks, const 
     Es[r][q] = (gi < t.n) ? Ee[int64_t(gi) * GJ_NB + q] : T(0);
     int q2 = e / 64, c = e % 64;
     int gj = tj * 64 + c;
-    Fs[q2][c] = (gj < t.n && q2 < w) ? F[int64_t(q2) * t.n + gj] : T(0);
+    Fs[q2][c] = (gj < t.n && q2 < w) ? F[int64_t(q2) * t.ld + gj] : T(0);
   }
   for (int e = threadIdx.x; e < GJ_NB * GJ_NB; e += 256) Ds[e / GJ_NB][e % GJ_NB] = Di[e];
   __syncthreads();
@@ -764,6 +990,106 @@ __global__ void __launch_bounds__(256) k_gj_update(const InvTaskP* tasks, const 
         for (int q = 0; q < w; ++q) s = fma(-Es[li][q], Fs[q][lj], s);
         *ap = s;
       }
+    }
+  }
+}
+
+// FP32 rank-NB sweep on 128 x 128 tiles.  The sweep is bound by the read-modify-write of A,
+// so every global load of a tile is issued at once: the A tile and F = D^-1 A[P, :] go to
+// shared memory with cp.async, E = A[:, P] (taken before the sweep) is staged transposed; one
+// barrier, then the 8 x 8 register-tiled product E F and the epilogue with the four cases of
+// the block Gauss-Jordan step (pivot block D^-1, pivot rows F, pivot columns -E D^-1, the rest
+// A - E F).  F has the leading dimension of the matrix, so every row starts 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+constexpr int GJU_LD = 132;  // shared row stride (floats) of the update tiles
+constexpr size_t GJU_SMEM = size_t(128 + 32 + 32) * GJU_LD * sizeof(float);
+
+__global__ void __launch_bounds__(256, 2) k_gj_update_f32(const InvTaskP* __restrict__ tasks,
+                                                          const int32_t* __restrict__ tile_task,
+                                                          const int32_t* __restrict__ tile_id, int kb,
+                                                          const float* __restrict__ dinv, const float* __restrict__ Fp,
+                                                          const float* __restrict__ E, int64_t stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Cs = reinterpret_cast<float*>(smem_raw);  // 128 x GJU_LD
+  float* Es = Cs + 128 * GJU_LD;                   // 32 x GJU_LD, Es[k][m] = E[m0 + m][k]
+  float* Fs = Es + 32 * GJU_LD;                    // 32 x GJU_LD, Fs[k][c] = F[k][n0 + c]
+  __shared__ float Ds[GJ_NB][GJ_NB + 1];
+  const InvTaskP t = tasks[tile_task[blockIdx.x]];
+  if (kb >= t.n) return;
+  const int w = min(GJ_NB, t.n - kb);
+  const int tiles = (t.n + 127) / 128;
+  const int m0 = (tile_id[blockIdx.x] / tiles) * 128, n0 = (tile_id[blockIdx.x] % tiles) * 128;
+  const float* Di = dinv + int64_t(t.id) * GJ_NB * GJ_NB;
+  const float* F = Fp + int64_t(t.id) * stride;
+  const float* Ee = E + int64_t(t.id) * stride;
+  float* Am = static_cast<float*>(t.a);
+  const int nch = min(32, (t.ld - n0) / 4);  // 16-byte chunks of a tile row inside the padded row
+  for (int e = threadIdx.x; e < 128 * 32; e += 256) {  // A tile
+    const int r = e >> 5, ch = e & 31;
+    if (m0 + r < t.n && ch < nch) cp_async16(Cs + r * GJU_LD + ch * 4, Am + int64_t(m0 + r) * t.ld + n0 + ch * 4);
+  }
+  for (int e = threadIdx.x; e < 32 * 32; e += 256) {  // F tile
+    const int k = e >> 5, ch = e & 31;
+    if (k < w && ch < nch) cp_async16(Fs + k * GJU_LD + ch * 4, F + int64_t(k) * t.ld + n0 + ch * 4);
+  }
+  for (int e = threadIdx.x; e < 128 * 8; e += 256) {  // E tile, transposed
+    const int r = e >> 3, q = (e & 7) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m0 + r < t.n) v = *reinterpret_cast<const float4*>(Ee + int64_t(m0 + r) * GJ_NB + q);
+    Es[(q + 0) * GJU_LD + r] = v.x;
+    Es[(q + 1) * GJU_LD + r] = v.y;
+    Es[(q + 2) * GJU_LD + r] = v.z;
+    Es[(q + 3) * GJU_LD + r] = v.w;
+  }
+  for (int e = threadIdx.x; e < GJ_NB * GJ_NB; e += 256) Ds[e / GJ_NB][e % GJ_NB] = Di[e];
+  cp_async_wait_all();
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int k = 0; k < w; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(Es + k * GJU_LD + ty * 4);
+    const float4 a1 = *reinterpret_cast<const float4*>(Es + k * GJU_LD + 64 + ty * 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(Fs + k * GJU_LD + tx * 4);
+    const float4 b1 = *reinterpret_cast<const float4*>(Fs + k * GJU_LD + 64 + tx * 4);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int li = gemm_row(i), gi = m0 + li;
+    if (gi >= t.n) continue;
+    const bool pi = gi >= kb && gi < kb + w;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int lj = gemm_col(j), gj = n0 + lj;
+      if (gj >= t.n) continue;
+      const bool pj = gj >= kb && gj < kb + w;
+      float v;
+      if (pi && pj) {
+        v = Ds[gi - kb][gj - kb];
+      } else if (pi) {
+        v = Fs[(gi - kb) * GJU_LD + lj];
+      } else if (pj) {
+        float sum = 0.f;
+        for (int q = 0; q < w; ++q) sum = fmaf(Es[q * GJU_LD + li], Ds[q][gj - kb], sum);
+        v = -sum;
+      } else {
+        v = Cs[li * GJU_LD + lj] - acc[i][j];
+      }
+      Am[int64_t(gi) * t.ld + gj] = v;
     }
   }
 }
@@ -808,7 +1134,10 @@ void run_inverse(DevArena& tmp, const std::vector<InvTaskP>& tasks_in, std::vect
   if (tasks.empty()) return;
   const int nt = int(tasks.size());
   const int64_t nq = int64_t(tasks_in.size());
-  const int64_t stride = int64_t(nmax) * GJ_NB;
+  int ldmax = 8;
+  for (const InvTaskP& t : tasks) ldmax = std::max(ldmax, t.ld);
+  // F rows have the matrices' leading dimension
+  const int64_t stride = std::max<int64_t>(pad8(nmax), ldmax) * GJ_NB;
   T* scratch = tmp.alloc<T>(size_t(nq) * stride);
   T* Fp = tmp.alloc<T>(size_t(nq) * stride);
   T* E = tmp.alloc<T>(size_t(nq) * stride);
@@ -817,9 +1146,10 @@ void run_inverse(DevArena& tmp, const std::vector<InvTaskP>& tasks_in, std::vect
   double* d_min = tmp.alloc<double>(nq);
   k_fill_d<<<int((nq + 255) / 256), 256, 0, s>>>(d_min, DBL_MAX, nq);
   InvTaskP* d_tasks = tmp.upload(tasks, s);
+  const int TE = sizeof(T) == 4 ? 128 : 64;  // update tile edge
   std::vector<int32_t> tt, ti;
   for (int q = 0; q < nt; ++q) {
-    int tl = (tasks[q].n + 63) / 64;
+    int tl = (tasks[q].n + TE - 1) / TE;
     for (int i = 0; i < tl * tl; ++i) {
       tt.push_back(q);
       ti.push_back(i);
@@ -828,12 +1158,21 @@ void run_inverse(DevArena& tmp, const std::vector<InvTaskP>& tasks_in, std::vect
   int32_t* d_tt = tmp.upload(tt, s);
   int32_t* d_ti = tmp.upload(ti, s);
   dim3 gcol((nmax + 255) / 256, nt);
+  const size_t panel_smem = size_t(200) * 1024;
+  const int panel_rs = int(panel_smem / ((GJ_NB + 1) * sizeof(T)));
+  GDSW_CUDA(cudaFuncSetAttribute(k_gj_panel_fast<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(panel_smem)));
+  GDSW_CUDA(cudaFuncSetAttribute(k_gj_update_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(GJU_SMEM)));
   for (int kb = 0; kb < nmax; kb += GJ_NB) {
-    k_gj_panel<T><<<nt, 256, 0, s>>>(d_tasks, kb, scratch, stride, piv, nmax, d_min);
+    k_gj_panel_fast<T><<<nt, 1024, panel_smem, s>>>(d_tasks, kb, scratch, stride, piv, nmax, d_min, panel_rs);
     k_gj_swap<T><<<gcol, 256, 0, s>>>(d_tasks, kb, piv, nmax);
     k_gj_dinv<T><<<nt, 256, 0, s>>>(d_tasks, kb, dinv);
     k_gj_fe<T><<<gcol, 256, 0, s>>>(d_tasks, kb, dinv, Fp, E, stride);
-    k_gj_update<T><<<int(tt.size()), 256, 0, s>>>(d_tasks, d_tt, d_ti, kb, dinv, Fp, E, stride);
+    if (sizeof(T) == 4)
+      k_gj_update_f32<<<int(tt.size()), 256, GJU_SMEM, s>>>(d_tasks, d_tt, d_ti, kb, reinterpret_cast<const float*>(dinv),
+                                                     reinterpret_cast<const float*>(Fp),
+                                                     reinterpret_cast<const float*>(E), stride);
+    else
+      k_gj_update<T><<<int(tt.size()), 256, 0, s>>>(d_tasks, d_tt, d_ti, kb, dinv, Fp, E, stride);
     check_launch("gauss-jordan panel");
   }
   k_gj_colperm<T><<<gcol, 256, 0, s>>>(d_tasks, piv, nmax);

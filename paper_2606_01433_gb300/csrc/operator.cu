@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(256) k_lift(const int32_t* __restrict__ rows, 
 }
 
 // ------------------------------------------------------------------ a3: SpMV
-// Velocity rows from the sliced copy: one warp per slice of 32 rows, lane = row, every lane
-// running the same number of blocks (the slice's longest row; shorter rows are zero padded),
+// Velocity rows from the sliced copy: slices of 32 rows, lane = row, every lane running the
+// same number of blocks (the slice's longest row; shorter rows are zero padded),
 // so each FP64 warp instruction has all 32 lanes busy.  Slot group g (32 slots, one per lane)
 // keeps its 3x3 blocks component-major: value m of lane l at g * 288 + m * 32 + l (B^T: at
 // g * 96 + m * 32 + l), so every value load is one coalesced 256-byte access.
@@ -349,6 +349,22 @@ __global__ void k_sell_fill(const int32_t* __restrict__ src, int64_t nslots, int
   for (int c = 0; c < m; ++c) to[g * (32 * m) + c * 32 + lane] = e >= 0 ? from[int64_t(e) * m + c] : 0.0;
 }
 
+__device__ __forceinline__ void sell_block(const int32_t* __restrict__ acol, const double* __restrict__ aval,
+                                           const double* __restrict__ x, int64_t g, int lane, double& a0, double& a1,
+                                           double& a2) {
+  const int64_t j = __ldg(acol + g * 32 + lane);
+  const double x0 = __ldg(x + 3 * j), x1 = __ldg(x + 3 * j + 1), x2 = __ldg(x + 3 * j + 2);
+  const double* v = aval + g * 288 + lane;
+  const double v0 = __ldcs(v), v1 = __ldcs(v + 32), v2 = __ldcs(v + 64), v3 = __ldcs(v + 96), v4 = __ldcs(v + 128),
+               v5 = __ldcs(v + 160), v6 = __ldcs(v + 192), v7 = __ldcs(v + 224), v8 = __ldcs(v + 256);
+  a0 = fma(v2, x2, fma(v1, x1, fma(v0, x0, a0)));
+  a1 = fma(v5, x2, fma(v4, x1, fma(v3, x0, a1)));
+  a2 = fma(v8, x2, fma(v7, x1, fma(v6, x0, a2)));
+}
+
+// Velocity part: CTA b takes slices 2b and 2b + 1, four warps per slice; warp k of a slice
+// takes the slot groups g = g0 + k, g0 + k + 4, ... (two in flight), and the four partial
+// sums of a row are added in warp order.  CTAs from ceil(nslices / 2) on take 8 pressure rows.
 __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ sell_row, const int64_t* __restrict__ aoff,
                                               const int32_t* __restrict__ acol, const double* __restrict__ aval,
                                               const int64_t* __restrict__ boff, const int32_t* __restrict__ bcol,
@@ -357,53 +373,60 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ sell_r
                                               const double* __restrict__ bval, int64_t nv, int64_t np,
                                               const double* __restrict__ x, double* __restrict__ y,
                                               const double* __restrict__ rhs) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
+  __shared__ double red[8][3][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nu = 3 * nv;
-  if (wid < nslices) {
+  const int64_t vblocks = (nslices + 1) / 2;
+  if (blockIdx.x < vblocks) {
+    const int64_t sl = 2 * int64_t(blockIdx.x) + (warp >> 2);
+    const int sub = warp & 3;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    const int64_t g0 = aoff[wid] >> 5, g1 = aoff[wid + 1] >> 5;
-    for (int64_t g = g0; g < g1; ++g) {
-      const int64_t j = __ldg(acol + g * 32 + lane);
-      const double x0 = __ldg(x + 3 * j), x1 = __ldg(x + 3 * j + 1), x2 = __ldg(x + 3 * j + 2);
-      const double* v = aval + g * 288 + lane;
-      a0 = fma(__ldcs(v + 0), x0, a0);
-      a0 = fma(__ldcs(v + 32), x1, a0);
-      a0 = fma(__ldcs(v + 64), x2, a0);
-      a1 = fma(__ldcs(v + 96), x0, a1);
-      a1 = fma(__ldcs(v + 128), x1, a1);
-      a1 = fma(__ldcs(v + 160), x2, a1);
-      a2 = fma(__ldcs(v + 192), x0, a2);
-      a2 = fma(__ldcs(v + 224), x1, a2);
-      a2 = fma(__ldcs(v + 256), x2, a2);
-    }
-    const int64_t h0 = boff[wid] >> 5, h1 = boff[wid + 1] >> 5;
-    for (int64_t g = h0; g < h1; ++g) {
-      const double xp = __ldg(x + nu + __ldg(bcol + g * 32 + lane));
-      const double* v = btval + g * 96 + lane;
-      a0 = fma(__ldcs(v + 0), xp, a0);
-      a1 = fma(__ldcs(v + 32), xp, a1);
-      a2 = fma(__ldcs(v + 64), xp, a2);
-    }
-    const int32_t row = sell_row[wid * 32 + lane];
-    if (row >= 0) {
-      const int64_t o = 3 * int64_t(row);
-      if (rhs) {
-        a0 = rhs[o] - a0;
-        a1 = rhs[o + 1] - a1;
-        a2 = rhs[o + 2] - a2;
+    if (sl < nslices) {
+      const int64_t g0 = aoff[sl] >> 5, g1 = aoff[sl + 1] >> 5;
+      int64_t g = g0 + sub;
+      for (; g + 4 < g1; g += 8) {  // two independent slot groups per pass
+        double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+        sell_block(acol, aval, x, g, lane, a0, a1, a2);
+        sell_block(acol, aval, x, g + 4, lane, b0, b1, b2);
+        a0 += b0;
+        a1 += b1;
+        a2 += b2;
       }
-      y[o] = a0;
-      y[o + 1] = a1;
-      y[o + 2] = a2;
+      if (g < g1) sell_block(acol, aval, x, g, lane, a0, a1, a2);
+      const int64_t h0 = boff[sl] >> 5, h1 = boff[sl + 1] >> 5;
+      for (int64_t h = h0 + sub; h < h1; h += 4) {
+        const double xp = __ldg(x + nu + __ldg(bcol + h * 32 + lane));
+        const double* v = btval + h * 96 + lane;
+        a0 = fma(__ldcs(v + 0), xp, a0);
+        a1 = fma(__ldcs(v + 32), xp, a1);
+        a2 = fma(__ldcs(v + 64), xp, a2);
+      }
     }
-  } else if (wid < nslices + np) {
-    const int64_t P = wid - nslices;
+    red[warp][0][lane] = a0;
+    red[warp][1][lane] = a1;
+    red[warp][2][lane] = a2;
+    __syncthreads();
+    if (sub == 0 && sl < nslices) {
+      const int32_t row = sell_row[sl * 32 + lane];
+      if (row >= 0) {
+        const int64_t o = 3 * int64_t(row);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double t = red[warp][c][lane];
+#pragma unroll
+          for (int k = 1; k < 4; ++k) t += red[warp + k][c][lane];
+          y[o + c] = rhs ? rhs[o + c] - t : t;
+        }
+      }
+    }
+  } else {
+    const int64_t P = (int64_t(blockIdx.x) - vblocks) * 8 + warp;
+    if (P >= np) return;
     const int64_t f0 = int64_t(b_ptr[P]) * 3, f1 = int64_t(b_ptr[P + 1]) * 3;
     double acc = 0.0;
     for (int64_t f = f0 + lane; f < f1; f += 32) {
-      int64_t e = f / 3;
-      int d = int(f - 3 * e);
+      const int64_t e = f / 3;
+      const int d = int(f - 3 * e);
       acc = fma(__ldcs(bval + f), __ldg(x + 3 * int64_t(b_col[e]) + d), acc);
     }
 #pragma unroll
@@ -481,8 +504,8 @@ void launch_spmv(gdsw_ctx* c, const double* x, double* y, const double* rhs, cud
   const int64_t nv = c->mesh.nv, np = c->mesh.np;
   const double* bval = c->d_val + 9 * c->nnzb + 3 * c->nbt;
   const int64_t ns = c->n_sell_slices;
-  const int64_t warps = ns + np;
-  k_spmv<<<int((warps + 7) / 8), 256, 0, s>>>(c->d_sell_row, c->d_sell_aoff, c->d_sell_acol, c->d_sell_aval,
+  const int64_t blocks = (ns + 1) / 2 + (np + 7) / 8;
+  k_spmv<<<int(blocks), 256, 0, s>>>(c->d_sell_row, c->d_sell_aoff, c->d_sell_acol, c->d_sell_aval,
                                               c->d_sell_boff, c->d_sell_bcol, c->d_sell_btval, ns, c->d_b_ptr,
                                               c->d_b_col, bval, nv, np, x, y, rhs);
   check_launch("k_spmv");
