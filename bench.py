@@ -49,9 +49,11 @@ def parse():
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--prof-stride", type=int, default=8,
                     help="CUDA-event timing of every k-th preconditioner apply inside the timed region")
-    ap.add_argument("--sweep", choices=["persistent", "steps"], default="steps",
-                    help="local solves as one persistent launch per level, or one launch per slab step")
+    ap.add_argument("--sweep", choices=["auto", "persistent", "steps"], default="auto",
+                    help="local solves: the set-up autotuner's choice, one persistent launch per level, "
+                         "or one launch per slab step")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM of the persistent sweep (0 = all)")
+    ap.add_argument("--tile-rows", type=int, default=0, help="rows per forward GEMV tile (0 = the autotuner's)")
     ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals of mixed requests")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--serve-sizes", type=str, default="8,12,16,20,24,28,32")
@@ -326,8 +328,10 @@ def run_gdsw(args, rank, world, local):
     t0 = time.perf_counter()
     ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8, restart=100, max_it=1000)
     setup_mixed_s = time.perf_counter() - t0
-    persistent = args.sweep == "persistent"
-    ctx.gdsw_set_local_sweep(persistent, args.ctas_per_sm)
+    if args.sweep != "auto":
+        ctx.gdsw_set_local_sweep(args.sweep == "persistent", args.ctas_per_sm, args.tile_rows)
+    tuned = ctx.sizes
+    persistent = bool(tuned.persistent[0]) if args.sweep == "auto" else args.sweep == "persistent"
     n = ctx.n
     lib = gdsw.load()
     import ctypes
@@ -397,7 +401,8 @@ def run_gdsw(args, rank, world, local):
         t0 = time.perf_counter()
         c64 = gdsw.Context(p, precision=("fp64",) * 3, phi_precision="fp64", tol=1e-8)
         setup64 = time.perf_counter() - t0
-        c64.gdsw_set_local_sweep(persistent, args.ctas_per_sm)
+        if args.sweep != "auto":
+            c64.gdsw_set_local_sweep(args.sweep == "persistent", args.ctas_per_sm, args.tile_rows)
         for _ in range(min(args.warmup, 1)):
             step(c64)
         c64.gdsw_profile_enable(True)
@@ -421,7 +426,8 @@ def run_gdsw(args, rank, world, local):
         del c64
         torch.cuda.empty_cache()
         ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8)
-        ctx.gdsw_set_local_sweep(persistent, args.ctas_per_sm)
+        if args.sweep != "auto":
+            ctx.gdsw_set_local_sweep(args.sweep == "persistent", args.ctas_per_sm, args.tile_rows)
 
     # end to end through the host-buffer entry point: u_k, b and x0 from pinned host memory,
     # x back to host, inside the timed region
@@ -496,6 +502,9 @@ def run_gdsw(args, rank, world, local):
                      "peak_kind": peak_kind, "avg_launch_ms": gemv_avg_ms, "avg_launch_bytes": gemv_avg_bytes,
                      "traffic": (ratio * gemv_avg_bytes) if ratio else None,
                      "fwd_launch_bytes": fwd_bytes},
+        "autotune": {"tile_rows": [int(v) for v in list(tuned.tile_rows)[:tuned.levels - 1]],
+                     "persistent": [int(v) for v in list(tuned.persistent)[:tuned.levels - 1]],
+                     "local_solve_ms": [float(v) for v in list(tuned.tuned_ms)[:tuned.levels - 1]]},
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

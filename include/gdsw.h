@@ -130,6 +130,9 @@ typedef struct {
   int64_t device_bytes;     /* bytes the context holds on the device */
   double setup_ms[6];       /* host symbolic, viscosity+assembly, level-1 factors, Phi+A0,
                                coarse levels, total */
+  int32_t tile_rows[3];     /* rows per forward GEMV tile chosen by the set-up autotuner */
+  int32_t persistent[3];    /* 1: local solve as one persistent launch (autotuner's choice) */
+  double tuned_ms[3];       /* the chosen configuration's local-solve time (0: not tuned) */
 } gdsw_sizes_info;
 
 /* Per-call kernel timing (CUDA events on the context stream) and algorithmic bytes. */
@@ -237,16 +240,19 @@ int gdsw_plan_bytes(const gdsw_ctx* ctx, int32_t level, int32_t direction, int32
 
 /* How the local solves of every level run (the arithmetic, and so the result, is the same
  * bit for bit either way):
- *   persistent = 0 (default): one launch per slab step, forward then backward (Section 2.1
+ *   persistent = 0: one launch per slab step, forward then backward (Section 2.1
  *     A_i^{-1} applied as block-LDL^T sweeps);
  *   persistent = 1: one persistent launch per level and apply; CTAs take the tiles of all
  *     slab steps from a work list in dependency order and wait (at most 1 s per wait, else
  *     gdsw_solve returns GDSW_ERR_TIMEOUT) until the tiles they read from are written.
  * ctas_per_sm: resident CTAs per SM of the persistent launch (0 = as many as fit); fewer
- * leave room for the coarse branch that runs concurrently on a second stream.  Must not be
- * called while the context has work in flight or inside a stream capture; a context whose
- * apply is captured in a CUDA graph (use_graph) keeps its mode (GDSW_ERR_INVALID_ARG). */
-int gdsw_set_local_sweep(gdsw_ctx* ctx, int32_t persistent, int32_t ctas_per_sm);
+ * leave room for the coarse branch that runs concurrently on a second stream.
+ * tile_rows: rows per forward GEMV tile, 32, 64 or 128 (0 = keep).  gdsw_setup chooses the
+ * level-1 mode and tile rows by timing applies (gdsw_sizes reports the choice); this call
+ * overrides it for every level.  Must not be called while the context has work in flight or
+ * inside a stream capture; a context whose apply is captured in a CUDA graph (use_graph)
+ * keeps its mode (GDSW_ERR_INVALID_ARG). */
+int gdsw_set_local_sweep(gdsw_ctx* ctx, int32_t persistent, int32_t ctas_per_sm, int32_t tile_rows);
 
 int gdsw_profile_enable(gdsw_ctx* ctx, int32_t on);
 int gdsw_profile_read(gdsw_ctx* ctx, gdsw_profile* prof);

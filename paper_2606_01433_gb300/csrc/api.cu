@@ -295,6 +295,7 @@ static void build_sweep(gdsw_ctx* c, LevelDev& L, int nslab, int Kmax, const std
   SP.d_items = c->arena.upload(items, c->stream);
   SP.d_tasks = c->arena.upload(all, c->stream);
   SP.d_ctr = c->arena.alloc<unsigned>(nctr);
+  SP.G = L.fwd.rows_per_tile / 32;
 }
 
 static void resize_sweep(LevelDev& L, int ctas_per_sm) {
@@ -414,6 +415,78 @@ static void build_local_plan(gdsw_ctx* c, const SlabSet& S, LevelDev& L) {
   L.fwd.d_tiles = dl;
   L.bwd.d_tasks = dt;
   L.bwd.d_tiles = dl;
+}
+
+// Tile-shape autotuner for the level-1 local solves, run at the end of the set-up: whole
+// preconditioner applies (level-1 sweeps with the coarse branch running beside them on the
+// second stream) are timed with CUDA events, best of three after a warm-up, with 32, 64 and
+// 128 rows per forward tile, each as one launch per slab step and as the persistent launch;
+// the fastest is kept.  Every candidate computes the same numbers bit for bit -- a row's dot
+// product is one warp's in a fixed order and the persistent launch runs the same tiles -- so
+// the choice changes only the schedule.  Small problems (level-1 sweeps under 64 MB) keep
+// the defaults.
+static void apply_precond_impl(gdsw_ctx* c, const double* r, double* z, cudaStream_t s);
+
+static void autotune_level1(gdsw_ctx* c) {
+  LevelDev& L = c->ld[0];
+  double bytes = L.red_bytes;
+  for (double b : L.fwd_bytes) bytes += b;
+  for (double b : L.bwd_bytes) bytes += b;
+  if (bytes < 64e6 || L.n <= 0) return;
+  cudaStream_t s = c->stream;
+  DevArena tmp;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  try {
+    const int64_t n = c->mesh.n;
+    double* r = tmp.alloc<double>(n);
+    double* z = tmp.alloc<double>(n);
+    GDSW_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * n, s));
+    GDSW_CUDA(cudaEventCreate(&e0));
+    GDSW_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestG = 1, curG = L.fwd.rows_per_tile / 32;
+    bool bestP = false;
+    for (int G : {1, 2, 4}) {
+      if (G != curG) {
+        L.fwd.rows_per_tile = 32 * G;
+        build_local_plan(c, c->lh[0].loc, L);
+        curG = G;
+      }
+      for (bool P : {false, true}) {
+        L.persistent = P;
+        apply_precond_impl(c, r, z, s);
+        float t = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          GDSW_CUDA(cudaEventRecord(e0, s));
+          apply_precond_impl(c, r, z, s);
+          GDSW_CUDA(cudaEventRecord(e1, s));
+          GDSW_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          GDSW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          t = std::min(t, ms);
+        }
+        if (t < best) {
+          best = t;
+          bestG = G;
+          bestP = P;
+        }
+      }
+    }
+    if (bestG != curG) {
+      L.fwd.rows_per_tile = 32 * bestG;
+      build_local_plan(c, c->lh[0].loc, L);
+    }
+    L.persistent = bestP;
+    L.tuned_ms = best;
+  } catch (...) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    tmp.free_all();
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tmp.free_all();
 }
 
 // ------------------------------------------------------------------ coarse space upload
@@ -913,7 +986,7 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
       launch_gemv<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), v, v, v, P, k, ld, s);
     }
   };
-  if (c->persistent_sweep && L.sweep.nitems > 0) {
+  if (L.persistent && L.sweep.nitems > 0) {
     // the whole forward / reduction / backward sequence as one persistent launch
     double bytes = L.red_bytes;
     for (double b : L.fwd_bytes) bytes += b;
@@ -1014,6 +1087,10 @@ static void apply_level(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
     ProfScope ps(c, GDSW_K_PROLONG, double(L.phi_bytes) + 16.0 * L.nidofs, s);
     launch_prolong(L, L.x0, z, s);
   }
+}
+
+static void apply_precond_impl(gdsw_ctx* c, const double* r, double* z, cudaStream_t s) {
+  apply_level(c, 0, r, z, s);
 }
 
 void apply_precond(gdsw_ctx* c, const double* r, double* z, cudaStream_t s) {
@@ -1300,6 +1377,7 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
   double t5 = now_ms();
   c->setup_ms[4] = t5 - t4;
   GDSW_CUDA(cudaStreamSynchronize(s));
+  autotune_level1(c);
   if (opt->use_graph) capture_graph(c);
   c->apply_bytes = apply_bytes(c);
   c->setup_ms[5] = now_ms() - t0;
@@ -1427,6 +1505,11 @@ int gdsw_sizes(const gdsw_ctx* c, gdsw_sizes_info* info) {
   s.phi_entries = c->lh.empty() ? 0 : int64_t(c->lh[0].cs.idofs.size());
   s.device_bytes = c->host_only ? c->est_device_bytes : int64_t(c->arena.bytes);
   for (int q = 0; q < 6; ++q) s.setup_ms[q] = c->setup_ms[q];
+  for (size_t l = 0; l < c->ld.size() && l < 3; ++l) {
+    s.tile_rows[l] = c->ld[l].fwd.rows_per_tile;
+    s.persistent[l] = c->ld[l].persistent ? 1 : 0;
+    s.tuned_ms[l] = c->ld[l].tuned_ms;
+  }
   *info = s;
   return GDSW_OK;
 }
@@ -1596,15 +1679,23 @@ int gdsw_plan_bytes(const gdsw_ctx* c, int32_t level, int32_t direction, int32_t
   return GDSW_OK;
 }
 
-int gdsw_set_local_sweep(gdsw_ctx* c, int32_t persistent, int32_t ctas_per_sm) {
+int gdsw_set_local_sweep(gdsw_ctx* c, int32_t persistent, int32_t ctas_per_sm, int32_t tile_rows) {
   if (!c || c->host_only || ctas_per_sm < 0) return GDSW_ERR_INVALID_ARG;
+  if (tile_rows != 0 && tile_rows != 32 && tile_rows != 64 && tile_rows != 128) return GDSW_ERR_INVALID_ARG;
   if (c->apply_graph) {
     c->err = "gdsw_set_local_sweep: the apply is already captured in a CUDA graph (use_graph)";
     return GDSW_ERR_INVALID_ARG;
   }
   GDSW_TRY(c, {
-    c->persistent_sweep = persistent != 0;
-    for (LevelDev& L : c->ld) resize_sweep(L, ctas_per_sm);
+    for (size_t l = 0; l < c->ld.size(); ++l) {
+      LevelDev& L = c->ld[l];
+      L.persistent = persistent != 0;
+      if (tile_rows != 0 && tile_rows != L.fwd.rows_per_tile) {
+        L.fwd.rows_per_tile = tile_rows;
+        build_local_plan(c, c->lh[l].loc, L);
+      }
+      resize_sweep(L, ctas_per_sm);
+    }
   });
 }
 

@@ -228,6 +228,7 @@ struct SweepPlan {
   GemvTask* d_tasks = nullptr;   // forward, backward and reduction tasks of the level
   unsigned* d_ctr = nullptr;     // [0] = claim counter, then 4 counters per slab
   int nitems = 0, nctr = 0, xs_elems = 0, grid = 0, ctas_per_sm = 0, max_per_sm = 0;
+  int G = 1;                     // row groups of 32 per forward tile
   size_t smem = 0;
 };
 constexpr unsigned long long kSweepWaitLimitNs = 1000000000ull;  // 1 s per wait
@@ -240,6 +241,8 @@ struct LevelDev {
   int32_t* gdof = nullptr;
   GemvPlan fwd, bwd;            // forward launches (Sinv, G) and backward launches (W)
   SweepPlan sweep;              // the same tiles as one persistent launch
+  bool persistent = false;      // local solve as the persistent launch (else one launch per slab step)
+  double tuned_ms = 0;          // autotuned local-solve time (0: not tuned)
   void* vec = nullptr;          // local vector workspace (2 * nvec, compute precision)
   int32_t *sc_ptr = nullptr, *sc_pos = nullptr;
   double* sc_w = nullptr;
@@ -328,7 +331,6 @@ struct gdsw_ctx {
   int64_t n_lift_rows = 0;
   bool b_assembled = false;         // B does not depend on the viscosity: assembled once
   unsigned* d_sweep_flag = nullptr; // set by a persistent sweep whose wait ran out
-  bool persistent_sweep = false;    // local solves as one persistent launch per level (else per slab step)
   double* d_gdir = nullptr;         // Dirichlet datum, 3 per node
   void* d_tables = nullptr;         // RefTables
   double* d_val = nullptr;          // [A blocks (9 per block) | BT (3 per entry) | B (3 per entry)]

@@ -118,9 +118,11 @@ __device__ __forceinline__ void sym_tile(const TM* __restrict__ M, const TV* xba
   }
 }
 
-// Rows [row0, row0 + 8 RPW) of one task.  Vector reads go through L2 (ld.global.cg): in the
-// persistent sweep other CTAs write the local vectors while this one runs.
-template <typename TM, typename TV, int RPW>
+// Rows [row0, row0 + 8 RPW G) of one task: G consecutive groups of 8 RPW rows share one
+// staging of the input vector, and every row is one warp's dot product in the same order
+// whatever G is.  Vector reads go through L2 (ld.global.cg): in the persistent sweep other
+// CTAs write the local vectors while this one runs.
+template <typename TM, typename TV, int RPW, int G>
 __device__ __forceinline__ void rows_tile(const TM* __restrict__ M, const TV* xbase, TV* ybase, const TV* bbase,
                                           const GemvTask& t, int row0, TV* xs) {
   const int ld = t.ld;
@@ -128,73 +130,77 @@ __device__ __forceinline__ void rows_tile(const TM* __restrict__ M, const TV* xb
   __syncthreads();
   constexpr int V = Vec16<TM>::N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rbeg = row0 + warp * RPW;
-  TV acc[RPW];
-  const TM* rowp[RPW];
 #pragma unroll
-  for (int q = 0; q < RPW; ++q) {
-    acc[q] = TV(0);
-    int r = rbeg + q;
-    rowp[q] = M + t.mat + int64_t(r < t.rows ? r : 0) * ld;
-  }
-  int c = lane * V;
-  for (; c + 32 * V < ld; c += 64 * V) {  // two column chunks per row in flight
-    TV mv0[RPW][V], mv1[RPW][V];
+  for (int g = 0; g < G; ++g) {  // G is a compile-time constant: a runtime count here slows the loads
+    const int rbeg = row0 + g * 8 * RPW + warp * RPW;
+    if (rbeg - warp * RPW >= t.rows) break;
+    TV acc[RPW];
+    const TM* rowp[RPW];
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
-      if (rbeg + q < t.rows) {
-        load16s(rowp[q] + c, mv0[q]);
-        load16s(rowp[q] + c + 32 * V, mv1[q]);
+      acc[q] = TV(0);
+      int r = rbeg + q;
+      rowp[q] = M + t.mat + int64_t(r < t.rows ? r : 0) * ld;
+    }
+    int c = lane * V;
+    for (; c + 32 * V < ld; c += 64 * V) {  // two column chunks per row in flight
+      TV mv0[RPW][V], mv1[RPW][V];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        if (rbeg + q < t.rows) {
+          load16s(rowp[q] + c, mv0[q]);
+          load16s(rowp[q] + c + 32 * V, mv1[q]);
+        }
+      }
+      TV xv0[V], xv1[V];
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        xv0[u] = xs[c + u];
+        xv1[u] = xs[c + 32 * V + u];
+      }
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        if (rbeg + q < t.rows) {
+#pragma unroll
+          for (int u = 0; u < V; ++u) acc[q] = fma(mv1[q][u], xv1[u], fma(mv0[q][u], xv0[u], acc[q]));
+        }
       }
     }
-    TV xv0[V], xv1[V];
+    if (c < ld) {
+      TV xv[V];
 #pragma unroll
-    for (int u = 0; u < V; ++u) {
-      xv0[u] = xs[c + u];
-      xv1[u] = xs[c + 32 * V + u];
+      for (int u = 0; u < V; ++u) xv[u] = xs[c + u];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        if (rbeg + q < t.rows) {
+          TV mv[V];
+          load16s(rowp[q] + c, mv);
+#pragma unroll
+          for (int u = 0; u < V; ++u) acc[q] = fma(mv[u], xv[u], acc[q]);
+        }
+      }
     }
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
-      if (rbeg + q < t.rows) {
 #pragma unroll
-        for (int u = 0; u < V; ++u) acc[q] = fma(mv1[q][u], xv1[u], fma(mv0[q][u], xv0[u], acc[q]));
-      }
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
     }
-  }
-  if (c < ld) {
-    TV xv[V];
+    if (lane < RPW) {
+      TV a = acc[0];
 #pragma unroll
-    for (int u = 0; u < V; ++u) xv[u] = xs[c + u];
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-      if (rbeg + q < t.rows) {
-        TV mv[V];
-        load16s(rowp[q] + c, mv);
-#pragma unroll
-        for (int u = 0; u < V; ++u) acc[q] = fma(mv[u], xv[u], acc[q]);
+      for (int q = 1; q < RPW; ++q)
+        if (lane == q) a = acc[q];
+      int r = rbeg + lane;
+      if (r < t.rows) {
+        TV v = TV(t.alpha) * a;
+        if (t.base >= 0) v += __ldcg(bbase + t.base + r);
+        ybase[t.y + r] = v;
       }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < RPW; ++q) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-  }
-  if (lane < RPW) {
-    TV a = acc[0];
-#pragma unroll
-    for (int q = 1; q < RPW; ++q)
-      if (lane == q) a = acc[q];
-    int r = rbeg + lane;
-    if (r < t.rows) {
-      TV v = TV(t.alpha) * a;
-      if (t.base >= 0) v += __ldcg(bbase + t.base + r);
-      ybase[t.y + r] = v;
     }
   }
 }
 
-template <typename TM, typename TV, int RPW>
+template <typename TM, typename TV, int RPW, int G>
 __global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV* xbase, TV* ybase,
                                               const TV* bbase, const GemvTask* __restrict__ tasks,
                                               const GemvTile* __restrict__ tiles) {
@@ -205,42 +211,48 @@ __global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV
   if (t.kind == 1)  // packed symmetric tile; partial sums go to ybase + t.part
     sym_tile<TM, TV>(M, xbase, ybase, t, tl.row0 >> 16, tl.row0 & 0xffff, xs);
   else
-    rows_tile<TM, TV, RPW>(M, xbase, ybase, bbase, t, tl.row0, xs);
+    rows_tile<TM, TV, RPW, G>(M, xbase, ybase, bbase, t, tl.row0, xs);
 }
 
 // ------------------------------------------------------------------ ragged batched GEMV, transposed
-// y[c] = base[c] + alpha * sum_r M[r][c] x[r] for the columns [col0, col0 + 32 V) of a task
+// y[c] = base[c] + alpha * sum_r M[r][c] x[r] for the columns [col0, col0 + LW V) of a task
 // (used with the sub-diagonal blocks G of a symmetric LDL^T factorisation, whose
-// transposes are the super-diagonal blocks).  Each lane owns V consecutive columns (one
-// 16-byte load per row) and the 8 warps split the rows, four rows in flight per warp;
-// partial sums are combined in shared memory in a fixed order.  Narrow tiles (32 V columns)
-// give several CTAs per SM and per task, so the ragged launch stays balanced across SMs.
+// transposes are the super-diagonal blocks).  A group of LW lanes reads one row of the tile
+// (a lane owns V consecutive columns, one 16-byte load); the 256 / LW groups split the rows,
+// four rows in flight each; the partial sums of a column are combined in shared memory in a
+// fixed order.  Narrow tiles (LW V columns) give many CTAs per task, so the ragged launch
+// (tasks of different heights) spreads evenly over the SMs.
+// lanes per tile row of the transposed GEMV: half warps for FP32 / FP64 entries, whole warps
+// for BF16 (whose 16-byte loads already hold 8 columns)
+template <typename TM> struct ColsLanes { static constexpr int LW = 16; };
+template <> struct ColsLanes<__nv_bfloat16> { static constexpr int LW = 32; };
+
 template <typename TM, typename TV>
 __device__ __forceinline__ void cols_tile(const TM* __restrict__ M, const TV* xbase, TV* ybase, const TV* bbase,
                                           const GemvTask& t, int col0, TV* xs, TV* part) {
-  constexpr int V = Vec16<TM>::N, C = 32 * V;
+  constexpr int V = Vec16<TM>::N, LW = ColsLanes<TM>::LW, C = LW * V, NG = 256 / LW;
   for (int r = threadIdx.x; r < t.rows; r += blockDim.x) xs[r] = __ldcg(xbase + t.x + r);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = col0 + lane * V;  // tile column start + lane's V columns
+  const int ll = threadIdx.x % LW, grp = threadIdx.x / LW;  // NG row groups of LW lanes
+  const int c0 = col0 + ll * V;  // tile column start + this lane's V columns
   TV acc[V];
 #pragma unroll
   for (int u = 0; u < V; ++u) acc[u] = TV(0);
   if (c0 < t.ld) {
     const TM* p = M + t.mat + c0;
-    int r = warp;
-    for (; r + 24 < t.rows; r += 32) {
+    int r = grp;
+    for (; r + 3 * NG < t.rows; r += 4 * NG) {
       TV v[4][V];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) load16s(p + int64_t(r + 8 * q) * t.ld, v[q]);
+      for (int q = 0; q < 4; ++q) load16s(p + int64_t(r + NG * q) * t.ld, v[q]);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const TV xq = xs[r + 8 * q];
+        const TV xq = xs[r + NG * q];
 #pragma unroll
         for (int u = 0; u < V; ++u) acc[u] = fma(v[q][u], xq, acc[u]);
       }
     }
-    for (; r < t.rows; r += 8) {
+    for (; r < t.rows; r += NG) {
       TV v0[V];
       load16s(p + int64_t(r) * t.ld, v0);
       const TV x0 = xs[r];
@@ -249,14 +261,14 @@ __device__ __forceinline__ void cols_tile(const TM* __restrict__ M, const TV* xb
     }
   }
 #pragma unroll
-  for (int u = 0; u < V; ++u) part[warp * (C + 1) + lane * V + u] = acc[u];
+  for (int u = 0; u < V; ++u) part[grp * (C + 1) + ll * V + u] = acc[u];
   __syncthreads();
   for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
     const int c = col0 + cc;
     if (c < t.cols) {
       TV s = part[cc];
 #pragma unroll
-      for (int w = 1; w < 8; ++w) s += part[w * (C + 1) + cc];
+      for (int g = 1; g < NG; ++g) s += part[g * (C + 1) + cc];
       TV v = TV(t.alpha) * s;
       if (t.base >= 0) v += __ldcg(bbase + t.base + c);
       ybase[t.y + c] = v;
@@ -268,9 +280,9 @@ template <typename TM, typename TV>
 __global__ void __launch_bounds__(256) k_gemvt(const TM* __restrict__ M, const TV* xbase, TV* ybase,
                                                const TV* bbase, const GemvTask* __restrict__ tasks,
                                                const GemvTile* __restrict__ tiles) {
-  constexpr int C = 32 * Vec16<TM>::N;
+  constexpr int LW = ColsLanes<TM>::LW, C = LW * Vec16<TM>::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ TV part[8 * (C + 1)];
+  __shared__ TV part[(256 / LW) * (C + 1)];
   const GemvTile tl = tiles[blockIdx.x];
   const GemvTask t = tasks[tl.task];
   cols_tile<TM, TV>(M, xbase, ybase, bbase, t, tl.row0, reinterpret_cast<TV*>(smem_raw), part);
@@ -286,7 +298,13 @@ void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P
     k_gemvt<TM, TV><<<t1 - t0, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
     check_launch("k_gemvt");
   } else {
-    k_gemv<TM, TV, 4><<<t1 - t0, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+    const int nb = t1 - t0;
+    if (P.rows_per_tile == 128)
+      k_gemv<TM, TV, 4, 4><<<nb, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+    else if (P.rows_per_tile == 64)
+      k_gemv<TM, TV, 4, 2><<<nb, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+    else
+      k_gemv<TM, TV, 4, 1><<<nb, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
     check_launch("k_gemv");
   }
 }
@@ -354,13 +372,13 @@ __device__ __forceinline__ bool wait_count(const unsigned* cnt, unsigned need, u
   return true;
 }
 
-template <typename TM, typename TV>
+template <typename TM, typename TV, int G>
 __global__ void __launch_bounds__(256, 3) k_sweep(const TM* __restrict__ M, TV* vec, const GemvTask* __restrict__ tasks,
                                                const SweepItem* __restrict__ items, int nitems, unsigned* ctr,
                                                unsigned* flag, int T, int xs_elems, unsigned long long limit_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TV* xs = reinterpret_cast<TV*>(smem_raw);
-  TV* cpart = xs + xs_elems;  // 8 x (32 V + 1) column partials of the transposed tiles
+  TV* cpart = xs + xs_elems;  // column partials of the transposed tiles
   __shared__ int s_item[2];
   __shared__ int s_ok;
   if (threadIdx.x == 0) s_item[0] = int(atomicAdd(ctr, 1u));
@@ -382,7 +400,7 @@ __global__ void __launch_bounds__(256, 3) k_sweep(const TM* __restrict__ M, TV* 
     if (!s_ok) break;
     const GemvTask t = tasks[w.task];
     if (w.op == SWEEP_ROWS)
-      rows_tile<TM, TV, 4>(M, vec, vec, vec, t, w.arg, xs);
+      rows_tile<TM, TV, 4, G>(M, vec, vec, vec, t, w.arg, xs);
     else if (w.op == SWEEP_SYM)
       sym_tile<TM, TV>(M, vec, vec, t, w.arg >> 16, w.arg & 0xffff, xs);
     else if (w.op == SWEEP_REDUCE)
@@ -400,13 +418,20 @@ __global__ void __launch_bounds__(256, 3) k_sweep(const TM* __restrict__ M, TV* 
 
 template <typename TM, typename TV>
 void size_sweep(SweepPlan& P) {
-  constexpr int C = 32 * Vec16<TM>::N;
-  P.smem = (size_t(P.xs_elems) + 8 * (C + 1)) * sizeof(TV);
+  constexpr int LW = ColsLanes<TM>::LW, C = LW * Vec16<TM>::N;
+  P.smem = (size_t(P.xs_elems) + (256 / LW) * (C + 1)) * sizeof(TV);
   GDSW_CHECK(P.smem <= size_t(200) * 1024, GDSW_ERR_INVALID_ARG, "persistent sweep: staging exceeds shared memory");
   // one limit for every level's launch of this instantiation (the attribute is per kernel)
-  GDSW_CUDA(cudaFuncSetAttribute(k_sweep<TM, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  GDSW_CUDA(cudaFuncSetAttribute(k_sweep<TM, TV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  GDSW_CUDA(cudaFuncSetAttribute(k_sweep<TM, TV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  GDSW_CUDA(cudaFuncSetAttribute(k_sweep<TM, TV, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0, dev = 0, nsm = 0;
-  GDSW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<TM, TV>, 256, P.smem));
+  if (P.G == 4)
+    GDSW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<TM, TV, 4>, 256, P.smem));
+  else if (P.G == 2)
+    GDSW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<TM, TV, 2>, 256, P.smem));
+  else
+    GDSW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<TM, TV, 1>, 256, P.smem));
   GDSW_CUDA(cudaGetDevice(&dev));
   GDSW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   GDSW_CHECK(per_sm > 0, GDSW_ERR_CUDA, "persistent sweep: no CTA fits on an SM");
@@ -419,8 +444,15 @@ template <typename TM, typename TV>
 void launch_sweep(const TM* M, TV* vec, const SweepPlan& P, unsigned* flag, int T, cudaStream_t s) {
   if (P.nitems == 0) return;
   GDSW_CUDA(cudaMemsetAsync(P.d_ctr, 0, sizeof(unsigned) * P.nctr, s));
-  k_sweep<TM, TV><<<P.grid, 256, P.smem, s>>>(M, vec, P.d_tasks, P.d_items, P.nitems, P.d_ctr, flag, T, P.xs_elems,
-                                             kSweepWaitLimitNs);
+  if (P.G == 4)
+    k_sweep<TM, TV, 4><<<P.grid, 256, P.smem, s>>>(M, vec, P.d_tasks, P.d_items, P.nitems, P.d_ctr, flag, T,
+                                                   P.xs_elems, kSweepWaitLimitNs);
+  else if (P.G == 2)
+    k_sweep<TM, TV, 2><<<P.grid, 256, P.smem, s>>>(M, vec, P.d_tasks, P.d_items, P.nitems, P.d_ctr, flag, T,
+                                                   P.xs_elems, kSweepWaitLimitNs);
+  else
+    k_sweep<TM, TV, 1><<<P.grid, 256, P.smem, s>>>(M, vec, P.d_tasks, P.d_items, P.nitems, P.d_ctr, flag, T,
+                                                   P.xs_elems, kSweepWaitLimitNs);
   check_launch("k_sweep");
 }
 template void size_sweep<double, double>(SweepPlan&);
@@ -463,9 +495,15 @@ template void launch_gemv<__nv_bfloat16, float>(const __nv_bfloat16*, const floa
                                                 const GemvPlan&, int, int, cudaStream_t);
 
 void set_gemv_smem_limits() {
-  cudaFuncSetAttribute(k_gemv<double, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_gemv<float, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_gemv<__nv_bfloat16, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<double, double, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<float, float, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<__nv_bfloat16, float, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<double, double, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<float, float, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<__nv_bfloat16, float, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<double, double, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<float, float, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_gemv<__nv_bfloat16, float, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_gemvt<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
   cudaFuncSetAttribute(k_gemvt<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
   cudaFuncSetAttribute(k_gemvt<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);

@@ -68,7 +68,8 @@ class gdsw_sizes_info(C.Structure):
                 ("n_parts", C.c_int32 * 3), ("local_dofs", C.c_int64 * 3), ("factor_entries", C.c_int64 * 3),
                 ("max_local", C.c_int64 * 3), ("max_slabs", C.c_int32), ("nnzb_A", C.c_int64),
                 ("nnz_B", C.c_int64), ("phi_entries", C.c_int64), ("device_bytes", C.c_int64),
-                ("setup_ms", C.c_double * 6)]
+                ("setup_ms", C.c_double * 6), ("tile_rows", C.c_int32 * 3), ("persistent", C.c_int32 * 3),
+                ("tuned_ms", C.c_double * 3)]
 
 
 class gdsw_profile(C.Structure):
@@ -113,7 +114,7 @@ def load(path: str = LIB_PATH):
         "gdsw_level_entities": ([vp, i32, C.POINTER(i32)], C.c_int),
         "gdsw_kernel_launches": ([], i64),
         "gdsw_plan_bytes": ([vp, i32, i32, i32, C.POINTER(C.c_double)], C.c_int),
-        "gdsw_set_local_sweep": ([vp, i32, i32], C.c_int),
+        "gdsw_set_local_sweep": ([vp, i32, i32, i32], C.c_int),
         "gdsw_profile_enable": ([vp, i32], C.c_int),
         "gdsw_profile_read": ([vp, C.POINTER(gdsw_profile)], C.c_int),
         "gdsw_profile_reset": ([vp], C.c_int),
@@ -293,10 +294,11 @@ class Context:
         self._check(self.lib.gdsw_level_entities(self.h, level, C.byref(n)))
         return n.value
 
-    def gdsw_set_local_sweep(self, persistent=True, ctas_per_sm=0):
-        """Local solves as one persistent launch per level, or one launch per slab step (the default
-        of a new context)."""
-        return self._check(self.lib.gdsw_set_local_sweep(self.h, 1 if persistent else 0, int(ctas_per_sm)))
+    def gdsw_set_local_sweep(self, persistent=True, ctas_per_sm=0, tile_rows=0):
+        """Override the set-up autotuner: local solves as one persistent launch per level or one
+        launch per slab step, and rows per forward tile (32/64/128; 0 keeps the current)."""
+        return self._check(self.lib.gdsw_set_local_sweep(self.h, 1 if persistent else 0, int(ctas_per_sm),
+                                                         int(tile_rows)))
 
     def gdsw_profile_enable(self, on=True):
         """on: False/0 = off, True/1 = time every apply, k > 1 = every k-th apply."""

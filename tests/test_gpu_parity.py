@@ -243,28 +243,30 @@ def test_host_buffers_and_graph(lib):
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_persistent_sweep_equals_step_launches(lib, prec):
     """The persistent level sweep (one launch per level; tiles claimed in dependency order,
-    waits on per-slab counters) runs the same tiles with the same arithmetic as one launch
-    per slab step: every level's local branch and the whole apply agree bit for bit, at
-    full and at reduced residency, and the solve matches the oracle as before."""
+    waits on per-slab counters) and every forward tile height (32/64/128 rows) run the same
+    arithmetic as one launch per slab step with 32-row tiles: the local branch and the whole
+    apply agree bit for bit (so the set-up autotuner's choice never changes a result), at
+    full and at reduced residency, and the solve converges as before."""
     p = I.channel(16, parts=(4, 4, 4), groups=((2, 2, 2),), levels=3)
     ctx = lib.Context(p, precision=(prec,) * 3, phi_precision="fp32" if prec != "fp64" else "fp64", tol=1e-10)
     rng = np.random.default_rng(17)
     r = dev(rng.standard_normal(ctx.n))
     ref, out = {}, {}
-    ctx.gdsw_set_local_sweep(False)
+    ctx.gdsw_set_local_sweep(False, 0, 32)
     z = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
     ctx.gdsw_apply(r, z)
     ref["apply"] = host(z)
     ctx.gdsw_apply_local(0, r, z)
     ref["local0"] = host(z)
-    for ctas in (0, 1, 2):
-        ctx.gdsw_set_local_sweep(True, ctas)
+    for persistent, ctas, rows in ((True, 0, 32), (True, 1, 32), (True, 2, 64), (False, 0, 64), (False, 0, 128),
+                                   (True, 0, 128)):
+        ctx.gdsw_set_local_sweep(persistent, ctas, rows)
         for rep in range(2):
             z = torch.full((ctx.n,), float("nan"), dtype=torch.float64, device="cuda")
             ctx.gdsw_apply(r, z)
-            assert np.array_equal(host(z), ref["apply"]), (ctas, rep)
+            assert np.array_equal(host(z), ref["apply"]), (persistent, ctas, rows, rep)
             ctx.gdsw_apply_local(0, r, z)
-            assert np.array_equal(host(z), ref["local0"]), (ctas, rep)
+            assert np.array_equal(host(z), ref["local0"]), (persistent, ctas, rows, rep)
     ctx.gdsw_set_local_sweep(True, 0)
     b = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
     ctx.gdsw_rhs_lift(b)
