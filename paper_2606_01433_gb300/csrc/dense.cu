@@ -52,6 +52,32 @@ __device__ __forceinline__ void load16s(const __nv_bfloat16* p, float* v) {
   }
 }
 
+// raw 16-byte streaming load, unpacked only at the multiply (keeps BF16 tiles at half the
+// registers of unpacked floats)
+__device__ __forceinline__ uint4 ldraw(const void* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
+template <typename TM> struct Unpack;
+template <> struct Unpack<double> {
+  static __device__ __forceinline__ void run(const uint4& r, double* v) {
+    v[0] = __hiloint2double(int(r.y), int(r.x));
+    v[1] = __hiloint2double(int(r.w), int(r.z));
+  }
+};
+template <> struct Unpack<float> {
+  static __device__ __forceinline__ void run(const uint4& r, float* v) {
+    v[0] = __uint_as_float(r.x); v[1] = __uint_as_float(r.y); v[2] = __uint_as_float(r.z); v[3] = __uint_as_float(r.w);
+  }
+};
+template <> struct Unpack<__nv_bfloat16> {
+  static __device__ __forceinline__ void run(const uint4& r, float* v) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&r);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 f = __bfloat1622float2(h[q]);
+      v[2 * q] = f.x; v[2 * q + 1] = f.y;
+    }
+  }
+};
+
 // ------------------------------------------------------------------ ragged batched GEMV
 // One CTA = 8 warps = ROWS rows of one task; each warp owns ROWS/8 rows and streams them
 // with 16-byte loads (four rows in flight per warp).  The task's input vector is staged in
@@ -144,12 +170,12 @@ __device__ __forceinline__ void rows_tile(const TM* __restrict__ M, const TV* xb
     }
     int c = lane * V;
     for (; c + 32 * V < ld; c += 64 * V) {  // two column chunks per row in flight
-      TV mv0[RPW][V], mv1[RPW][V];
+      uint4 m0[RPW], m1[RPW];
 #pragma unroll
       for (int q = 0; q < RPW; ++q) {
         if (rbeg + q < t.rows) {
-          load16s(rowp[q] + c, mv0[q]);
-          load16s(rowp[q] + c + 32 * V, mv1[q]);
+          m0[q] = ldraw(rowp[q] + c);
+          m1[q] = ldraw(rowp[q] + c + 32 * V);
         }
       }
       TV xv0[V], xv1[V];
@@ -161,8 +187,11 @@ __device__ __forceinline__ void rows_tile(const TM* __restrict__ M, const TV* xb
 #pragma unroll
       for (int q = 0; q < RPW; ++q) {
         if (rbeg + q < t.rows) {
+          TV mv0[V], mv1[V];
+          Unpack<TM>::run(m0[q], mv0);
+          Unpack<TM>::run(m1[q], mv1);
 #pragma unroll
-          for (int u = 0; u < V; ++u) acc[q] = fma(mv1[q][u], xv1[u], fma(mv0[q][u], xv0[u], acc[q]));
+          for (int u = 0; u < V; ++u) acc[q] = fma(mv1[u], xv1[u], fma(mv0[u], xv0[u], acc[q]));
         }
       }
     }
@@ -222,10 +251,8 @@ __global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV
 // four rows in flight each; the partial sums of a column are combined in shared memory in a
 // fixed order.  Narrow tiles (LW V columns) give many CTAs per task, so the ragged launch
 // (tasks of different heights) spreads evenly over the SMs.
-// lanes per tile row of the transposed GEMV: half warps for FP32 / FP64 entries, whole warps
-// for BF16 (whose 16-byte loads already hold 8 columns)
+// lanes per tile row of the transposed GEMV: half warps
 template <typename TM> struct ColsLanes { static constexpr int LW = 16; };
-template <> struct ColsLanes<__nv_bfloat16> { static constexpr int LW = 32; };
 
 template <typename TM, typename TV>
 __device__ __forceinline__ void cols_tile(const TM* __restrict__ M, const TV* xbase, TV* ybase, const TV* bbase,

@@ -47,9 +47,8 @@ template <typename T>
 void pack_tiles(DevArena& tmp, const T* src, T* dst, const std::vector<PackTile>& tiles, int TT, cudaStream_t s);
 // tile edge of the packed symmetric blocks: one 16-byte load per lane across a warp
 inline int sym_tile_size(int prec) { return prec == GDSW_FP64 ? 64 : (prec == GDSW_FP32 ? 128 : 256); }
-// column tile of the transposed GEMV: 16 lanes (FP64, FP32) or 32 lanes (BF16) x one 16-byte
-// load of entries
-inline int gemvt_tile_cols(int prec) { return prec == GDSW_FP64 ? 32 : (prec == GDSW_FP32 ? 64 : 256); }
+// column tile of the transposed GEMV: 16 lanes (half a warp) x one 16-byte load of entries
+inline int gemvt_tile_cols(int prec) { return prec == GDSW_FP64 ? 32 : (prec == GDSW_FP32 ? 64 : 128); }
 template <typename T>
 void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s);
 template <typename T>
