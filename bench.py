@@ -242,7 +242,7 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- serving
-def run_serving(n_req, sizes, slots, seed=5, budget_frac=0.8):
+def run_serving(n_req, sizes, slots, seed=5, budget_frac=0.8, fixed_rate=False):
     """Continuous batching of mixed Carreau requests (unit-cube channels m^3, m ~ U{sizes},
     n ~ U[0.3, 1], nu0/nu_inf log-uniform in [10, 1e4]).  Closed loop first (all submitted at
     once: throughput), then open loop with Poisson arrivals at 0.8x that throughput
@@ -260,33 +260,44 @@ def run_serving(n_req, sizes, slots, seed=5, budget_frac=0.8):
     closed = [srv.gdsw_server_wait(t)[0] for t in tickets]
     makespan = time.perf_counter() - t0
     thr = n_req / makespan
+    def open_loop(gaps):
+        tickets = []
+        t0 = time.perf_counter()
+        due = 0.0
+        for p, gap in zip(probs, gaps):
+            due += gap
+            delay = due - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.gdsw_server_submit(p))
+        done = [srv.gdsw_server_wait(t)[0] for t in tickets]
+        return done, time.perf_counter() - t0
+
     rng = np.random.default_rng(seed)
-    gaps = rng.exponential(1.0 / (0.8 * thr), size=n_req)
-    tickets = []
-    t0 = time.perf_counter()
-    due = 0.0
-    for p, gap in zip(probs, gaps):
-        due += gap
-        delay = due - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append(srv.gdsw_server_submit(p))
-    opened = [srv.gdsw_server_wait(t)[0] for t in tickets]
-    wall = time.perf_counter() - t0
+    opened, wall = open_loop(rng.exponential(1.0 / (0.8 * thr), size=n_req))
+    fixed = None
+    if fixed_rate:  # the same rate with equal gaps
+        fixed, fwall = open_loop(np.full(n_req, 1.0 / (0.8 * thr)))
     stats = srv.gdsw_server_stats_read()
     srv.close()
     lat = np.array([s.latency_ms for s in opened])
-    ok = sum(1 for s in closed + opened if s.state == gdsw.REQ_DONE and s.relres <= 1e-8)
+    ok = sum(1 for s in closed + opened + (fixed or []) if s.state == gdsw.REQ_DONE and s.relres <= 1e-8)
+    extra = {}
+    if fixed:
+        fl = np.array([s.latency_ms for s in fixed])
+        extra = {"fixed_rate": {"rate_per_s": 0.8 * thr, "throughput_per_s": n_req / fwall,
+                                "latency_ms": {"p50": float(np.percentile(fl, 50)), "p99": float(np.percentile(fl, 99)),
+                                               "max": float(fl.max())}}}
     return {"requests": n_req, "sizes": list(sizes), "slots": slots, "closed_loop_solves_per_s": thr,
             "closed_loop_makespan_s": makespan, "open_loop_rate_per_s": 0.8 * thr,
-            "open_loop_throughput_per_s": n_req / wall,
+            "open_loop_throughput_per_s": n_req / wall, **extra,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "setup_ms_p50": float(np.median([s.setup_ms for s in opened])),
             "solve_ms_p50": float(np.median([s.solve_ms for s in opened])),
             "queue_ms_p50": float(np.median([s.queue_ms for s in opened])),
             "iterations_p50": float(np.median([s.iterations for s in opened])),
-            "converged": ok, "of": 2 * n_req, "peak_running": stats.peak_running,
+            "converged": ok, "of": (3 if fixed else 2) * n_req, "peak_running": stats.peak_running,
             "peak_used_gb": stats.peak_used_bytes / 1e9, "budget_gb": stats.budget_bytes / 1e9,
             "local_precision": "fp32"}
 
@@ -297,7 +308,7 @@ def run_serve_mode(args, rank, world, local):
     __graft_entry__.build()
     torch.cuda.set_device(local)
     sizes = tuple(int(s) for s in args.serve_sizes.split(","))
-    res = run_serving(args.requests, sizes, args.slots)
+    res = run_serving(args.requests, sizes, args.slots, fixed_rate=True)
     if rank == 0:
         line = {"metric": "served Stokes solves: p50/p99 latency (ms) under Poisson arrivals at 0.8x closed-loop "
                           "throughput", "value": res["latency_ms"]["p99"], "unit": "ms", "n_gpus": world,
@@ -335,12 +346,16 @@ def run_gdsw(args, rank, world, local):
     n = ctx.n
     lib = gdsw.load()
     import ctypes
-    fwd_bytes = []
-    while True:
-        d = ctypes.c_double()
-        if lib.gdsw_plan_bytes(ctx.h, 0, 0, len(fwd_bytes), ctypes.byref(d)) != 0:
-            break
-        fwd_bytes.append(d.value)
+    def plan_bytes(direction):
+        out = []
+        while True:
+            d = ctypes.c_double()
+            if lib.gdsw_plan_bytes(ctx.h, 0, direction, len(out), ctypes.byref(d)) != 0:
+                return out
+            out.append(d.value)
+            if direction == 2:
+                return out
+    fwd_bytes, bwd_bytes, red_bytes = plan_bytes(0), plan_bytes(1), plan_bytes(2)
     b = torch.zeros(n, dtype=torch.float64, device=dev)
     x = torch.zeros_like(b)
 
@@ -501,7 +516,7 @@ def run_gdsw(args, rank, world, local):
                      "peak": peak, "unit": "GB/s", "frac": (gemv_gbs / peak) if gemv_gbs else None,
                      "peak_kind": peak_kind, "avg_launch_ms": gemv_avg_ms, "avg_launch_bytes": gemv_avg_bytes,
                      "traffic": (ratio * gemv_avg_bytes) if ratio else None,
-                     "fwd_launch_bytes": fwd_bytes},
+                     "fwd_launch_bytes": fwd_bytes, "bwd_launch_bytes": bwd_bytes, "reduce_bytes": red_bytes},
         "autotune": {"tile_rows": [int(v) for v in list(tuned.tile_rows)[:tuned.levels - 1]],
                      "persistent": [int(v) for v in list(tuned.persistent)[:tuned.levels - 1]],
                      "local_solve_ms": [float(v) for v in list(tuned.tuned_ms)[:tuned.levels - 1]]},

@@ -234,7 +234,8 @@ int gdsw_level_entities(gdsw_ctx* ctx, int32_t level, int32_t* n_entities);
 int64_t gdsw_kernel_launches(void);
 
 /* Algorithmic bytes of one launch of the level-l local-solve sweeps: direction 0 = forward
- * launches (k = 0 .. K-1), 1 = backward launches (k = 0 .. K-2), in launch order.  Used to
+ * launches (k = 0 .. K-1), 1 = backward launches (k = 0 .. K-2), in launch order, 2 = the
+ * partial-sum reduction of the packed symmetric blocks (k = 0; 0 bytes when none).  Used to
  * put the DRAM traffic of a profiled launch beside the bytes the method must move. */
 int gdsw_plan_bytes(const gdsw_ctx* ctx, int32_t level, int32_t direction, int32_t k, double* bytes);
 

@@ -1673,6 +1673,12 @@ int64_t gdsw_kernel_launches(void) { return launch_counter(); }
 
 int gdsw_plan_bytes(const gdsw_ctx* c, int32_t level, int32_t direction, int32_t k, double* bytes) {
   if (!c || c->host_only || !bytes || level < 0 || level >= int(c->ld.size())) return GDSW_ERR_INVALID_ARG;
+  if (direction == 2) {
+    if (k != 0) return GDSW_ERR_INVALID_ARG;
+    *bytes = c->ld[level].red_bytes;
+    return GDSW_OK;
+  }
+  if (direction != 0 && direction != 1) return GDSW_ERR_INVALID_ARG;
   const std::vector<double>& v = direction == 0 ? c->ld[level].fwd_bytes : c->ld[level].bwd_bytes;
   if (k < 0 || k >= int(v.size())) return GDSW_ERR_INVALID_ARG;
   *bytes = v[k];
