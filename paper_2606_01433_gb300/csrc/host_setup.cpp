@@ -8,6 +8,8 @@
 #include <map>
 #include <thread>
 
+#include <atomic>
+
 #include "common.h"
 
 namespace gdsw {
@@ -31,6 +33,24 @@ static void parallel_for(int64_t n, F f) {
       for (int64_t i = a; i < b; ++i) f(i);
     });
   }
+  for (auto& x : th) x.join();
+}
+
+// n independent tasks of uneven size (one per part): dynamic scheduling over the threads
+template <typename F>
+static void parallel_tasks(int64_t n, F f) {
+  int nt = int(std::thread::hardware_concurrency());
+  nt = std::max(1, std::min<int>(nt, 32));
+  if (n <= 1 || nt == 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < std::min<int64_t>(nt, n); ++t)
+    th.emplace_back([&] {
+      for (int64_t i = next++; i < n; i = next++) f(i);
+    });
   for (auto& x : th) x.join();
 }
 
@@ -72,22 +92,29 @@ bool MeshHost::shares_element(int64_t a, int64_t b) const {
 // visit every node within +-2 of `node` (in each direction) that shares a fluid element
 template <typename F>
 static void for_neighbors(const MeshHost& M, int64_t node, F f) {
-  int i, j, k;
+  // mark the nodes of the fluid elements that hold `node` in its 5 x 5 x 5 window, then visit
+  // the marks in window order (= increasing node index)
+  int i, j, k, ei[2], ej[2], ek[2];
   M.coords(node, i, j, k);
-  for (int dk = -2; dk <= 2; ++dk) {
-    int kk = k + dk;
-    if (kk < 0 || kk >= M.NZ) continue;
-    for (int dj = -2; dj <= 2; ++dj) {
-      int jj = j + dj;
-      if (jj < 0 || jj >= M.NY) continue;
-      for (int di = -2; di <= 2; ++di) {
-        int ii = i + di;
-        if (ii < 0 || ii >= M.NX) continue;
-        int64_t w = ii + int64_t(M.NX) * (jj + int64_t(M.NY) * kk);
-        if (M.active[w] && M.shares_element(node, w)) f(w);
+  const int ni = elem_range(i, M.nx, ei), nj = elem_range(j, M.ny, ej), nk = elem_range(k, M.nz, ek);
+  bool mark[125] = {};
+  bool any = false;
+  for (int c = 0; c < nk; ++c)
+    for (int b = 0; b < nj; ++b)
+      for (int a = 0; a < ni; ++a) {
+        if (!M.mask[ei[a] + int64_t(M.nx) * (ej[b] + int64_t(M.ny) * ek[c])]) continue;
+        any = true;
+        const int x0 = 2 * ei[a] - i + 2, y0 = 2 * ej[b] - j + 2, z0 = 2 * ek[c] - k + 2;  // element corner in the window
+        for (int z = 0; z < 3; ++z)
+          for (int y = 0; y < 3; ++y)
+            for (int x = 0; x < 3; ++x) mark[(x0 + x) + 5 * ((y0 + y) + 5 * (z0 + z))] = true;
       }
-    }
-  }
+  if (!any) return;
+  for (int dz = 0; dz < 5; ++dz)
+    for (int dy = 0; dy < 5; ++dy)
+      for (int dx = 0; dx < 5; ++dx)
+        if (mark[dx + 5 * (dy + 5 * dz)])
+          f(int64_t(i + dx - 2) + int64_t(M.NX) * (int64_t(j + dy - 2) + int64_t(M.NY) * (k + dz - 2)));
 }
 
 // ------------------------------------------------------------------ mesh and patterns
@@ -101,14 +128,15 @@ static void build_sell(MeshHost& M) {
   for (int64_t r = 0; r < nv; ++r) order[r] = int32_t(r);
   auto alen = [&](int32_t r) { return M.a_ptr[r + 1] - M.a_ptr[r]; };
   auto blen = [&](int32_t r) { return M.bt_ptr[r + 1] - M.bt_ptr[r]; };
-  for (int64_t w0 = 0; w0 < nv; w0 += W) {
+  parallel_tasks((nv + W - 1) / W, [&](int64_t q) {
+    const int64_t w0 = q * W;
     auto b = order.begin() + w0, e = order.begin() + std::min(nv, w0 + W);
     std::sort(b, e, [&](int32_t x, int32_t y) {
       if (alen(x) != alen(y)) return alen(x) > alen(y);
       if (blen(x) != blen(y)) return blen(x) > blen(y);
       return x < y;
     });
-  }
+  });
   const int64_t ns = (nv + 31) / 32;
   M.sell_row.assign(ns * 32, -1);
   M.sell_aoff.assign(ns + 1, 0);
@@ -128,7 +156,7 @@ static void build_sell(MeshHost& M) {
   M.sell_asrc.assign(M.sell_aoff[ns], -1);
   M.sell_bcol.assign(M.sell_boff[ns], 0);
   M.sell_bsrc.assign(M.sell_boff[ns], -1);
-  for (int64_t sl = 0; sl < ns; ++sl)
+  parallel_for(ns, [&](int64_t sl) {
     for (int l = 0; l < 32; ++l) {
       const int32_t r = M.sell_row[sl * 32 + l];
       if (r < 0) continue;
@@ -143,6 +171,7 @@ static void build_sell(MeshHost& M) {
         M.sell_bsrc[slot] = M.bt_ptr[r] + j;
       }
     }
+  });
 }
 
 void build_mesh(MeshHost& M, const gdsw_mesh* m) {
@@ -195,49 +224,63 @@ void build_mesh(MeshHost& M, const gdsw_mesh* m) {
   M.n = M.nu + M.np;
   GDSW_CHECK(M.n < (int64_t(1) << 31), GDSW_ERR_INVALID_ARG, "problem too large for int32 dof indices");
 
-  // neighbour lists (free velocity, pressure, Dirichlet velocity) per row node
-  auto build = [&](const std::vector<int32_t>& rows, int which, std::vector<int32_t>& ptr,
-                   std::vector<int32_t>& col) {
-    int64_t nr = int64_t(rows.size());
-    std::vector<std::vector<int32_t>> tmp(nr);
+  // neighbour lists per row node, all three kinds from one scan of the neighbours: free
+  // velocity nodes, pressure nodes, Dirichlet nodes with a nonzero datum (the only ones the
+  // lifting needs); lists in increasing index
+  auto build = [&](const std::vector<int32_t>& rows, std::vector<int32_t>* ptr[3], std::vector<int32_t>* col[3]) {
+    const int64_t nr = int64_t(rows.size());
+    std::vector<std::vector<int32_t>> tmp[3];
+    for (int k = 0; k < 3; ++k)
+      if (ptr[k]) tmp[k].resize(nr);
     parallel_for(nr, [&](int64_t r) {
-      auto& out = tmp[r];
       for_neighbors(M, rows[r], [&](int64_t w) {
-        if (which == 0) {
-          if (M.vidx[w] >= 0) out.push_back(M.vidx[w]);
-        } else if (which == 1) {
-          if (M.pidx[w] >= 0) out.push_back(M.pidx[w]);
-        } else {
-          // Dirichlet neighbours with a nonzero datum (the only ones the lifting needs)
-          uint8_t t = M.tags[w];
-          bool nz = M.g[3 * w] != 0.0 || M.g[3 * w + 1] != 0.0 || M.g[3 * w + 2] != 0.0;
-          if ((t == GDSW_TAG_WALL || t == GDSW_TAG_INFLOW) && nz) out.push_back(int32_t(w));
+        if (ptr[0] && M.vidx[w] >= 0) tmp[0][r].push_back(M.vidx[w]);
+        if (ptr[1] && M.pidx[w] >= 0) tmp[1][r].push_back(M.pidx[w]);
+        if (ptr[2]) {
+          const uint8_t t = M.tags[w];
+          const bool nz = M.g[3 * w] != 0.0 || M.g[3 * w + 1] != 0.0 || M.g[3 * w + 2] != 0.0;
+          if ((t == GDSW_TAG_WALL || t == GDSW_TAG_INFLOW) && nz) tmp[2][r].push_back(int32_t(w));
         }
       });
-      std::sort(out.begin(), out.end());
+      for (int k = 0; k < 3; ++k)
+        if (ptr[k]) std::sort(tmp[k][r].begin(), tmp[k][r].end());
     });
-    ptr.assign(nr + 1, 0);
-    for (int64_t r = 0; r < nr; ++r) ptr[r + 1] = ptr[r] + int32_t(tmp[r].size());
-    col.resize(ptr[nr]);
-    for (int64_t r = 0; r < nr; ++r) std::copy(tmp[r].begin(), tmp[r].end(), col.begin() + ptr[r]);
+    for (int k = 0; k < 3; ++k) {
+      if (!ptr[k]) continue;
+      ptr[k]->assign(nr + 1, 0);
+      for (int64_t r = 0; r < nr; ++r) (*ptr[k])[r + 1] = (*ptr[k])[r] + int32_t(tmp[k][r].size());
+      col[k]->resize((*ptr[k])[nr]);
+      parallel_for(nr, [&](int64_t r) {
+        std::copy(tmp[k][r].begin(), tmp[k][r].end(), col[k]->begin() + (*ptr[k])[r]);
+      });
+    }
   };
-  build(M.vnode, 0, M.a_ptr, M.a_col);
-  build(M.vnode, 1, M.bt_ptr, M.bt_col);
-  build(M.pnode, 0, M.b_ptr, M.b_col);
-  build(M.vnode, 2, M.ad_ptr, M.ad_col);
-  build(M.pnode, 2, M.bd_ptr, M.bd_col);
+  {
+    std::vector<int32_t>* vp[3] = {&M.a_ptr, &M.bt_ptr, &M.ad_ptr};
+    std::vector<int32_t>* vc[3] = {&M.a_col, &M.bt_col, &M.ad_col};
+    build(M.vnode, vp, vc);
+    std::vector<int32_t>* pp[3] = {&M.b_ptr, nullptr, &M.bd_ptr};
+    std::vector<int32_t>* pc[3] = {&M.b_col, nullptr, &M.bd_col};
+    build(M.pnode, pp, pc);
+  }
   // symmetric velocity pattern: diagonal block of each row and the transpose of each block
   M.a_diag.assign(M.nv, -1);
   M.a_tpos.resize(M.a_col.size());
-  for (int64_t I = 0; I < M.nv; ++I)
+  std::atomic<int> asym(0);
+  parallel_for(M.nv, [&](int64_t I) {
     for (int32_t blk = M.a_ptr[I]; blk < M.a_ptr[I + 1]; ++blk) {
       int32_t J = M.a_col[blk];
       if (J == I) M.a_diag[I] = blk;
       auto r0 = M.a_col.begin() + M.a_ptr[J], r1 = M.a_col.begin() + M.a_ptr[J + 1];
       auto it = std::lower_bound(r0, r1, int32_t(I));
-      GDSW_CHECK(it != r1 && *it == int32_t(I), GDSW_ERR_INVALID_ARG, "asymmetric velocity pattern");
+      if (it == r1 || *it != int32_t(I)) {
+        asym = 1;
+        continue;
+      }
       M.a_tpos[blk] = int32_t(it - M.a_col.begin());
     }
+  });
+  GDSW_CHECK(asym == 0, GDSW_ERR_INVALID_ARG, "asymmetric velocity pattern");
   for (int64_t I = 0; I < M.nv; ++I) GDSW_CHECK(M.a_diag[I] >= 0, GDSW_ERR_INVALID_ARG, "missing diagonal block");
   // assembly units: for each upper block, the fluid elements holding both nodes
   GDSW_CHECK(int64_t(M.fluid.size()) < (int64_t(1) << 22), GDSW_ERR_INVALID_ARG,
@@ -286,14 +329,20 @@ void build_mesh(MeshHost& M, const gdsw_mesh* m) {
   M.asm_cta.push_back(int32_t(nnzb));
   // BT entry (I, P) has the value of B entry (P, I)
   M.bt2b.resize(M.bt_col.size());
-  for (int64_t I = 0; I < M.nv; ++I)
+  std::atomic<int> basym(0);
+  parallel_for(M.nv, [&](int64_t I) {
     for (int32_t e = M.bt_ptr[I]; e < M.bt_ptr[I + 1]; ++e) {
       int32_t P = M.bt_col[e];
       auto b0 = M.b_col.begin() + M.b_ptr[P], b1 = M.b_col.begin() + M.b_ptr[P + 1];
       auto it = std::lower_bound(b0, b1, int32_t(I));
-      GDSW_CHECK(it != b1 && *it == int32_t(I), GDSW_ERR_INVALID_ARG, "asymmetric B pattern");
+      if (it == b1 || *it != int32_t(I)) {
+        basym = 1;
+        continue;
+      }
       M.bt2b[e] = int32_t(it - M.b_col.begin());
     }
+  });
+  GDSW_CHECK(basym == 0, GDSW_ERR_INVALID_ARG, "asymmetric B pattern");
   build_sell(M);
 }
 
@@ -558,7 +607,7 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
 
   // ---- overlapping subdomains (Section 2.1: k layers of elements) ----
   std::vector<std::vector<int64_t>> onodes(N);
-  parallel_for(N, [&](int64_t i) {
+  parallel_tasks(N, [&](int64_t i) {
     int lo[3], hi[3], nn[3] = {M.nx, M.ny, M.nz};
     for (int d = 0; d < 3; ++d) {
       lo[d] = std::max(0, bb[i][d] - overlap);
@@ -617,7 +666,7 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
   });
   {
     std::vector<SlabSet> parts(N);
-    parallel_for(N, [&](int64_t i) { slab_order(M, onodes[i], slab_elems, parts[i]); });
+    parallel_tasks(N, [&](int64_t i) { slab_order(M, onodes[i], slab_elems, parts[i]); });
     SlabSet& S = L.loc;
     S = SlabSet();
     for (int i = 0; i < N; ++i) {
@@ -725,7 +774,7 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
     if (M.active[v] && nsh[v] == 1 && has_free(v)) inodes[sh[v][0]].push_back(v);
   {
     std::vector<SlabSet> parts(N);
-    parallel_for(N, [&](int64_t i) { slab_order(M, inodes[i], slab_elems, parts[i]); });
+    parallel_tasks(N, [&](int64_t i) { slab_order(M, inodes[i], slab_elems, parts[i]); });
     SlabSet& S = L.inter;
     S = SlabSet();
     for (int i = 0; i < N; ++i) {
