@@ -231,3 +231,21 @@ def full_solution(sys_, x):
     pr = np.zeros(p.n_nodes)
     pr[mesh.pnodes] = x[mesh.nu:]
     return u, pr
+
+
+def picard(prob, steps):
+    """The Picard linearisation of Section 3 iterated: starting from the frozen velocity u_0 =
+    prob.uk, step k assembles the Stokes operator with nu(u_k) at the Gauss points, solves the
+    lifted system exactly (SciPy sparse LU) and takes the new velocity (free values plus the
+    Dirichlet data) as u_{k+1}.  Returns the free-dof solutions x_1 .. x_steps."""
+    import copy
+    import scipy.sparse.linalg as spla
+    p = copy.copy(prob)
+    xs = []
+    for _ in range(steps):
+        S = assemble(p)
+        x = spla.spsolve(S["A"].tocsc(), lifted_rhs(S))
+        u, _ = full_solution(S, x)
+        xs.append(x)
+        p.uk = u
+    return xs

@@ -323,3 +323,28 @@ def test_local_matrices_invertible():
             assert s[-1] > 1e-10 * s[0]
     s = np.linalg.svd(P.A0[-1], compute_uv=False)
     assert s[-1] > 1e-10 * s[0]
+
+
+def test_picard_pins():
+    """Section 3 Picard iteration in the oracle: with n = 1 (Newtonian Carreau limit) nu does
+    not depend on u, so every iterate is the same Stokes solution; for a shear-thinning fluid
+    the increments shrink (a contraction on this mildly nonlinear case) and the last iterate
+    satisfies the nonlinear system A(nu(u)) x = b(nu(u)) to the size of the last increment."""
+    import numpy as np
+    from oracle import fem
+    from paper_2606_01433_gb300 import inputs as I
+    p1 = I.box_problem(3, 3, 3, (1, 1, 1), form="symmetric", uk_seed=4, lam=1.0, n=1.0, nu_inf=0.0)
+    xs = fem.picard(p1, 2)
+    assert np.linalg.norm(xs[1] - xs[0]) <= 1e-12 * np.linalg.norm(xs[0])
+    p = I.box_problem(3, 3, 3, (1, 1, 1), form="symmetric", uk_seed=4, lam=1.0, n=0.6, nu_inf=1e-2)
+    xs = fem.picard(p, 6)
+    inc = [np.linalg.norm(xs[k + 1] - xs[k]) / np.linalg.norm(xs[k + 1]) for k in range(5)]
+    assert all(inc[k + 1] < inc[k] for k in range(4)), inc
+    S0 = fem.assemble(p)
+    u, _ = fem.full_solution(S0, xs[-1])
+    import copy
+    q = copy.copy(p)
+    q.uk = u
+    S = fem.assemble(q)
+    res = np.linalg.norm(S["A"] @ xs[-1] - fem.lifted_rhs(S)) / np.linalg.norm(fem.lifted_rhs(S))
+    assert res <= 10 * inc[-1], (res, inc)
