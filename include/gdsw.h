@@ -189,6 +189,14 @@ int gdsw_solve_host(gdsw_ctx* ctx, const double* b_host, double* x_host, gdsw_so
  * or NULL to keep the current one) and re-assemble A_cal in place (a Picard step with a
  * frozen preconditioner). */
 int gdsw_reassemble(gdsw_ctx* ctx, const double* uk_host);
+/* Picard update of the nonlinear Carreau iteration (Section 3, the Picard half of its
+ * alternating Picard-Newton loop): the frozen velocity u_k becomes the velocity of the
+ * solution x (device FP64, free dofs in gdsw_solve order) at the free nodes and the Dirichlet
+ * data g at the others.  The next gdsw_reassemble(ctx, NULL) then evaluates nu(u_k) and
+ * re-assembles; the preconditioner keeps its factors (a frozen-preconditioner Picard step; a
+ * new context refactors).  Newton terms are not provided: they make A non-symmetric.
+ * Asynchronous on the context stream. */
+int gdsw_picard_update(gdsw_ctx* ctx, const double* x);
 
 /* ---- component access for tests and profiling (same arithmetic as the apply) ---- */
 

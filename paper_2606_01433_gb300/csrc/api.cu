@@ -1569,6 +1569,11 @@ int gdsw_solve_host(gdsw_ctx* c, const double* bh, double* xh, gdsw_solve_info* 
   }
 }
 
+int gdsw_picard_update(gdsw_ctx* c, const double* x) {
+  if (!c || c->host_only || !x) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, launch_picard_velocity(c, x, c->stream));
+}
+
 int gdsw_reassemble(gdsw_ctx* c, const double* uk) {
   if (!c || c->host_only) return GDSW_ERR_INVALID_ARG;
   GDSW_TRY(c, {

@@ -57,6 +57,7 @@ void convert(const void* src, int sprec, void* dst, int dprec, int64_t n, cudaSt
 
 // operator.cu
 void launch_viscosity(gdsw_ctx* c, cudaStream_t s);
+void launch_picard_velocity(gdsw_ctx* c, const double* x, cudaStream_t s);
 void launch_assembly(gdsw_ctx* c, cudaStream_t s);
 void launch_lift(gdsw_ctx* c, double* b, cudaStream_t s);
 void launch_spmv(gdsw_ctx* c, const double* x, double* y, const double* b, cudaStream_t s);

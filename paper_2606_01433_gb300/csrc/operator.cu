@@ -453,6 +453,26 @@ void upload_tables(gdsw_ctx* c, cudaStream_t s) {
   c->d_tables = d;
 }
 
+// Picard update (Section 3): u_k at every free velocity node from the solution x (free dofs in
+// solve order); the Dirichlet nodes keep their data g (copied before this kernel)
+__global__ void k_picard_velocity(const int32_t* __restrict__ vnode, int64_t nv, const double* __restrict__ x,
+                                  double* __restrict__ uk) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 3 * nv) return;
+  const int64_t I = q / 3;
+  uk[3 * int64_t(vnode[I]) + (q - 3 * I)] = x[q];
+}
+
+void launch_picard_velocity(gdsw_ctx* c, const double* x, cudaStream_t s) {
+  const int64_t nv = c->mesh.nv;
+  GDSW_CUDA(cudaMemcpyAsync(c->d_uk, c->d_gdir, sizeof(double) * 3 * c->mesh.nnodes, cudaMemcpyDeviceToDevice, s));
+  if (nv > 0) {
+    k_picard_velocity<<<int((3 * nv + 255) / 256), 256, 0, s>>>(c->d_vnode, nv, x, c->d_uk);
+    check_launch("k_picard_velocity");
+  }
+  c->has_uk = true;
+}
+
 void launch_viscosity(gdsw_ctx* c, cudaStream_t s) {
   int64_t nfe = int64_t(c->mesh.fluid.size());
   int64_t n = nfe * 27;

@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
         "gdsw_kernel_launches": ([], i64),
         "gdsw_plan_bytes": ([vp, i32, i32, i32, C.POINTER(C.c_double)], C.c_int),
         "gdsw_set_local_sweep": ([vp, i32, i32, i32], C.c_int),
+        "gdsw_picard_update": ([vp, vp], C.c_int),
         "gdsw_profile_enable": ([vp, i32], C.c_int),
         "gdsw_profile_read": ([vp, C.POINTER(gdsw_profile)], C.c_int),
         "gdsw_profile_reset": ([vp], C.c_int),
@@ -245,6 +246,21 @@ class Context:
             return self._check(self.lib.gdsw_reassemble(self.h, None))
         u = _np(uk, np.float64)
         return self._check(self.lib.gdsw_reassemble(self.h, u.ctypes.data))
+
+    def gdsw_picard_update(self, x):
+        """u_k <- velocity of the device solution x (free nodes) and the Dirichlet data."""
+        return self._check(self.lib.gdsw_picard_update(self.h, _ptr(x)))
+
+    def picard_step(self, x, b):
+        """One Section 3 Picard step with the frozen preconditioner of this context: re-evaluate
+        nu(u_k) and re-assemble, lift the right-hand side into b, solve into x (warm start from
+        the previous iterate), then take u_{k+1} from x.  x, b: device FP64 vectors of length n.
+        Returns the solve's gdsw_solve_info."""
+        self.gdsw_reassemble()
+        self.gdsw_rhs_lift(b)
+        info = self.gdsw_solve(b, x)
+        self.gdsw_picard_update(x)
+        return info
 
     def gdsw_apply_local(self, level, r, z):
         return self._check(self.lib.gdsw_apply_local(self.h, level, _ptr(r), _ptr(z)))
