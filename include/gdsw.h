@@ -263,6 +263,13 @@ int gdsw_plan_bytes(const gdsw_ctx* ctx, int32_t level, int32_t direction, int32
  * keeps its mode (GDSW_ERR_INVALID_ARG). */
 int gdsw_set_local_sweep(gdsw_ctx* ctx, int32_t persistent, int32_t ctas_per_sm, int32_t tile_rows);
 
+/* Failure-path self-test of the persistent sweep's bounded waits: runs the level-1 sweep once
+ * with one dependency raised beyond what its producers signal, so that wait can never be met.
+ * The wait gives up after its 1 s limit, every CTA returns, and the call reports
+ * GDSW_ERR_TIMEOUT (GDSW_ERR_CUDA if no timeout was seen).  The GPU is never left waiting;
+ * the context stays usable (the next apply starts from fresh counters and gathers anew). */
+int gdsw_sweep_wait_selftest(gdsw_ctx* ctx);
+
 int gdsw_profile_enable(gdsw_ctx* ctx, int32_t on);
 int gdsw_profile_read(gdsw_ctx* ctx, gdsw_profile* prof);
 int gdsw_profile_reset(gdsw_ctx* ctx);

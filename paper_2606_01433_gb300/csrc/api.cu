@@ -1690,6 +1690,48 @@ int gdsw_plan_bytes(const gdsw_ctx* c, int32_t level, int32_t direction, int32_t
   return GDSW_OK;
 }
 
+int gdsw_sweep_wait_selftest(gdsw_ctx* c) {
+  if (!c || c->host_only || c->ld.empty() || c->ld[0].sweep.nitems == 0) return GDSW_ERR_INVALID_ARG;
+  LevelDev& L = c->ld[0];
+  cudaStream_t s = c->stream;
+  DevArena tmp;
+  unsigned flag = 0;
+  try {
+    std::vector<SweepItem> items(L.sweep.nitems);
+    GDSW_CUDA(cudaMemcpyAsync(items.data(), L.sweep.d_items, sizeof(SweepItem) * items.size(), cudaMemcpyDeviceToHost, s));
+    GDSW_CUDA(cudaStreamSynchronize(s));
+    size_t q = 0;
+    while (q < items.size() && items[q].wait0 < 0) ++q;
+    GDSW_CHECK(q < items.size(), GDSW_ERR_INVALID_ARG, "level-1 sweep has no dependency to wait for");
+    items[q].need0 += 1;  // one more than its producers will ever signal
+    SweepPlan P = L.sweep;
+    P.d_items = tmp.upload(items, s);
+    if (L.prec == GDSW_FP64)
+      launch_sweep<double, double>(static_cast<const double*>(L.fac), static_cast<double*>(L.vec), P, c->d_sweep_flag,
+                                   L.sym_T, s);
+    else if (L.prec == GDSW_FP32)
+      launch_sweep<float, float>(static_cast<const float*>(L.fac), static_cast<float*>(L.vec), P, c->d_sweep_flag,
+                                 L.sym_T, s);
+    else
+      launch_sweep<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), static_cast<float*>(L.vec), P,
+                                         c->d_sweep_flag, L.sym_T, s);
+    GDSW_CUDA(cudaMemcpyAsync(&flag, c->d_sweep_flag, sizeof(flag), cudaMemcpyDeviceToHost, s));
+    GDSW_CUDA(cudaMemsetAsync(c->d_sweep_flag, 0, sizeof(unsigned), s));
+    GDSW_CUDA(cudaStreamSynchronize(s));
+  } catch (const gdsw::Error& e) {
+    tmp.free_all();
+    c->err = e.msg;
+    return e.code;
+  }
+  tmp.free_all();
+  if (!flag) {
+    c->err = "gdsw_sweep_wait_selftest: the unsatisfiable wait did not report a timeout";
+    return GDSW_ERR_CUDA;
+  }
+  c->err = "persistent local sweep: a dependency wait exceeded its time limit (self-test)";
+  return GDSW_ERR_TIMEOUT;
+}
+
 int gdsw_set_local_sweep(gdsw_ctx* c, int32_t persistent, int32_t ctas_per_sm, int32_t tile_rows) {
   if (!c || c->host_only || ctas_per_sm < 0) return GDSW_ERR_INVALID_ARG;
   if (tile_rows != 0 && tile_rows != 32 && tile_rows != 64 && tile_rows != 128) return GDSW_ERR_INVALID_ARG;

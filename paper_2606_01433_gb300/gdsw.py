@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         "gdsw_plan_bytes": ([vp, i32, i32, i32, C.POINTER(C.c_double)], C.c_int),
         "gdsw_set_local_sweep": ([vp, i32, i32, i32], C.c_int),
         "gdsw_picard_update": ([vp, vp], C.c_int),
+        "gdsw_sweep_wait_selftest": ([vp], C.c_int),
         "gdsw_profile_enable": ([vp, i32], C.c_int),
         "gdsw_profile_read": ([vp, C.POINTER(gdsw_profile)], C.c_int),
         "gdsw_profile_reset": ([vp], C.c_int),
@@ -246,6 +247,10 @@ class Context:
             return self._check(self.lib.gdsw_reassemble(self.h, None))
         u = _np(uk, np.float64)
         return self._check(self.lib.gdsw_reassemble(self.h, u.ctypes.data))
+
+    def gdsw_sweep_wait_selftest(self):
+        """Run the level-1 persistent sweep with one unreachable dependency (expects GDSW_ERR_TIMEOUT)."""
+        return self._check(self.lib.gdsw_sweep_wait_selftest(self.h))
 
     def gdsw_picard_update(self, x):
         """u_k <- velocity of the device solution x (free nodes) and the Dirichlet data."""

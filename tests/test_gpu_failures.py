@@ -1,7 +1,8 @@
 """Failure detection, injected on the host (no GPU fault, trap or hang): a non-finite
-right-hand side, an iteration cap, and a problem whose coarse operator is singular (pure
-Neumann data: translations and the pressure constant are in the kernel).  Each returns its
-status code and leaves the context usable."""
+right-hand side, an iteration cap, a problem whose coarse operator is singular (pure Neumann
+data: translations and the pressure constant are in the kernel), and a device wait that can
+never be met (the persistent sweep's bounded wait).  Each returns its status code and leaves
+the context usable."""
 import numpy as np
 import pytest
 
@@ -48,3 +49,25 @@ def test_singular_coarse_operator(lib):
     with pytest.raises(lib.GdswError) as e:
         lib.Context(p)
     assert e.value.code == lib.GDSW_ERR_SINGULAR
+
+
+def test_persistent_sweep_wait_limit(lib):
+    """A dependency of the persistent level sweep that its producers never signal: the wait ends
+    after its 1 s limit, every CTA returns, the call reports GDSW_ERR_TIMEOUT, and the same
+    context then solves normally."""
+    import time
+    p = I.box_problem(4, 4, 4, (2, 2, 2), levels=2, form="symmetric", uk_seed=3, lam=1.0, n=0.5, nu_inf=1e-3)
+    ctx = lib.Context(p, tol=1e-10, precision=("fp32",) * 3, phi_precision="fp32")
+    t0 = time.perf_counter()
+    with pytest.raises(lib.GdswError) as e:
+        ctx.gdsw_sweep_wait_selftest()
+    elapsed = time.perf_counter() - t0
+    assert e.value.code == lib.GDSW_ERR_TIMEOUT
+    assert 0.9 <= elapsed < 60.0, elapsed
+    ctx.gdsw_set_local_sweep(True, 0)
+    b = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.gdsw_rhs_lift(b)
+    x = torch.zeros_like(b)
+    info = ctx.gdsw_solve(b, x)
+    assert info.status == 0 and info.relres <= 1e-10
+    ctx.close()
