@@ -103,12 +103,11 @@ static T* ptr_at(void* base, int64_t off) {
   return static_cast<T*>(base) + off;
 }
 
-// ------------------------------------------------------------------ block-tridiagonal LDU factorisation
-// For slab blocks A_kk (diagonal), B_k (rows of slab k coupled to slab k-1) and C_k
-// (columns of slab k+1 coupled to slab k), compute in place
-//   S_0 = A_00, S_k = A_kk - B_k S_{k-1}^{-1} C_{k-1},  Sinv_k = S_k^{-1},
-//   G_k = B_k S_{k-1}^{-1},  W_k = S_k^{-1} C_k,
-// so that A = L D U with L_{k,k-1} = G_k, D = diag(S_k), U_{k,k+1} = W_k.
+// ------------------------------------------------------------------ block-tridiagonal LDL^T factorisation
+// For slab blocks A_kk (diagonal) and B_k (rows of slab k coupled to slab k-1; the operator is
+// symmetric, so the block above the diagonal is B_k^T), compute in place
+//   S_0 = A_00, S_k = A_kk - G_k B_k^T,  G_k = B_k S_{k-1}^{-1},  Sinv_k = S_k^{-1},
+// so that A = L D L^T with L_{k,k-1} = G_k and D = diag(S_k).
 template <typename T>
 static void factor_slabs(const SlabSet& S, T* fac, double& minpiv, cudaStream_t s) {
   DevArena tmp;
@@ -970,8 +969,8 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
     else
       launch_gather<float>(r, L.gdof, static_cast<float*>(L.vec), nv, s);
   }
-  // block-LDU sweeps: forward launches (S_k^{-1} y_k and the G_{k+1} update), then backward
-  // launches (W_k), every one a ragged batched GEMV over all parts of the level
+  // block-LDL^T sweeps: forward launches (S_k^{-1} y_k and the G_{k+1} update), then backward
+  // launches (G_{k+1}^T), every one a ragged batched GEMV over all parts of the level
   const int group = l == 0 ? GDSW_K_LOCAL : GDSW_K_COARSE;
   auto sweep = [&](const GemvPlan& P, int k, int ld, double bytes) {
     ProfScope ps(c, group, bytes, s);

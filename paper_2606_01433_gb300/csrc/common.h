@@ -239,7 +239,7 @@ struct LevelDev {
   void* fac = nullptr;          // factors in storage precision
   int64_t nfac = 0, nvec = 0;
   int32_t* gdof = nullptr;
-  GemvPlan fwd, bwd;            // forward launches (Sinv, G) and backward launches (W)
+  GemvPlan fwd, bwd;            // forward launches (Sinv, G) and backward launches (G^T)
   SweepPlan sweep;              // the same tiles as one persistent launch
   bool persistent = false;      // local solve as the persistent launch (else one launch per slab step)
   double tuned_ms = 0;          // autotuned local-solve time (0: not tuned)
