@@ -54,6 +54,7 @@ def parse():
                          "or one launch per slab step")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM of the persistent sweep (0 = all)")
     ap.add_argument("--tile-rows", type=int, default=0, help="rows per forward GEMV tile (0 = the autotuner's)")
+    ap.add_argument("--graph", type=int, default=0, help="1: the preconditioner apply replays a captured CUDA graph")
     ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals of mixed requests")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--serve-sizes", type=str, default="8,12,16,20,24,28,32")
@@ -337,7 +338,8 @@ def run_gdsw(args, rank, world, local):
         mixed = (args.mixed, args.mixed, args.mixed)
         wname = WORKLOAD if args.m == 32 else WORKLOAD.replace("channel32", "channel%d" % args.m)
     t0 = time.perf_counter()
-    ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8, restart=100, max_it=1000)
+    ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8, restart=100, max_it=1000,
+                       use_graph=bool(args.graph))
     setup_mixed_s = time.perf_counter() - t0
     if args.sweep != "auto":
         ctx.gdsw_set_local_sweep(args.sweep == "persistent", args.ctas_per_sm, args.tile_rows)
@@ -440,7 +442,7 @@ def run_gdsw(args, rank, world, local):
         c64.close()
         del c64
         torch.cuda.empty_cache()
-        ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8)
+        ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8, use_graph=bool(args.graph))
         if args.sweep != "auto":
             ctx.gdsw_set_local_sweep(args.sweep == "persistent", args.ctas_per_sm, args.tile_rows)
 
@@ -492,6 +494,7 @@ def run_gdsw(args, rank, world, local):
                    "subdomains": [int(v) for v in list(sizes.n_parts)[:sizes.levels - 1]],
                    "coarse": [int(v) for v in list(sizes.n_coarse)[:sizes.levels - 1]],
                    "local_precision": args.mixed, "krylov_precision": "f64", "tol": 1e-8, "restart": 100,
+                   "apply_graph": bool(args.graph),
                    "l2": "inputs larger than L2 (no flush)", "replicas": world},
         "iterations": iters[-1],
         "relres": relres,
