@@ -110,7 +110,7 @@ static T* ptr_at(void* base, int64_t off) {
 // so that A = L D L^T with L_{k,k-1} = G_k and D = diag(S_k).
 template <typename T>
 static void factor_slabs(const SlabSet& S, T* fac, double& minpiv, cudaStream_t s) {
-  DevArena tmp;
+  DevArena tmp(s);
   int64_t maxB = 1, maxC = 1;
   for (int k = 0; k < S.Kmax; ++k) {
     int64_t sb = 0, sc = 0;
@@ -162,7 +162,7 @@ static void factor_slabs(const SlabSet& S, T* fac, double& minpiv, cudaStream_t 
 template <typename T>
 static void sweep_multi(const SlabSet& S, const T* fac, T* R, T* W, const std::vector<int64_t>& toff,
                         const std::vector<int>& ldt, const std::vector<int>& nc, cudaStream_t s) {
-  DevArena tmp;
+  DevArena tmp(s);
   try {
     for (int k = 0; k < S.Kmax; ++k) {
       std::vector<GemmTaskP> g, d;
@@ -433,7 +433,7 @@ static void autotune_level1(gdsw_ctx* c) {
   for (double b : L.bwd_bytes) bytes += b;
   if (bytes < 64e6 || L.n <= 0) return;
   cudaStream_t s = c->stream;
-  DevArena tmp;
+  DevArena tmp(s);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   try {
     const int64_t n = c->mesh.n;
@@ -680,7 +680,7 @@ static void level1_locals(gdsw_ctx* c, double& minpiv) {
   LevelDev& L = c->ld[0];
   cudaStream_t s = c->stream;
   MatView A = matview(c);
-  DevArena tmp;
+  DevArena tmp(s);
   T* fac = tmp.alloc<T>(S.nfac);
   GDSW_CUDA(cudaMemsetAsync(fac, 0, S.nfac * sizeof(T), s));
   std::vector<int32_t> owner;
@@ -713,7 +713,7 @@ static void level1_coarse(gdsw_ctx* c, double* A0, double& minpiv) {
   const CoarseSpace& C = H.cs;
   cudaStream_t s = c->stream;
   MatView A = matview(c);
-  DevArena tmp;
+  DevArena tmp(s);
   try {
     T* fac = tmp.alloc<T>(S.nfac);
     GDSW_CUDA(cudaMemsetAsync(fac, 0, S.nfac * sizeof(T), s));
@@ -854,7 +854,7 @@ static void coarse_locals(gdsw_ctx* c, int l, double& minpiv) {
   const SlabSet& S = c->lh[l].loc;
   LevelDev& L = c->ld[l];
   cudaStream_t s = c->stream;
-  DevArena tmp;
+  DevArena tmp(s);
   T* fac = tmp.alloc<T>(S.nfac);
   GDSW_CUDA(cudaMemsetAsync(fac, 0, S.nfac * sizeof(T), s));
   std::vector<int64_t> oo(S.nsub);
@@ -889,7 +889,7 @@ static void coarse_basis(gdsw_ctx* c, int l, double* A0n, double& minpiv) {
   LevelDev& L = c->ld[l];
   cudaStream_t s = c->stream;
   const int64_t n = L.n, n0 = C.n0;
-  DevArena tmp;
+  DevArena tmp(s);
   try {
     double* fac = tmp.alloc<double>(S.nfac);
     GDSW_CUDA(cudaMemsetAsync(fac, 0, S.nfac * 8, s));
@@ -1190,6 +1190,8 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
   GDSW_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   GDSW_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   cudaStream_t s = c->stream;
+  c->arena.stream = s;  // context memory is allocated and freed in the order of its stream
+  c->arena.ordered = true;
   set_gemv_smem_limits();
   set_prolong_smem_limits();
   c->ld.assign(nlev, LevelDev());
@@ -1358,7 +1360,7 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
     GDSW_CUDA(cudaStreamSynchronize(s));
     double amax = 0.0;
     for (double v : hA) amax = std::max(amax, std::fabs(v));
-    DevArena tmp;
+    DevArena tmp(s);
     std::vector<double> mp;
     run_inverse<double>(tmp, {{c->d_coarsest_inv, int(n0), ldc, 0}}, mp, s);
     tmp.free_all();
@@ -1464,14 +1466,14 @@ void gdsw_destroy(gdsw_ctx* c) {
     delete c;
     return;
   }
-  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->stream2) cudaStreamSynchronize(c->stream2);
+  cudaStreamSynchronize(c->stream);
   if (c->apply_graph) cudaGraphExecDestroy(c->apply_graph);
   for (auto& p : c->pending) {
     c->ev_pool.push_back(p.a);
     c->ev_pool.push_back(p.b);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  if (c->h_scal) cudaFreeHost(c->h_scal);
   c->arena.free_all();
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -1693,7 +1695,7 @@ int gdsw_sweep_wait_selftest(gdsw_ctx* c) {
   if (!c || c->host_only || c->ld.empty() || c->ld[0].sweep.nitems == 0) return GDSW_ERR_INVALID_ARG;
   LevelDev& L = c->ld[0];
   cudaStream_t s = c->stream;
-  DevArena tmp;
+  DevArena tmp(s);
   unsigned flag = 0;
   try {
     std::vector<SweepItem> items(L.sweep.nitems);

@@ -42,14 +42,26 @@ inline void check_launch(const char* what) {
 }
 
 // ------------------------------------------------------------------ device memory
+// Stream-ordered when built with a stream (cudaMallocAsync / cudaFreeAsync on that stream):
+// freeing then never waits for the whole device, so contexts that set up, solve and tear down
+// on different streams (the solve server's slots) do not stall one another.  Memory of an
+// arena may only be used by work ordered after its allocation on that stream and freed after
+// the last such work.
 struct DevArena {
   std::vector<void*> ptrs;
   size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  bool ordered = false;
+  DevArena() = default;
+  explicit DevArena(cudaStream_t s) : stream(s), ordered(true) {}
   template <typename T>
   T* alloc(size_t n) {
     if (n == 0) n = 1;
     void* p = nullptr;
-    GDSW_CUDA(cudaMalloc(&p, n * sizeof(T)));
+    if (ordered)
+      GDSW_CUDA(cudaMallocAsync(&p, n * sizeof(T), stream));
+    else
+      GDSW_CUDA(cudaMalloc(&p, n * sizeof(T)));
     ptrs.push_back(p);
     bytes += n * sizeof(T);
     return static_cast<T*>(p);
@@ -60,16 +72,22 @@ struct DevArena {
     if (!v.empty()) GDSW_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     return p;
   }
+  void free_one(void* p) {
+    if (ordered)
+      cudaFreeAsync(p, stream);
+    else
+      cudaFree(p);
+  }
   void release(void* p) {
     for (auto& q : ptrs)
       if (q == p) {
-        cudaFree(q);
+        free_one(q);
         q = nullptr;
       }
   }
   void free_all() {
     for (void* p : ptrs)
-      if (p) cudaFree(p);
+      if (p) free_one(p);
     ptrs.clear();
     bytes = 0;
   }
@@ -349,7 +367,7 @@ struct gdsw_ctx {
   int m_alloc = 0;
   double *d_V = nullptr, *d_Z = nullptr, *d_w = nullptr, *d_H = nullptr, *d_gvec = nullptr;
   double *d_cs = nullptr, *d_sn = nullptr, *d_part = nullptr, *d_scal = nullptr, *d_y = nullptr;
-  double* h_scal = nullptr;         // pinned host mirror of a few scalars
+  double h_scal[8] = {0};           // host mirror of a few scalars
   int n_part_blocks = 0;
   int* d_status = nullptr;          // device error word
   // CUDA graph of the apply

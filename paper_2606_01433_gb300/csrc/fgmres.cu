@@ -176,7 +176,6 @@ static void ensure_workspace(gdsw_ctx* c, int m) {
   c->d_y = c->arena.alloc<double>(m + 1);
   c->d_part = c->arena.alloc<double>(int64_t(RB) * (m + 2));
   c->d_scal = c->arena.alloc<double>(8);
-  if (!c->h_scal) GDSW_CUDA(cudaMallocHost(&c->h_scal, 8 * sizeof(double)));
   c->m_alloc = m;
 }
 

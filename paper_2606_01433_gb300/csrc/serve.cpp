@@ -93,8 +93,8 @@ void run_job(gdsw_server* S, int slot, Job& J) {
     setup_impl(c, &J.req.mesh, &J.req.visc, &J.req.part, &J.req.levels, &o);
     double t1 = now_ms();
     cudaStream_t s = S->streams[slot];
-    GDSW_CUDA(cudaMalloc(&d_b, 8 * n));
-    GDSW_CUDA(cudaMalloc(&d_x, 8 * n));
+    GDSW_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_b), 8 * n, s));  // stream-ordered: no device-wide sync
+    GDSW_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_x), 8 * n, s));
     if (!J.rhs.empty())
       GDSW_CUDA(cudaMemcpyAsync(d_b, J.rhs.data(), 8 * n, cudaMemcpyHostToDevice, s));
     else
@@ -105,8 +105,8 @@ void run_job(gdsw_server* S, int slot, Job& J) {
     GDSW_CUDA(cudaMemcpyAsync(J.req.x, d_x, 8 * n, cudaMemcpyDeviceToHost, s));
     GDSW_CUDA(cudaStreamSynchronize(s));
     double t2 = now_ms();
-    cudaFree(d_b);
-    cudaFree(d_x);
+    cudaFreeAsync(d_b, s);
+    cudaFreeAsync(d_x, s);
     d_b = d_x = nullptr;
     gdsw_destroy(c);
     c = nullptr;
@@ -123,8 +123,9 @@ void run_job(gdsw_server* S, int slot, Job& J) {
     if (J.st.state == GDSW_REQ_DONE) S->stats.completed++;
     else S->stats.failed++;
   } catch (const gdsw::Error& e) {
-    if (d_b) cudaFree(d_b);
-    if (d_x) cudaFree(d_x);
+    if (d_b) cudaFreeAsync(d_b, S->streams[slot]);
+    if (d_x) cudaFreeAsync(d_x, S->streams[slot]);
+    if (d_b || d_x) cudaStreamSynchronize(S->streams[slot]);
     if (c) gdsw_destroy(c);
     std::lock_guard<std::mutex> lk(S->mu);
     if (reserved) {
