@@ -8,7 +8,7 @@ Tolerances (relative 2-norm unless stated):
     go through explicit inverses of Schur complements whose conditioning costs a few
     digits, which 1e-12 covers on these sizes;
   * FP64 preconditioner apply: <= 1e-11; FP64 FGMRES solution at the same tolerance:
-    <= 1e-10 and iteration counts within +-1 (the north-star bar);
+    <= 1e-10 and iteration counts within +-1;
   * mixed paths (FP32 / BF16 local factors, FP32 coarse basis): solved to a tolerance tight
     enough that the forward error against the FP64 oracle solution is <= 1e-8.
 Sizes span several 32-row GEMV tiles with ragged tails, 2-4 levels, obstacles (irregular
@@ -154,7 +154,7 @@ def test_apply_and_solve_fp64(lib, name):
 @pytest.mark.parametrize("name", ["channel16_obstacles", "die_rcb_4lvl", "box_4lvl"])
 @pytest.mark.parametrize("prec", [FP32, BF16], ids=["fp32", "bf16"])
 def test_mixed_precision_solve(lib, name, prec):
-    """North-star precision pattern: FP32 / BF16 local factors (FP32 accumulation), FP32
+    """Mixed precision: FP32 / BF16 local factors (FP32 accumulation), FP32
     coarse basis, recovered by the FP64 outer FGMRES: forward error <= 1e-8 against the
     FP64 oracle solution."""
     from oracle import fem, fgmres
