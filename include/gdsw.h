@@ -204,14 +204,15 @@ int gdsw_picard_update(gdsw_ctx* ctx, const double* x);
  * (D_i = I for plain weighting).  r, z: device FP64 vectors of that level's size. */
 int gdsw_apply_local(gdsw_ctx* ctx, int32_t level, const double* r, double* z);
 /* The same result as gdsw_apply_local, computed without allocating any memory: for callers
- * that must not call cudaMalloc/cudaFree while they run (work recorded into a CUDA graph whose
- * capture may not contain allocations, or a process that has handed every free byte of the
- * device to its own memory pool).  The paper has no counterpart; this is an interface
- * variant of the level-l local branch.
+ * that must not call cudaMalloc/cudaFree while they run -- a process that has handed every
+ * free byte of the device to its own memory pool, or a latency-critical loop that cannot
+ * afford the device-wide synchronisation a cudaFree implies.  The paper has no counterpart;
+ * this is an interface variant of the level-l local branch.
  *   - Scratch: a fixed 4 MiB (4,194,304-byte) 256-byte-aligned array in the library's device
  *     memory, held by every GPU that loads the library until the process exits.  The level's
- *     concatenated local vectors (2 x local dofs x 8 bytes for FP64 factors, x 4 for FP32/BF16)
- *     must fit; larger levels get GDSW_ERR_INVALID_ARG with the size in gdsw_last_error.
+ *     concatenated local vectors and the partial sums of its packed symmetric blocks
+ *     ((2 x local dofs + partials) x 8 bytes for FP64 factors, x 4 for FP32/BF16) must fit;
+ *     larger levels get GDSW_ERR_INVALID_ARG with the size in gdsw_last_error.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *     with that device current); make that first call before any stream capture.
  *   - Every call on a device shares the one array and leaves the last call's values in it;

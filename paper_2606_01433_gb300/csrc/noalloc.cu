@@ -4,10 +4,9 @@
 // a workspace allocated with the context -- lives in a fixed, file-scope device array.
 //
 // Who needs this: code that must not allocate device memory at solve time.  Examples are a
-// caller that records its work into a CUDA graph whose capture must not contain
-// allocations, or a service that has already handed all free device memory to its own pool
-// and cannot let a library call cudaMalloc/cudaFree (which would also synchronise the
-// device) in the middle of a request.
+// service that has already handed all free device memory to its own pool, and a
+// latency-critical loop that cannot let a library call cudaMalloc/cudaFree (a cudaFree also
+// synchronises the whole device) in the middle of a request.
 #include <mutex>
 
 #include "common.h"

@@ -1,6 +1,7 @@
 """gdsw_apply_local_noalloc: the local branch of a level computed without allocating memory
-(for callers that cannot call cudaMalloc while they run, e.g. inside a CUDA-graph capture or
-in a process whose device memory is all pre-reserved).  Its result must equal
+(for callers that cannot call cudaMalloc while they run, e.g. a process whose device memory is
+all pre-reserved by its own pool, or a latency-critical loop that cannot take the device-wide
+synchronisation of a cudaFree).  Its result must equal
 gdsw_apply_local's, call after call, since the two run the same kernels in the same order;
 only the scratch differs (a fixed device array instead of the context's workspace).
 
