@@ -31,8 +31,12 @@ Readings where the paper is silent (the same list is in the design notes):
   * weighting: "plain" (the paper's additive sum) or "pou" (prolongation weighted by the
     inverse multiplicity of each dof among the overlapping subdomains).
 
+Optional variant (two levels only): rotation modes per entity (rigid rotations about the
+entity's centroid), the null-space enrichment the paper leaves out.
+
 Parity status: pinned (partition of unity, constant reproduction, extension property,
-brute-force dense preconditioner, one-subdomain reduction, level collapse, symmetry).
+brute-force dense preconditioner, one-subdomain reduction, level collapse, symmetry; the
+rotation variant by rigid rotations lying in the range of Phi).
 """
 from __future__ import annotations
 
@@ -102,13 +106,14 @@ def _multiplicity_weights(dofs, n):
 
 
 def _coarse_columns(entity_modes):
-    """Number the coarse dofs: entities in order, modes in (ux, uy, uz, p) order."""
+    """Number the coarse dofs: entities in order, modes in (ux, uy, uz, p[, rx, ry, rz])
+    order."""
     col = {}
     nodes = []
     c = 0
     for e, modes in enumerate(entity_modes):
         dl, ml = [], []
-        for m in range(MODES):
+        for m in range(len(modes)):
             if modes[m]:
                 col[(e, m)] = c
                 dl.append(c); ml.append(m)
@@ -147,8 +152,14 @@ def overlapping_dofs(sys_, prob, overlap=1):
     return out
 
 
-def build_level1(sys_, prob, overlap=1, dense_local=False):
-    """First level from the mesh and the element partition (Section 2.1)."""
+def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False):
+    """First level from the mesh and the element partition (Section 2.1).
+
+    rotations=True adds, per entity with at least two free velocity nodes, the three rigid
+    rotations about the entity's centroid, e_a x (x - x_c), restricted to its velocity dofs
+    (modes rx, ry, rz after ux, uy, uz, p) -- the null-space enrichment that Section 2.1
+    leaves out of the monolithic space.  A rotation that vanishes on the entity (the one
+    about the line of a straight edge) is dropped."""
     mesh = sys_["mesh"]
     A = sys_["A"]
     n = A.shape[0]
@@ -216,33 +227,59 @@ def build_level1(sys_, prob, overlap=1, dense_local=False):
         for comp in _components(node_adj, members):
             entities.append((s, np.sort(comp)))
     entities.sort(key=lambda t: (t[0], int(t[1][0])))
-    ent_modes = []
+    # node coordinates: Q2 node (i, j, k) at origin + (h/2)(i, j, k)
+    nid = np.arange(nn)
+    xyz = np.asarray(prob.origin, dtype=np.float64)[None, :] + 0.5 * prob.h * np.stack(
+        [nid % mesh.nxn, (nid // mesh.nxn) % mesh.nyn, nid // (mesh.nxn * mesh.nyn)], axis=1)
+    ent_modes, ent_rot = [], []
     for s, nodes in entities:
         hv = (mesh.vindex[nodes] >= 0).any()
         hp = (mesh.pindex[nodes] >= 0).any()
-        ent_modes.append([hv, hv, hv, hp])
+        modes = [hv, hv, hv, hp]
+        rot = None
+        if rotations:
+            vn = nodes[mesh.vindex[nodes] >= 0]
+            rot = np.zeros((vn.size, 3, 3))      # rot[node, mode a, component c]
+            if vn.size >= 2:
+                d = xyz[vn] - xyz[vn].mean(axis=0)
+                for a in range(3):
+                    rot[:, a, :] = np.cross(np.eye(3)[a][None, :], d)
+            keep = [np.linalg.norm(rot[:, a, :]) > 1e-8 * prob.h for a in range(3)]
+            modes += keep
+        ent_modes.append(modes)
+        ent_rot.append(rot)
     col, n0, cnodes = _coarse_columns(ent_modes)
-    # Phi_Gamma: Gamma dof -> coarse column
-    g_rows, g_cols = [], []
+    # Phi_Gamma: Gamma dof -> coarse column (translations and the pressure constant are
+    # indicators; rotations carry the coordinates relative to the entity's centroid)
+    g_rows, g_cols, g_vals = [], [], []
     for e, (s, nodes) in enumerate(entities):
         v = vnode_dof[nodes]
         v = v[v >= 0]
         for c in range(3):
             g_rows.append(v + c); g_cols.append(np.full(v.size, col[(e, c)]) if v.size else np.zeros(0, int))
+            g_vals.append(np.ones(v.size))
         pdofs = pnode_dof[nodes]
         pdofs = pdofs[pdofs >= 0]
         if pdofs.size:
-            g_rows.append(pdofs); g_cols.append(np.full(pdofs.size, col[(e, 3)]))
+            g_rows.append(pdofs); g_cols.append(np.full(pdofs.size, col[(e, 3)])); g_vals.append(np.ones(pdofs.size))
+        if rotations:
+            for a in range(3):
+                if (e, 4 + a) not in col:
+                    continue
+                for c in range(3):
+                    g_rows.append(v + c); g_cols.append(np.full(v.size, col[(e, 4 + a)]))
+                    g_vals.append(ent_rot[e][:, a, c])
     g_rows = np.concatenate(g_rows) if g_rows else np.zeros(0, int)
     g_cols = np.concatenate(g_cols) if g_cols else np.zeros(0, int)
-    PhiG = sp.csr_matrix((np.ones(g_rows.size), (g_rows, g_cols)), shape=(n, n0))
+    g_vals = np.concatenate(g_vals) if g_vals else np.zeros(0)
+    PhiG = sp.csr_matrix((g_vals, (g_rows, g_cols)), shape=(n, n0))
     gamma = np.zeros(n, dtype=bool)
     gamma[g_rows] = True
     # interior dofs of each subdomain: free dofs of nodes with sharing set {i}
     inter_nodes = np.nonzero((nsh == 1) & has_free)[0]
     owner = NS.indices[NS.indptr[inter_nodes]]
     lev.interior = []
-    Phi_rows, Phi_cols, Phi_vals = [g_rows], [g_cols], [np.ones(g_rows.size)]
+    Phi_rows, Phi_cols, Phi_vals = [g_rows], [g_cols], [g_vals]
     AG = A[:, gamma.nonzero()[0]] @ PhiG[gamma.nonzero()[0]]       # A_{:,Gamma} Phi_Gamma
     AG = AG.tocsr()
     for i in range(N):
@@ -349,12 +386,14 @@ class GDSW:
     """Multilevel monolithic GDSW preconditioner (Section 2.2 four-level equation, for
     L = 2, 3, 4 levels)."""
 
-    def __init__(self, sys_, prob, levels=None, weighting="pou", overlap=1, dense_local=False):
+    def __init__(self, sys_, prob, levels=None, weighting="pou", overlap=1, dense_local=False, rotations=False):
         L = prob.levels if levels is None else levels
+        if rotations and L > 2:
+            raise ValueError("rotation modes are defined for two-level GDSW only")
         self.L = L
         self.weighting = weighting
         self.levels = []
-        lev, A0 = build_level1(sys_, prob, overlap=overlap, dense_local=dense_local)
+        lev, A0 = build_level1(sys_, prob, overlap=overlap, dense_local=dense_local, rotations=rotations)
         self.levels.append(lev)
         self.A0 = [sys_["A"], A0]
         for l in range(2, L):

@@ -348,3 +348,32 @@ def test_picard_pins():
     S = fem.assemble(q)
     res = np.linalg.norm(S["A"] @ xs[-1] - fem.lifted_rhs(S)) / np.linalg.norm(fem.lifted_rhs(S))
     assert res <= 10 * inc[-1], (res, inc)
+
+
+def test_rotation_modes_pin():
+    """Rotations in the coarse null space (the variant Section 2.1 leaves out): with the three
+    rigid rotations per entity about its centroid, a global rigid rotation of the pure-Neumann
+    symmetric-form problem lies exactly in the range of Phi (it is in the kernel of A, so its
+    discrete extension reproduces it); without them it does not.  The default coarse space is
+    unchanged by the option."""
+    import numpy as np
+    from oracle import fem, gdsw as og
+    from paper_2606_01433_gb300 import inputs as I
+    p = I.box_problem(4, 4, 4, (2, 2, 2), levels=2, form="symmetric", bc="neumann")
+    S = fem.assemble(p)
+    m = S["mesh"]
+    nid = m.vnodes
+    xyz = np.stack([nid % m.nxn, (nid // m.nxn) % m.nyn, nid // (m.nxn * m.nyn)], axis=1) * 0.5 * p.h
+    r = np.zeros(S["A"].shape[0])
+    d = xyz - np.array([0.37, 0.52, 0.41])
+    r[:m.nu] = np.cross(np.array([0.3, -0.5, 0.8])[None, :], d).ravel()   # rigid rotation, p = 0
+    assert np.linalg.norm(S["A"] @ r) <= 1e-10 * np.linalg.norm(r)          # in the kernel of A
+    rot, _ = og.build_level1(S, p, rotations=True)
+    plain, _ = og.build_level1(S, p)
+    base = og.build_level1(S, p, rotations=False)[0]
+    assert (plain.Phi != base.Phi).nnz == 0 and rot.n0 > plain.n0
+    for lev, ok in ((rot, True), (plain, False)):
+        Phi = lev.Phi.toarray()
+        c = np.linalg.lstsq(Phi, r, rcond=None)[0]
+        res = np.linalg.norm(Phi @ c - r) / np.linalg.norm(r)
+        assert (res <= 1e-10) if ok else (res >= 1e-3), (ok, res)
