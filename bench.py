@@ -47,8 +47,8 @@ def parse():
                     help="channel: 32^3 Carreau channel (3 levels); die: 64x64x128 die-like channel (4 levels)")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
-    ap.add_argument("--prof-stride", type=int, default=8,
-                    help="CUDA-event timing of every k-th preconditioner apply inside the timed region")
+    ap.add_argument("--prof-stride", type=int, default=1,
+                    help="CUDA-event timing of every k-th preconditioner apply in the profiled pass")
     ap.add_argument("--sweep", choices=["auto", "persistent", "steps"], default="auto",
                     help="local solves: the set-up autotuner's choice, one persistent launch per level, "
                          "or one launch per slab step")
@@ -157,88 +157,138 @@ def barrier(world):
         dist.barrier()
 
 
-# ----------------------------------------------------------------------------- CPU oracle sample
-def oracle_sample(p, iterations, repeats=1):
-    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the same workload and
-    scale it to ms per step: 1/16 of the elements assembled (x16), one median-size level-1
-    subdomain solve with its sparse LU (x64 subdomains per apply; the LU itself is set-up,
-    excluded like the GPU factorisation), one SpMV, per FGMRES iteration x iterations."""
+# ----------------------------------------------------------------------------- CPU oracle
+GOLDEN = os.path.join(ROOT, "tests", "golden", "channel32_oracle.json")
+
+
+def oracle_iterations(p):
+    """The oracle's own FGMRES iteration count on this workload (to 1e-8), from the golden
+    file that tests/golden/make_channel32_oracle.py writes with oracle/ alone."""
+    d = json.load(open(GOLDEN))
+    assert d["workload"] == p.name and d["tol"] == 1e-8, "golden file is for another workload"
+    return int(d["iterations"]), d
+
+
+def oracle_sample(p):
+    """cpu_baseline: the FP64 oracle, as it stands, on a bounded sample of the workload, on
+    a pool of all host cores (oracle/parallel.py), scaled to ms per step.  Sample: the full
+    assembly (pool threads), the factorisation of one level-1 subdomain per worker (spread
+    over the size range; set-up, excluded) and one parallel round of their local solves, one
+    SpMV; per step = assembly + its x (64/W rounds of local solves + SpMV), with the
+    oracle's own iteration count its (golden file).  Coarse levels, Phi products and the
+    Arnoldi work are left out of this sample; the reference arm times them."""
     import numpy as np
-    import scipy.sparse.linalg as spla
     from oracle import fem, gdsw as og
-    from paper_2606_01433_gb300 import inputs as I
-    # assembly on a 1/16 element subset (a thin slab of the box)
-    q = I.Problem(**{k: getattr(p, k) for k in p.__dataclass_fields__})
-    q.mask = p.mask.copy()
-    ne = p.nx * p.ny * p.nz
-    keep = np.zeros(ne, dtype=bool)
-    keep[: ne // 16] = True
-    q.mask[~keep] = 0
-    t0 = time.perf_counter()
-    fem.assemble(q)
-    t_asm = (time.perf_counter() - t0) * 16
-    S = fem.assemble(p) if not hasattr(oracle_sample, "_S") else oracle_sample._S
-    oracle_sample._S = S
-    if not hasattr(oracle_sample, "_lu"):
-        lev_dofs = None
-        from paper_2606_01433_gb300 import gdsw as G
-        try:
-            ctx = G.Context(p, analyze_only=True)
-            lev_dofs = ctx.gdsw_level_dofs(0)
-            ctx.close()
-        except Exception:
-            lev_dofs = None
-        if lev_dofs is None:
-            lev, _ = og.build_level1(S, p)
-            lev_dofs = lev.dofs
-        sizes = [len(d) for d in lev_dofs]
-        med = int(np.argsort(sizes)[len(sizes) // 2])
-        d = lev_dofs[med]
-        oracle_sample._lu = spla.splu(S["A"][d][:, d].tocsc())
-        oracle_sample._nsub = len(lev_dofs)
-        oracle_sample._nloc = len(d)
-    lu = oracle_sample._lu
-    r = np.random.default_rng(0).standard_normal(oracle_sample._nloc)
-    x = np.random.default_rng(1).standard_normal(S["A"].shape[0])
-    t0 = time.perf_counter()
-    for _ in range(repeats):
-        lu.solve(r)
-    t_loc = (time.perf_counter() - t0) / repeats
-    t0 = time.perf_counter()
-    S["A"] @ x
-    t_spmv = time.perf_counter() - t0
-    t_iter = oracle_sample._nsub * t_loc + 2 * t_spmv
-    ms = 1e3 * (t_asm + iterations * t_iter)
-    sample = ("1/16 of the elements assembled (x16); one median level-1 subdomain (%d dofs) sparse-LU solve "
-              "(x%d subdomains) + 2 SpMV per iteration, x%d FGMRES iterations; LU set-up excluded"
-              % (oracle_sample._nloc, oracle_sample._nsub, iterations))
-    return ms, sample
+    from oracle.parallel import HostPool
+    its, _ = oracle_iterations(p)
+    with HostPool() as pool:
+        t0 = time.perf_counter()
+        S = fem.assemble(p, pool=pool)
+        t_asm = time.perf_counter() - t0
+        A = S["A"]
+        dofs = og.overlapping_dofs(S, p)
+        order = np.argsort([len(d) for d in dofs], kind="stable")
+        pick = order[np.unique(np.linspace(0, len(dofs) - 1, min(pool.cores, len(dofs))).round().astype(int))]
+        pool.share_csr("A", A)
+        pool.factor("sample", "A", [dofs[i] for i in pick])
+        r = np.random.default_rng(0).standard_normal(A.shape[0])
+        pool.solve("sample", r)
+        t0 = time.perf_counter()
+        pool.solve("sample", r)
+        t_round = time.perf_counter() - t0
+        pool.matvec(A, r)
+        t0 = time.perf_counter()
+        pool.matvec(A, r)
+        t_spmv = time.perf_counter() - t0
+        cores = pool.cores
+    rounds = len(dofs) / len(pick)
+    ms = 1e3 * (t_asm + its * (rounds * t_round + t_spmv))
+    sample = ("oracle on a pool of %d host cores: full assembly (%.2f s); one parallel round of %d level-1 "
+              "subdomain solves (%.1f ms, x%.1f rounds per apply) + one SpMV (%.1f ms) per iteration, x%d oracle "
+              "iterations; factorisations excluded (set-up), coarse levels, Phi products and Arnoldi not sampled"
+              % (cores, t_asm, len(pick), 1e3 * t_round, rounds, 1e3 * t_spmv, its))
+    return ms, sample, cores
+
+
+def oracle_reference(p, steps, warmup):
+    """Reference arm: the complete FP64 oracle on a pool of all host cores.
+
+    Set-up (timed once, reported apart): assembly, the multilevel GDSW set-up and one
+    complete GDSW-FGMRES solve to 1e-8, which gives the oracle's own iteration count and its
+    Arnoldi/least-squares time.  Each step is a bounded sample: one complete preconditioner
+    apply (every level) and one SpMV of the oracle, timed; ms per step = assembly +
+    iterations x (apply + SpMV) + the solve's remaining Krylov work."""
+    import numpy as np
+    from oracle import fem, fgmres, gdsw as og
+    from oracle.parallel import HostPool
+    with HostPool() as pool:
+        t0 = time.perf_counter()
+        S = fem.assemble(p, pool=pool)
+        t_asm = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        P = og.GDSW(S, p, pool=pool)
+        t_setup = time.perf_counter() - t0
+        A = S["A"]
+        b = fem.lifted_rhs(S)
+        acc = {"apply": 0.0, "spmv": 0.0}
+
+        def timed(key, fn):
+            def run(v):
+                t = time.perf_counter()
+                out = fn(v)
+                acc[key] += time.perf_counter() - t
+                return out
+            return run
+        t0 = time.perf_counter()
+        x, info = fgmres.fgmres(timed("spmv", lambda v: pool.matvec(A, v)), b, timed("apply", P.apply),
+                                tol=1e-8, restart=100, max_it=1000)
+        t_solve = time.perf_counter() - t0
+        its = info["iterations"]
+        t_rest = t_solve - acc["apply"] - acc["spmv"]
+        rng = np.random.default_rng(0)
+        vals = []
+        wall0 = time.perf_counter()
+        for k in range(warmup + steps):
+            r = rng.standard_normal(A.shape[0])
+            t0 = time.perf_counter()
+            P.apply(r)
+            t_a = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            pool.matvec(A, r)
+            t_s = time.perf_counter() - t0
+            if k >= warmup:
+                vals.append(1e3 * (t_asm + its * (t_a + t_s) + t_rest))
+        wall = time.perf_counter() - wall0
+        cores = pool.cores
+    return {"ms": statistics.mean(vals), "cores": cores, "iterations": its, "relres": info["relres"],
+            "assembly_s": t_asm, "setup_s": t_setup, "full_solve_s": t_solve, "krylov_rest_s": t_rest,
+            "apply_s_mean": acc["apply"] / max(its, 1), "spmv_s_mean": acc["spmv"] / max(its + 2, 1),
+            "sample_wall_s": wall}
 
 
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
-    """The FP64 CPU oracle on the host cores, timed on a bounded sample per step."""
+    """The FP64 CPU oracle on the host cores (the reference arm)."""
     if rank != 0:
         return
     from paper_2606_01433_gb300 import inputs as I
     p = I.channel(args.m)
-    its = 55  # FGMRES iterations of this workload (measured on the GPU arm, FP32 and FP64 alike)
-    for _ in range(args.warmup):
-        oracle_sample(p, its)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ms, sample = oracle_sample(p, its)
-        vals.append(ms)
-    wall = time.perf_counter() - t0
-    v = statistics.mean(vals)
+    o = oracle_reference(p, args.steps, args.warmup)
+    v = o["ms"]
+    sample = ("complete oracle set-up and one complete solve to 1e-8 (%d iterations, %.1f s, assembly %.1f s) on a "
+              "pool of %d host cores; per step one complete oracle preconditioner apply + one SpMV, timed, scaled "
+              "by the oracle's iteration count, plus the assembly and the solve's remaining Krylov work"
+              % (o["iterations"], o["full_solve_s"], o["assembly_s"], o["cores"]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD if args.m == 32 else WORKLOAD.replace("channel32", "channel%d" % args.m),
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": o["cores"], "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "sample_wall_s": wall}
+            "oracle": {k: o[k] for k in ("iterations", "relres", "assembly_s", "setup_s", "full_solve_s",
+                                         "krylov_rest_s", "apply_s_mean", "spmv_s_mean", "sample_wall_s")},
+            "measured_complete_step_ms": 1e3 * (o["assembly_s"] + o["full_solve_s"])}
     print(json.dumps(line), flush=True)
 
 
@@ -369,8 +419,6 @@ def run_gdsw(args, rank, world, local):
 
     for _ in range(args.warmup):
         info = step(ctx)
-    ctx.gdsw_profile_enable(args.prof_stride)
-    ctx.gdsw_profile_reset()
     stream = torch.cuda.current_stream()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = Clocks(local)
@@ -395,9 +443,18 @@ def run_gdsw(args, rank, world, local):
     step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
     total_ms = allreduce_max(total_ms, world, dev)
+    relres = info.relres
+    # profiled pass: the same steps again with CUDA events around every kernel group of
+    # every prof_stride-th apply (per-kernel times for the roofline; kept out of the headline)
+    ctx.gdsw_profile_enable(args.prof_stride)
+    ctx.gdsw_profile_reset()
+    for _ in range(args.steps):
+        step(ctx)
+    torch.cuda.synchronize()
     prof = ctx.gdsw_profile_read()
     ctx.gdsw_profile_enable(False)
-    relres = info.relres
+    fp64_tflops = gdsw.probe_fma("fp64")
+    fp32_tflops = gdsw.probe_fma("fp32")
     # dominant kernel: the level-1 block-LDU sweep GEMV
     loc = prof["local"]
     gemv_gbs = loc["bytes"] / (loc["ms"] * 1e-3) / 1e9 if loc["ms"] > 0 else None
@@ -409,6 +466,15 @@ def run_gdsw(args, rank, world, local):
     spmv_gbs = sp["bytes"] / (sp["ms"] * 1e-3) / 1e9 if sp["ms"] > 0 else None
     ar = prof["arnoldi"]
     asm_ms = (prof["assembly"]["ms"] + prof["viscosity"]["ms"]) / args.steps
+    kernels = {}
+    for name, g in prof.items():
+        if g["calls"] > 0 and g["ms"] > 0:
+            kernels[name] = {"calls": int(g["calls"]), "ms_per_call": g["ms"] / g["calls"],
+                             "bytes_per_call": g["bytes"] / g["calls"],
+                             "gbs": g["bytes"] / (g["ms"] * 1e-3) / 1e9}
+    sizes0 = ctx.sizes
+    spmv_flops = 18.0 * sizes0.nnzb_A + 12.0 * sizes0.nnz_B
+    spmv_tflops = spmv_flops / (sp["ms"] / max(sp["calls"], 1) * 1e-3) / 1e12 if sp["ms"] > 0 else None
 
     # FP64 path for the mixed-vs-FP64 comparison
     fp64 = None
@@ -505,6 +571,13 @@ def run_gdsw(args, rank, world, local):
         "apply_gbs": apply_gbs,
         "apply_ms": ap["ms"] / max(ap["calls"], 1),
         "spmv_gbs": spmv_gbs,
+        "spmv_fp64": {"flops_per_call": spmv_flops, "tflops": spmv_tflops, "fp64_fma_peak_tflops": fp64_tflops,
+                      "frac_of_fp64_peak": (spmv_tflops / fp64_tflops) if spmv_tflops else None,
+                      "frac_of_hbm": (spmv_gbs / measured_peaks()[0]) if spmv_gbs else None},
+        "fma_probe_tflops": {"fp64": fp64_tflops, "fp32": fp32_tflops},
+        "kernels": kernels,
+        "profiled_pass": "kernel-group times from CUDA events on every %d-th apply of a second run of the same "
+                         "%d steps after the timed region" % (args.prof_stride, args.steps),
         "arnoldi_ms_per_solve": ar["ms"] / max(ar["calls"], 1) * iters[-1],
         "spmv_ms_per_solve": sp["ms"] / max(sp["calls"], 1) * (iters[-1] + 2),
         "fp64": fp64,
@@ -529,9 +602,9 @@ def run_gdsw(args, rank, world, local):
         "serving": serving,
     }
     if rank == 0:
-        if world == 1 and os.environ.get("GDSW_BENCH_NO_CPU") != "1":
-            ms, sample = oracle_sample(p, iters[-1])
-            line["cpu_baseline"] = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
+        if world == 1 and os.environ.get("GDSW_BENCH_NO_CPU") != "1" and args.workload == "channel" and args.m == 32:
+            ms, sample, cores = oracle_sample(p)
+            line["cpu_baseline"] = {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
         else:
             line["cpu_baseline"] = None
         line["throughput_solves_per_s"] = world * 1e3 / ms_step

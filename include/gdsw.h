@@ -57,6 +57,9 @@ enum gdsw_status {
 enum gdsw_tag { GDSW_TAG_INTERIOR = 0, GDSW_TAG_WALL = 1, GDSW_TAG_INFLOW = 2, GDSW_TAG_OUTFLOW = 3 };
 enum gdsw_form { GDSW_FORM_GRADIENT = 0, GDSW_FORM_SYMMETRIC = 1 };
 enum gdsw_precision { GDSW_FP64 = 0, GDSW_FP32 = 1, GDSW_BF16 = 2 };
+/* Engine of the FP32 set-up GEMMs (local factorisation, coarse basis): the tensor cores with
+ * the 3xTF32 split (AUTO, the default, for tasks of at least 96 x 96 outputs), or SIMT FMA. */
+enum gdsw_gemm_engine { GDSW_GEMM_AUTO = 0, GDSW_GEMM_SIMT = 1, GDSW_GEMM_TENSOR = 2 };
 enum gdsw_weighting { GDSW_WEIGHT_POU = 0, GDSW_WEIGHT_PLAIN = 1 };
 
 typedef struct gdsw_ctx gdsw_ctx;
@@ -198,6 +201,43 @@ int gdsw_reassemble(gdsw_ctx* ctx, const double* uk_host);
  * Asynchronous on the context stream. */
 int gdsw_picard_update(gdsw_ctx* ctx, const double* x);
 
+/* ---- geometric multigrid with the multilevel GDSW method as its coarse solver ----
+ * Section 3 of the paper also uses the Schwarz method as the coarse-grid solver of a
+ * geometric multigrid method: FGMRES preconditioned by it solves the coarsest problem to a
+ * relative residual of 1e-1.  Here the grids are contexts of nested voxel meshes (each twice
+ * as fine as the next, same fluid region), finest first, all on one stream: the fine grids
+ * set up with levels = 1 (operator only: assembly, SpMV, lifting), the coarsest with its
+ * multilevel GDSW preconditioner, whose FGMRES tolerance (gdsw_options.tol) is the
+ * coarse-solve tolerance.  gdsw_mg_create builds, on every fine grid, the element-Vanka
+ * patches (the free dofs of an element's 27 Q2 and 8 Q1 nodes; explicit inverses of the
+ * principal submatrices of the assembled operator, inverted in FP64 and stored in the
+ * smoother precision) and the transfer to the next coarser grid (nodal interpolation P of
+ * Q2 velocity and Q1 pressure, zero at coarse Dirichlet nodes; R = P^T), and attaches the
+ * V-cycle as the preconditioner of the finest context: gdsw_solve on grids[0] then runs FP64
+ * FGMRES preconditioned by V-cycles.  A smoothing step is a multiplicative sweep over the
+ * eight element colours (parity of the voxel indices): r = b - A z in FP64, then every patch
+ * e of the colour adds omega A_e^{-1} r_e to z.  The multigrid object does not own the grid
+ * contexts; destroy it before them.  Errors as for the other calls; a failed create leaves
+ * its reason in gdsw_mg_last_error(NULL). */
+typedef struct gdsw_mg gdsw_mg;
+typedef struct gdsw_mg_options {
+  double omega;                 /* Vanka damping (1 = undamped) */
+  int32_t pre, post;            /* smoothing steps before / after the coarse correction */
+  int32_t smoother_precision;   /* GDSW_FP32 (patch inverses and products in FP32) or GDSW_FP64 */
+} gdsw_mg_options;
+int gdsw_mg_create(gdsw_ctx* const* grids, int32_t ngrids, const gdsw_mg_options* opt, gdsw_mg** out);
+void gdsw_mg_destroy(gdsw_mg* mg);
+const char* gdsw_mg_last_error(const gdsw_mg* mg);
+/* z = V r: one V-cycle from a zero initial guess (device FP64 vectors of the finest grid). */
+int gdsw_mg_vcycle(gdsw_mg* mg, const double* r, double* z);
+/* steps smoothing steps on fine grid `grid` (0 = finest), x updated in place. */
+int gdsw_mg_smooth(gdsw_mg* mg, int32_t grid, const double* b, double* x, int32_t steps);
+/* zf += P xc from grid+1 to grid; rc = R rf = P^T rf from grid to grid+1. */
+int gdsw_mg_prolong(gdsw_mg* mg, int32_t grid, const double* xc, double* zf);
+int gdsw_mg_restrict(gdsw_mg* mg, int32_t grid, const double* rf, double* rc);
+/* V-cycles run, coarse solves and their total FGMRES iterations since creation. */
+int gdsw_mg_stats(const gdsw_mg* mg, int64_t* cycles, int64_t* coarse_solves, int64_t* coarse_iterations);
+
 /* ---- component access for tests and profiling (same arithmetic as the apply) ---- */
 
 /* Level l (0-based Schwarz level) local branch only: z = sum_i R_i^T D_i A_i^{-1} R_i r
@@ -214,7 +254,10 @@ int gdsw_apply_local(gdsw_ctx* ctx, int32_t level, const double* r, double* z);
  *     ((2 x local dofs + partials) x 8 bytes for FP64 factors, x 4 for FP32/BF16) must fit;
  *     larger levels get GDSW_ERR_INVALID_ARG with the size in gdsw_last_error.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- *     with that device current); make that first call before any stream capture.
+ *     with that device current); make that first call before any stream capture.  The
+ *     device current at the call must be the one the context was set up on (else
+ *     GDSW_ERR_INVALID_ARG).  The address is kept until the process exits: no call may
+ *     follow a cudaDeviceReset of that device.
  *   - Every call on a device shares the one array and leaves the last call's values in it;
  *     nothing has to start at zero (each entry read is written earlier in the same call).
  *     Calls that overlap on the GPU (other streams, other threads, other contexts) race.
@@ -241,6 +284,36 @@ int gdsw_level_entities(gdsw_ctx* ctx, int32_t level, int32_t* n_entities);
 
 /* Number of CUDA kernels this library has launched in this process (all contexts). */
 int64_t gdsw_kernel_launches(void);
+
+/* One FP32 GEMM task of the set-up: C = alpha op(A) op(B) + beta C, row-major device
+ * matrices (op(A) = A^T when trans_a, op(B) = B^T when trans_b; op(A) is M x K, op(B) K x N). */
+typedef struct gdsw_gemm_task {
+  const float* a;
+  const float* b;
+  float* c;
+  int32_t M, N, K, lda, ldb, ldc, trans_a, trans_b;
+  double alpha, beta;
+} gdsw_gemm_task;
+
+/* The batched FP32 GEMM of the set-up (the dense contractions of the local block-LDL^T
+ * factorisation of Section 2.1's A_i and of the coarse basis Phi_I = -A_II^{-1} A_IGamma
+ * Phi_Gamma): engine GDSW_GEMM_TENSOR runs every task on the tensor cores (tcgen05 kind::tf32,
+ * TMA-staged, 3xTF32 split, FP32 accumulation; needs M, N, K >= 1), GDSW_GEMM_SIMT on the
+ * SIMT kernels, GDSW_GEMM_AUTO as the set-up does.  Tasks must not overlap in C.  Synchronous
+ * (on the legacy default stream); GDSW_ERR_TIMEOUT if a pipeline wait of the tensor-core
+ * kernel gave up, GDSW_ERR_INVALID_ARG for a bad task. */
+int gdsw_gemm_f32(const gdsw_gemm_task* tasks, int32_t ntasks, int32_t engine);
+
+/* Default engine of the FP32 set-up GEMMs for contexts set up afterwards (process-wide). */
+int gdsw_set_gemm_engine(int32_t engine);
+
+/* FMA throughput of the current device in TFLOP/s (precision GDSW_FP64 or GDSW_FP32): one
+ * launch of independent fused multiply-add chains (8 per thread, 8 CTAs of 256 threads per
+ * SM), timed with CUDA events after a warm-up launch.  It is the arithmetic roofline of the
+ * FP64 operator kernels (SpMV, assembly, Arnoldi), which GB300's narrow FP64 pipe bounds
+ * rather than memory.  Synchronous; allocates a small output buffer with cudaMalloc.
+ * Returns GDSW_ERR_INVALID_ARG for another precision or a NULL pointer. */
+int gdsw_probe_fma(int32_t precision, double* tflops);
 
 /* Algorithmic bytes of one launch of the level-l local-solve sweeps: direction 0 = forward
  * launches (k = 0 .. K-1), 1 = backward launches (k = 0 .. K-2), in launch order, 2 = the

@@ -163,13 +163,15 @@ def element_divergence(h, tabs):
     return Be.reshape(8, 81)
 
 
-def assemble(prob, chunk=2048):
+def assemble(prob, chunk=2048, pool=None):
     """Assemble the full saddle-point operator on free dofs plus the coupling to the
     Dirichlet velocity dofs (for lifting).
 
     Returns dict with
       mesh, A_cal (n x n CSR, free dofs), A_fd (n x 3 n_dirichlet_nodes, free rows x
       Dirichlet velocity columns), g_d (3 n_dirichlet_nodes,) Dirichlet values, nu_q.
+    With a host pool (oracle/parallel.py) the element chunks and each round of their
+    pairwise sums run on its threads; the chunks and the summation tree are the serial ones.
     """
     mesh = Mesh(prob)
     tabs = reference_tables()
@@ -177,24 +179,27 @@ def assemble(prob, chunk=2048):
     Be = element_divergence(prob.h, tabs)
     ne = mesh.elems.size
     nu_tot, nd = mesh.nu, 3 * mesh.dnodes.size
+    run = map if pool is None else pool.map
 
     # global velocity column index: free -> [0, nu), Dirichlet -> nu + [0, nd)
     vcol = np.where(mesh.vindex >= 0, 3 * mesh.vindex, -1)
     dcol = np.where(mesh.dindex >= 0, nu_tot + 3 * mesh.dindex, -1)
     node_col = np.where(vcol >= 0, vcol, dcol)            # (n_nodes,)
     nvel = nu_tot + nd
-    parts = []
-    for s in range(0, ne, chunk):
+
+    def velocity_chunk(s):
         e = slice(s, min(ne, s + chunk))
         Ke = element_matrices(prob.form, prob.h, nu_q[e], tabs)       # (c, 81, 81)
         nodes = mesh.enodes[e]                                        # (c, 27)
         dof = (node_col[nodes][:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 81)
         r = np.repeat(dof[:, :, None], 81, axis=2).ravel()
         c = np.repeat(dof[:, None, :], 81, axis=1).ravel()
-        parts.append(sp.csr_matrix((Ke.ravel(), (r, c)), shape=(nvel, nvel)))
+        return sp.csr_matrix((Ke.ravel(), (r, c)), shape=(nvel, nvel))
+
+    parts = list(run(velocity_chunk, range(0, ne, chunk)))
     while len(parts) > 1:     # pairwise sums keep the peak memory low
-        parts = [parts[i] + parts[i + 1] if i + 1 < len(parts) else parts[i]
-                 for i in range(0, len(parts), 2)]
+        pairs = [parts[i:i + 2] for i in range(0, len(parts), 2)]
+        parts = list(run(lambda ab: ab[0] + ab[1] if len(ab) == 2 else ab[0], pairs))
     K = parts[0]
     # divergence rows (pressure) x velocity columns
     prow = mesh.pindex[mesh.epnodes]                                   # (ne, 8)

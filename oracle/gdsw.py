@@ -34,6 +34,11 @@ Readings where the paper is silent (the same list is in the design notes):
 Optional variant (two levels only): rotation modes per entity (rigid rotations about the
 entity's centroid), the null-space enrichment the paper leaves out.
 
+Optional mixed-precision emulation (`local_precision`): the inputs and outputs of every
+local solve of a level are rounded to FP32 or BF16 while the solve itself stays exact, so
+that iteration counts of the GPU's mixed path (FP32/BF16 local solves recovered by the FP64
+FGMRES) have an oracle counterpart.
+
 Parity status: pinned (partition of unity, constant reproduction, extension property,
 brute-force dense preconditioner, one-subdomain reduction, level collapse, symmetry; the
 rotation variant by rigid rotations lying in the range of Phi).
@@ -90,12 +95,44 @@ class SchwarzLevel:
     n0: int
     coarse_nodes: list    # per coarse node: (sharing-set tuple, dof list, mode list)
 
+    pool = None           # host pool holding this level's factors (oracle/parallel.py)
+    pool_key = None
+    rounding = None       # mixed-precision emulation: round local-solve inputs and outputs
+
+    def local_solves(self, r):
+        """[A_i^{-1} R_i r for every subdomain i], in subdomain order.  With a rounding
+        function the restricted inputs and the local solutions are rounded to that precision
+        (the local solve itself stays exact FP64)."""
+        if self.rounding is not None:
+            r = self.rounding(r)
+        if self.pool is not None:
+            z = self.pool.solve(self.pool_key, r)
+        else:
+            z = [s.solve(r[d]) for d, s in zip(self.dofs, self.solvers)]
+        return z if self.rounding is None else [self.rounding(zi) for zi in z]
+
     def apply_local(self, r, weighting):
         z = np.zeros_like(r)
-        for d, s, w in zip(self.dofs, self.solvers, self.weights):
-            zi = s.solve(r[d])
+        for d, zi, w in zip(self.dofs, self.local_solves(r), self.weights):
             z[d] += (w * zi) if weighting == "pou" else zi
         return z
+
+
+def round_fp32(x):
+    """Round to IEEE binary32, nearest-even (NumPy's conversion), back in FP64."""
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def round_bf16(x):
+    """Round to bfloat16, back in FP64: the nearest number with an 8-bit significand
+    (binary32's exponent range), ties to the even significand.  With x = m 2^e and
+    1/2 <= |m| < 1, m is rounded to a multiple of 2^-8 (exact scalings by powers of two and
+    NumPy's round-half-even rint); normal range only, which covers every value here."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+ROUNDING = {"fp64": None, "fp32": round_fp32, "bf16": round_bf16}
 
 
 def _multiplicity_weights(dofs, n):
@@ -152,8 +189,12 @@ def overlapping_dofs(sys_, prob, overlap=1):
     return out
 
 
-def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False):
+def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False, pool=None):
     """First level from the mesh and the element partition (Section 2.1).
+
+    With a host pool (oracle/parallel.py) the local factorisations and the interior solves
+    of the coarse basis run in its worker processes; the factors stay there and the level's
+    local solves go through the pool.
 
     rotations=True adds, per entity with at least two free velocity nodes, the three rigid
     rotations about the entity's centroid, e_a x (x - x_c), restricted to its velocity dofs
@@ -206,9 +247,14 @@ def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False):
         nodes = col.indices[col.data == deg[col.indices]]
         lev.dofs.append(node_dofs(nodes))
     lev.solvers = []
-    for d in lev.dofs:
-        Ai = A[d][:, d]
-        lev.solvers.append(LocalSolver(Ai.toarray() if dense_local else Ai))
+    if pool is not None and not dense_local:
+        pool.share_csr("A", A)
+        lev.pool, lev.pool_key = pool, "level1"
+        pool.factor(lev.pool_key, "A", lev.dofs)
+    else:
+        for d in lev.dofs:
+            Ai = A[d][:, d]
+            lev.solvers.append(LocalSolver(Ai.toarray() if dense_local else Ai))
     lev.weights, lev.mult = _multiplicity_weights(lev.dofs, n)
     lev.N = N
 
@@ -282,6 +328,7 @@ def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False):
     Phi_rows, Phi_cols, Phi_vals = [g_rows], [g_cols], [g_vals]
     AG = A[:, gamma.nonzero()[0]] @ PhiG[gamma.nonzero()[0]]       # A_{:,Gamma} Phi_Gamma
     AG = AG.tocsr()
+    blocks = []                      # (interior dofs, coupled columns, -A_IGamma Phi_Gamma)
     for i in range(N):
         I = node_dofs(inter_nodes[owner == i])
         lev.interior.append(I)
@@ -291,7 +338,13 @@ def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False):
         cols = np.unique(rhs.indices)
         if cols.size == 0:
             continue
-        X = LocalSolver(A[I][:, I]).solve(rhs[:, cols].toarray())
+        blocks.append((I, cols, rhs[:, cols].toarray()))
+    if pool is not None:
+        pool.share_csr("A", A)
+        Xs = pool.extend("A", [(I, R) for I, cols, R in blocks])
+    else:
+        Xs = [LocalSolver(A[I][:, I]).solve(R) for I, cols, R in blocks]
+    for (I, cols, R), X in zip(blocks, Xs):
         rr, cc = np.meshgrid(I, cols, indexing="ij")
         Phi_rows.append(rr.ravel()); Phi_cols.append(cc.ravel()); Phi_vals.append(X.ravel())
     lev.Phi = sp.csr_matrix((np.concatenate(Phi_vals), (np.concatenate(Phi_rows), np.concatenate(Phi_cols))),
@@ -301,7 +354,13 @@ def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False):
     lev.n0 = n0
     lev.coarse_nodes = [(entities[e][0], cnodes[e][0], cnodes[e][1]) for e in range(len(entities))]
     lev.entities = entities
-    A0 = (lev.Phi.T @ (A @ lev.Phi)).toarray() if n0 else np.zeros((0, 0))
+    if n0 == 0:
+        A0 = np.zeros((0, 0))
+    elif pool is None:
+        A0 = (lev.Phi.T @ (A @ lev.Phi)).toarray()
+    else:   # the same products, by row blocks on the pool's threads
+        AP = pool.row_product(A, lev.Phi)
+        A0 = pool.row_product(lev.Phi.T.tocsr(), AP).toarray()
     return lev, A0
 
 
@@ -386,14 +445,22 @@ class GDSW:
     """Multilevel monolithic GDSW preconditioner (Section 2.2 four-level equation, for
     L = 2, 3, 4 levels)."""
 
-    def __init__(self, sys_, prob, levels=None, weighting="pou", overlap=1, dense_local=False, rotations=False):
+    def __init__(self, sys_, prob, levels=None, weighting="pou", overlap=1, dense_local=False, rotations=False,
+                 pool=None, local_precision=None):
+        """local_precision: None (all FP64) or one of "fp64", "fp32", "bf16" per Schwarz level
+        (levels 1 .. L-1): the mixed-precision emulation rounds that level's local-solve inputs
+        and outputs to the given precision; the coarsest direct solve stays FP64."""
         L = prob.levels if levels is None else levels
         if rotations and L > 2:
             raise ValueError("rotation modes are defined for two-level GDSW only")
         self.L = L
         self.weighting = weighting
         self.levels = []
-        lev, A0 = build_level1(sys_, prob, overlap=overlap, dense_local=dense_local, rotations=rotations)
+        self.pool = pool
+        lev, A0 = build_level1(sys_, prob, overlap=overlap, dense_local=dense_local, rotations=rotations,
+                               pool=pool)
+        if pool is not None:      # the first level's transfers as row-block products
+            lev.PhiT = lev.Phi.T.tocsr()
         self.levels.append(lev)
         self.A0 = [sys_["A"], A0]
         for l in range(2, L):
@@ -402,6 +469,8 @@ class GDSW:
             self.levels.append(lev)
             self.A0.append(A0)
         self.coarsest = LocalSolver(A0)
+        for lev, prec in zip(self.levels, local_precision or ()):
+            lev.rounding = ROUNDING[prec]
 
     def apply(self, r, level=0):
         """z = B r, recursively: local sum on this level plus Phi (next level) Phi^T."""
@@ -409,12 +478,13 @@ class GDSW:
         z = lev.apply_local(r, self.weighting)
         if lev.n0 == 0:
             return z
-        r0 = lev.Phi.T @ r
+        pooled = self.pool is not None and level == 0
+        r0 = self.pool.matvec(lev.PhiT, r) if pooled else lev.Phi.T @ r
         if level + 1 == len(self.levels):
             x0 = self.coarsest.solve(r0)
         else:
             x0 = self.apply(r0, level + 1)
-        return z + lev.Phi @ x0
+        return z + (self.pool.matvec(lev.Phi, x0) if pooled else lev.Phi @ x0)
 
     def dense(self):
         """The preconditioner as a dense matrix (for small tests)."""

@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "libgdsw.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["api.cu", "dense.cu", "operator.cu", "schwarz.cu", "setup.cu", "fgmres.cu", "host_setup.cpp", "noalloc.cu",
-         "serve.cpp"]
+         "serve.cpp", "probe.cu", "tc_gemm.cu", "mg.cu"]
 
 
 def _nvcc() -> str:

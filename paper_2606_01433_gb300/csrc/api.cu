@@ -1093,6 +1093,11 @@ static void apply_precond_impl(gdsw_ctx* c, const double* r, double* z, cudaStre
 }
 
 void apply_precond(gdsw_ctx* c, const double* r, double* z, cudaStream_t s) {
+  if (c->ext_precond) {  // a preconditioner attached from outside (the multigrid V-cycle)
+    c->ext_precond(c->ext_data, r, z, s);
+    return;
+  }
+  GDSW_CHECK(!c->ld.empty(), GDSW_ERR_INVALID_ARG, "operator-only context has no preconditioner");
   if (c->prof.enabled) {
     c->prof_gate = (c->apply_count % c->prof_stride) == 0;
     ++c->apply_count;
@@ -1139,8 +1144,8 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
   GDSW_CHECK(mesh && visc && part && lv && opt, GDSW_ERR_INVALID_ARG, "null argument");
   GDSW_CHECK(mesh->nx > 0 && mesh->ny > 0 && mesh->nz > 0 && mesh->h > 0, GDSW_ERR_INVALID_ARG, "bad mesh size");
   GDSW_CHECK(mesh->mask && mesh->tags && mesh->g && part->elem_part, GDSW_ERR_INVALID_ARG, "null mesh array");
-  GDSW_CHECK(lv->levels >= 2 && lv->levels <= 4, GDSW_ERR_INVALID_ARG, "levels must be 2, 3 or 4");
-  GDSW_CHECK(part->n_groups == lv->levels - 2, GDSW_ERR_INVALID_ARG, "need levels-2 grouping arrays");
+  GDSW_CHECK(lv->levels >= 1 && lv->levels <= 4, GDSW_ERR_INVALID_ARG, "levels must be 1 (operator only), 2, 3 or 4");
+  GDSW_CHECK(part->n_groups == std::max(lv->levels - 2, 0), GDSW_ERR_INVALID_ARG, "need levels-2 grouping arrays");
   GDSW_CHECK(lv->overlap >= 1 && lv->overlap <= 4, GDSW_ERR_INVALID_ARG, "overlap must be 1..4");
   GDSW_CHECK(opt->slab_elems >= 0, GDSW_ERR_INVALID_ARG, "slab_elems must be >= 0");
   for (int l = 0; l < lv->levels - 1; ++l)
@@ -1158,7 +1163,7 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
     // ---- host symbolic set-up (shared by gdsw_analyze, gdsw_setup and the server's admission)
     build_mesh(c->mesh, mesh);
     c->lh.assign(nlev, LevelHost());
-    build_level1(c, part, lv->overlap, opt->slab_elems);
+    if (nlev > 0) build_level1(c, part, lv->overlap, opt->slab_elems);
     for (int l = 1; l < nlev; ++l) {
       GDSW_CHECK(part->groups[l - 1] != nullptr, GDSW_ERR_INVALID_ARG, "null grouping array");
       build_coarse_level(c, l, part->groups[l - 1], part->group_len[l - 1]);
@@ -1179,13 +1184,14 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
     }
     b += 8.0 * (2.0 * c->opt.restart + 2.0) * M.n;
     // the factorisation works in a temporary copy of the level-1 factors and interiors
-    b += double(c->lh[0].loc.nfac) * (opt->precision[0] == GDSW_FP64 ? 8 : 4);
+    if (nlev > 0) b += double(c->lh[0].loc.nfac) * (opt->precision[0] == GDSW_FP64 ? 8 : 4);
     c->est_device_bytes = int64_t(b);
     c->host_ready = true;
   }
   if (c->host_only) return;
   // NULL selects the legacy default stream, so calls order with other default-stream work
   c->stream = static_cast<cudaStream_t>(opt->stream);
+  GDSW_CUDA(cudaGetDevice(&c->device));
   GDSW_CUDA(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
   GDSW_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   GDSW_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
@@ -1261,6 +1267,10 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
   GDSW_CUDA(cudaStreamSynchronize(s));
   double t2 = now_ms();
   c->setup_ms[1] = t2 - t1;
+  if (nlev == 0) {  // operator only: assembly, SpMV and lifting, no Schwarz levels
+    c->setup_ms[5] = now_ms() - t0;
+    return;
+  }
   // ---- level 1
   double minpiv = 0;
   {

@@ -307,6 +307,10 @@ struct LevelDev {
 struct gdsw_ctx {
   std::string err;
   bool host_only = false;           // created by gdsw_analyze: no device state
+  int device = -1;                  // CUDA device current at set-up (owns every device buffer)
+  // preconditioner attached from outside (a multigrid V-cycle over this context's grid), or null
+  void (*ext_precond)(void* data, const double* r, double* z, cudaStream_t s) = nullptr;
+  void* ext_data = nullptr;
   bool host_ready = false;          // host symbolic structures built
   bool capturing = false;           // inside CUDA-graph capture (no profiling events)
   int prof_stride = 1;              // time every prof_stride-th apply (and the work after it)

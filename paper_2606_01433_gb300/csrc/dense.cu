@@ -699,13 +699,29 @@ __global__ void __launch_bounds__(256, 2) k_gemm_f32(const GemmTaskP* __restrict
   }
 }
 
+// Which kernel takes the FP32 tasks of 96 x 96 outputs and more: the tensor cores (3xTF32,
+// tc_gemm.cu; the default) or the SIMT 128 x 128 tiles below.
+static int g_gemm_engine = GDSW_GEMM_AUTO;
+void set_gemm_engine(int e) { g_gemm_engine = e; }
+int gemm_engine() { return g_gemm_engine; }
+
 template <typename T>
 void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s) {
+  run_gemm_engine<T>(tmp, tasks, s, g_gemm_engine);
+}
+
+template <typename T>
+void run_gemm_engine(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s, int engine) {
   if (tasks.empty()) return;
   std::vector<int32_t> tt, ti, bt, bi;  // 64-tiles (k_gemm), 128-tiles (k_gemm_f32)
+  std::vector<GemmTaskP> tc;             // tasks for the tensor cores
   for (size_t q = 0; q < tasks.size(); ++q) {
     const auto& t = tasks[q];
     if (t.M <= 0 || t.N <= 0) continue;
+    if (sizeof(T) == 4 && t.M >= 96 && t.N >= 96 && t.K >= 1 && engine != GDSW_GEMM_SIMT) {
+      tc.push_back(t);
+      continue;
+    }
     if (sizeof(T) == 4 && t.M >= 96 && t.N >= 96) {
       int nt = ((t.M + 127) / 128) * ((t.N + 127) / 128);
       for (int i = 0; i < nt; ++i) {
@@ -720,6 +736,7 @@ void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s
       ti.push_back(i);
     }
   }
+  if (!tc.empty()) run_gemm_tc(tc, s);
   if (tt.empty() && bt.empty()) return;
   GemmTaskP* d_t = tmp.upload(tasks, s);
   if (!tt.empty()) {
@@ -737,6 +754,7 @@ void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s
 }
 template void run_gemm<double>(DevArena&, const std::vector<GemmTaskP>&, cudaStream_t);
 template void run_gemm<float>(DevArena&, const std::vector<GemmTaskP>&, cudaStream_t);
+template void run_gemm_engine<float>(DevArena&, const std::vector<GemmTaskP>&, cudaStream_t, int);
 
 // ------------------------------------------------------------------ batched Gauss-Jordan inverse
 // In-place inversion of square blocks with partial pivoting, blocked by panels of NB

@@ -52,6 +52,12 @@ inline int gemvt_tile_cols(int prec) { return prec == GDSW_FP64 ? 32 : (prec == 
 template <typename T>
 void run_gemm(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s);
 template <typename T>
+void run_gemm_engine(DevArena& tmp, const std::vector<GemmTaskP>& tasks, cudaStream_t s, int engine);
+void set_gemm_engine(int e);
+int gemm_engine();
+// tc_gemm.cu: FP32 tasks on the tensor cores (3xTF32); synchronises the stream
+void run_gemm_tc(const std::vector<GemmTaskP>& tasks, cudaStream_t s);
+template <typename T>
 void run_inverse(DevArena& tmp, const std::vector<InvTaskP>& tasks, std::vector<double>& minpiv, cudaStream_t s);
 void convert(const void* src, int sprec, void* dst, int dprec, int64_t n, cudaStream_t s);
 

@@ -8,6 +8,7 @@
 // latency-critical loop that cannot let a library call cudaMalloc/cudaFree (a cudaFree also
 // synchronises the whole device) in the middle of a request.
 #include <mutex>
+#include <new>
 
 #include "common.h"
 #include "kernels.h"
@@ -21,13 +22,19 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of the scratch array, looked up once per device with that device current.
 // (In host code the array's name is only a host-side stand-in, never a device address.)
+// The cache holds until the process exits; a cudaDeviceReset unloads the module, after which
+// the cached address is stale, so no call may follow a reset of the device it was made on.
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[64] = {nullptr};
 
-static void* noalloc_scratch_address() {
-  int dev = -1;
-  GDSW_CUDA(cudaGetDevice(&dev));
+// dev: the device the context was set up on, which must be the current device.
+static void* noalloc_scratch_address(int dev) {
   GDSW_CHECK(dev >= 0 && dev < 64, GDSW_ERR_INVALID_ARG, "device ordinal out of range");
+  int cur = -1;
+  GDSW_CUDA(cudaGetDevice(&cur));
+  GDSW_CHECK(cur == dev, GDSW_ERR_INVALID_ARG,
+             "gdsw_apply_local_noalloc: the current device (" + std::to_string(cur) +
+                 ") is not the device the context was set up on (" + std::to_string(dev) + ")");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
@@ -86,11 +93,17 @@ extern "C" int gdsw_apply_local_noalloc(gdsw_ctx* c, int32_t level, const double
                "-byte scratch; use gdsw_apply_local";
       return GDSW_ERR_INVALID_ARG;
     }
-    void* vec = noalloc_scratch_address();
+    void* vec = noalloc_scratch_address(c->device);
     local_solve_into(c, level, r, z, vec, c->stream);
     return GDSW_OK;
   } catch (const gdsw::Error& e) {
     c->err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return GDSW_ERR_OOM;
+  } catch (...) {
+    c->err = "unknown error";
+    return GDSW_ERR_CUDA;
   }
 }

@@ -83,30 +83,50 @@ void launch_restrict_reduce(const void* yc, int prec, const double* r, const int
 
 // z[I_J[l]] += sum_j PhiT_J[j][l] x0[cols_J[j]]: one thread per interior dof, coalesced
 // along the rows of the stored transpose; every interior dof belongs to exactly one part.
+// Accumulation precision follows the stored basis: an FP64 basis accumulates in FP64; an FP32
+// basis forms each run of eight products in FP32 (x0 rounded to FP32 in shared memory, the
+// precision the basis itself carries) and adds the run totals in FP64, so the kernel issues
+// one FP64 add per eight columns instead of one FP64 FMA per column -- GB300's FP64 pipe
+// would otherwise bound it, far below the memory rate.
+template <typename TP>
+struct ProAcc {
+  using X = double;
+};
+template <>
+struct ProAcc<float> {
+  using X = float;
+};
+
 template <typename TP>
 __global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, const ProMeta* __restrict__ meta,
                                                  const int32_t* __restrict__ tile_part,
                                                  const int32_t* __restrict__ tile_col0,
                                                  const int32_t* __restrict__ idofs, const int32_t* __restrict__ cols,
                                                  const double* __restrict__ x0, double* __restrict__ z) {
-  extern __shared__ double xs[];
+  using X = typename ProAcc<TP>::X;
+  extern __shared__ double xs_raw[];
+  X* xs = reinterpret_cast<X*>(xs_raw);
   const int J = tile_part[blockIdx.x];
   const ProMeta m = meta[J];
-  for (int j = threadIdx.x; j < m.c; j += blockDim.x) xs[j] = x0[cols[m.coff + j]];
+  for (int j = threadIdx.x; j < m.c; j += blockDim.x) xs[j] = X(x0[cols[m.coff + j]]);
   __syncthreads();
   const int l = tile_col0[blockIdx.x] + threadIdx.x;
   if (l >= m.nI) return;
   double acc = 0.0;
   const TP* p = phiT + m.phi + l;
   int j = 0;
-  for (; j + 8 <= m.c; j += 8) {  // eight independent loads in flight, FMAs in column order
+  for (; j + 8 <= m.c; j += 8) {  // eight independent loads in flight, products in column order
     TP v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + int64_t(j + u) * m.ld);
+    X part = X(0);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc = fma(double(v[u]), xs[j + u], acc);
+    for (int u = 0; u < 8; ++u) part = fma(X(v[u]), xs[j + u], part);
+    acc += double(part);
   }
-  for (; j < m.c; ++j) acc = fma(double(__ldcs(p + int64_t(j) * m.ld)), xs[j], acc);
+  X part = X(0);
+  for (; j < m.c; ++j) part = fma(X(__ldcs(p + int64_t(j) * m.ld)), xs[j], part);
+  acc += double(part);
   int64_t g = idofs[m.ioff + l];
   z[g] += acc;
 }

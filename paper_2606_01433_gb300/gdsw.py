@@ -72,6 +72,19 @@ class gdsw_sizes_info(C.Structure):
                 ("tuned_ms", C.c_double * 3)]
 
 
+class gdsw_gemm_task(C.Structure):
+    _fields_ = [("a", C.c_void_p), ("b", C.c_void_p), ("c", C.c_void_p), ("M", C.c_int32), ("N", C.c_int32),
+                ("K", C.c_int32), ("lda", C.c_int32), ("ldb", C.c_int32), ("ldc", C.c_int32),
+                ("trans_a", C.c_int32), ("trans_b", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+GEMM_ENGINE = {"auto": 0, "simt": 1, "tensor": 2}
+
+
+class gdsw_mg_options(C.Structure):
+    _fields_ = [("omega", C.c_double), ("pre", C.c_int32), ("post", C.c_int32), ("smoother_precision", C.c_int32)]
+
+
 class gdsw_profile(C.Structure):
     _fields_ = [("enabled", C.c_int32), ("calls", C.c_int64 * 12), ("ms", C.c_double * 12),
                 ("bytes", C.c_double * 12)]
@@ -113,6 +126,17 @@ def load(path: str = LIB_PATH):
         "gdsw_level_dofs": ([vp, i32, dp, dp], C.c_int),
         "gdsw_level_entities": ([vp, i32, C.POINTER(i32)], C.c_int),
         "gdsw_kernel_launches": ([], i64),
+        "gdsw_probe_fma": ([i32, C.POINTER(C.c_double)], C.c_int),
+        "gdsw_gemm_f32": ([C.POINTER(gdsw_gemm_task), i32, i32], C.c_int),
+        "gdsw_mg_create": ([C.POINTER(vp), i32, C.POINTER(gdsw_mg_options), C.POINTER(vp)], C.c_int),
+        "gdsw_mg_destroy": ([vp], None),
+        "gdsw_mg_last_error": ([vp], C.c_char_p),
+        "gdsw_mg_vcycle": ([vp, dp, dp], C.c_int),
+        "gdsw_mg_smooth": ([vp, i32, dp, dp, i32], C.c_int),
+        "gdsw_mg_prolong": ([vp, i32, dp, dp], C.c_int),
+        "gdsw_mg_restrict": ([vp, i32, dp, dp], C.c_int),
+        "gdsw_mg_stats": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
+        "gdsw_set_gemm_engine": ([i32], C.c_int),
         "gdsw_plan_bytes": ([vp, i32, i32, i32, C.POINTER(C.c_double)], C.c_int),
         "gdsw_set_local_sweep": ([vp, i32, i32, i32], C.c_int),
         "gdsw_picard_update": ([vp, vp], C.c_int),
@@ -129,11 +153,46 @@ def load(path: str = LIB_PATH):
     return lib
 
 
+def probe_fma(precision="fp64"):
+    """FMA throughput of the current device in TFLOP/s (gdsw_probe_fma)."""
+    lib = load()
+    t = C.c_double()
+    rc = lib.gdsw_probe_fma(PREC[precision], C.byref(t))
+    if rc != GDSW_OK:
+        raise GdswError(rc, "gdsw_probe_fma failed")
+    return t.value
+
+
+def gemm_f32(tasks, engine="tensor"):
+    """Batched FP32 GEMM (gdsw_gemm_f32): tasks = [(A, B, C, trans_a, trans_b, alpha, beta)]
+    with contiguous float32 CUDA tensors; C = alpha op(A) op(B) + beta C in place."""
+    import torch
+    lib = load()
+    arr = (gdsw_gemm_task * max(len(tasks), 1))()
+    for i, (A, B, Cm, ta, tb, alpha, beta) in enumerate(tasks):
+        for t in (A, B, Cm):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise TypeError("expected contiguous float32 CUDA tensors")
+        M, K = (A.shape[1], A.shape[0]) if ta else (A.shape[0], A.shape[1])
+        N = B.shape[0] if tb else B.shape[1]
+        arr[i] = gdsw_gemm_task(A.data_ptr(), B.data_ptr(), Cm.data_ptr(), M, N, K, A.shape[1], B.shape[1],
+                                Cm.shape[1], int(ta), int(tb), float(alpha), float(beta))
+    rc = lib.gdsw_gemm_f32(arr, len(tasks), GEMM_ENGINE[engine])
+    if rc != GDSW_OK:
+        raise GdswError(rc, "gdsw_gemm_f32 failed")
+
+
+def set_gemm_engine(engine):
+    rc = load().gdsw_set_gemm_engine(GEMM_ENGINE[engine])
+    if rc != GDSW_OK:
+        raise GdswError(rc, "gdsw_set_gemm_engine failed")
+
+
 def declared_symbols():
     """Function names declared in include/gdsw.h (for the export check)."""
     import re
     hdr = open(os.path.join(os.path.dirname(HERE), "include", "gdsw.h")).read()
-    return sorted(set(re.findall(r"\b(gdsw_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"\b(gdsw_[a-z0-9_]+)\s*\(", hdr)))
 
 
 def _ptr(t):
@@ -174,7 +233,7 @@ class Context:
                            uk.ctypes.data if uk is not None else None)
         pa = gdsw_partition()
         pa.elem_part = part.ctypes.data
-        pa.n_groups = L - 2
+        pa.n_groups = max(L - 2, 0)     # levels = 1: operator only (no Schwarz levels)
         for l in range(L - 2):
             gr = _np(prob.groups[l], np.int32)
             self._keep.append(gr)
@@ -465,6 +524,70 @@ class Server:
         if getattr(self, "h", None):
             self.lib.gdsw_server_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- multigrid
+class Multigrid:
+    """Geometric multigrid over nested grids (gdsw_mg_*): probs finest first; the fine grids
+    become operator-only contexts, the coarsest a multilevel GDSW context whose FGMRES
+    tolerance coarse_tol is the coarse-solve tolerance.  solve() runs FP64 FGMRES on the
+    finest grid preconditioned by V-cycles (every step in the library's kernels)."""
+
+    def __init__(self, probs, omega=1.0, pre=2, post=2, smoother="fp32", coarse_tol=1e-1,
+                 coarse_precision=("fp32", "fp32", "fp32"), coarse_phi="fp32", tol=1e-8, restart=100, max_it=1000):
+        lib = load()
+        self.lib = lib
+        self.h = None
+        self.grids = [Context(p, levels=1, tol=tol, restart=restart, max_it=max_it) for p in probs[:-1]]
+        self.grids.append(Context(probs[-1], precision=coarse_precision, phi_precision=coarse_phi, tol=coarse_tol,
+                                  restart=100, max_it=1000))
+        arr = (C.c_void_p * len(self.grids))(*[g.h.value for g in self.grids])
+        o = gdsw_mg_options(float(omega), int(pre), int(post), PREC[smoother])
+        h = C.c_void_p()
+        rc = lib.gdsw_mg_create(arr, len(self.grids), C.byref(o), C.byref(h))
+        if rc != GDSW_OK:
+            raise GdswError(rc, lib.gdsw_mg_last_error(None).decode())
+        self.h = h
+        self.n = self.grids[0].n
+
+    def _check(self, rc):
+        if rc != GDSW_OK:
+            raise GdswError(rc, self.lib.gdsw_mg_last_error(self.h).decode())
+        return rc
+
+    def gdsw_mg_vcycle(self, r, z):
+        return self._check(self.lib.gdsw_mg_vcycle(self.h, _ptr(r), _ptr(z)))
+
+    def gdsw_mg_smooth(self, grid, b, x, steps):
+        return self._check(self.lib.gdsw_mg_smooth(self.h, grid, _ptr(b), _ptr(x), steps))
+
+    def gdsw_mg_prolong(self, grid, xc, zf):
+        return self._check(self.lib.gdsw_mg_prolong(self.h, grid, _ptr(xc), _ptr(zf)))
+
+    def gdsw_mg_restrict(self, grid, rf, rc):
+        return self._check(self.lib.gdsw_mg_restrict(self.h, grid, _ptr(rf), _ptr(rc)))
+
+    def gdsw_mg_stats(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self.lib.gdsw_mg_stats(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return dict(cycles=a.value, coarse_solves=b.value, coarse_iterations=c.value)
+
+    def solve(self, b, x):
+        """FGMRES on the finest grid, V-cycle preconditioned; x holds the initial guess."""
+        return self.grids[0].gdsw_solve(b, x)
+
+    def close(self):
+        if self.h:
+            self.lib.gdsw_mg_destroy(self.h)
+            self.h = None
+        for g in getattr(self, "grids", []):
+            g.close()
 
     def __del__(self):
         try:

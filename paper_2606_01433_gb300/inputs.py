@@ -240,6 +240,55 @@ def picard_velocity(p: Problem, seed: int):
     return np.ascontiguousarray(u)
 
 
+def mg_hierarchy(m=64, grids=3, parts=(8, 8, 8), groups=((2, 2, 2), (2, 2, 2)), levels=4, seed=4,
+                 nu0=1.0, nu_inf=1e-3, lam=1.0, n=0.5, carreau=True):
+    """Nested voxel grids for the geometric-multigrid role of the paper (Section 3: the
+    multigrid solver whose coarsest problem the multilevel Schwarz method solves): the
+    unit-cube channel (inflow x=0 with g = 16 y(1-y) z(1-z) e_x, outflow x=1, no-slip walls)
+    with m, m/2, ..., m/2^(grids-1) elements per edge, finest first.  Every grid samples the
+    same inflow profile and, for a Carreau fluid, the same frozen Picard velocity (the sine
+    field and amplitude of the finest grid, zero on walls and g on the inflow), so a coarse
+    node's values equal the fine values at the same point.  The coarsest grid carries the box
+    partition and grouping of the multilevel GDSW coarse solver; the finest carries a random
+    right-hand side on its free dofs (seed).  Newtonian (nu0, gradient form) when not
+    carreau."""
+    if m % (1 << (grids - 1)):
+        raise ValueError("m must be divisible by 2^(grids-1)")
+    out = []
+    fa = None
+    for gl in range(grids):
+        mm = m >> gl
+        h = 1.0 / mm
+        mask = np.ones(mm ** 3, dtype=np.uint8)
+        tags = boundary_tags(mm, mm, mm, h, (0, 0, 0), mask, inflow=(0, 0), outflow=(0, 1), extent=None)
+        last = gl == grids - 1
+        p = Problem("mg_cube_%d" % mm, mm, mm, mm, h, (0.0, 0.0, 0.0), mask, tags,
+                    np.zeros(((2 * mm + 1) ** 3, 3)), "symmetric" if carreau else "gradient", nu0=nu0,
+                    nu_inf=nu_inf if carreau else 0.0, lam=lam if carreau else 0.0, n_carreau=n if carreau else 1.0,
+                    levels=levels if last else 2, rhs_seed=seed if gl == 0 else None)
+        x = p.node_coords()
+        inl = tags == TAG_INFLOW
+        p.g[inl, 0] = 16.0 * x[inl, 1] * (1 - x[inl, 1]) * x[inl, 2] * (1 - x[inl, 2])
+        if carreau:
+            if fa is None:
+                rng = np.random.default_rng(seed)
+                field = sine_field(rng)
+                cen = element_centers(mm, mm, mm, h, p.origin)
+                fa = (field, 1.0 / (max(lam, 1e-30) * float(np.median(sine_grad_fro(field, cen, 1.0)))))
+            u = sine_eval(fa[0], x, fa[1])
+            u[tags == TAG_WALL] = 0.0
+            u[inl] = p.g[inl]
+            p.uk = np.ascontiguousarray(u)
+        if last:
+            p.part, used = box_partition(mm, mm, mm, parts)
+            p.groups = _groups_from_boxes(parts, groups, used, levels)
+        else:
+            p.part, _ = box_partition(mm, mm, mm, (1, 1, 1))
+            p.groups = []
+        out.append(p)
+    return out
+
+
 def random_rhs(n_free: int, seed: int):
     """b ~ N(0, 1) on the free dofs."""
     return np.random.default_rng(seed).standard_normal(n_free)

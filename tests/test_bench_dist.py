@@ -29,7 +29,10 @@ def _rank_main(rank, world, port, q):
     r, w, _ = bench.dist_init()
     slowest = bench.allreduce_max(10.0 * (rank + 1), w)
     bench.barrier(w)
-    bench.oracle_sample = lambda p, its, repeats=1: (123.0, "stub sample")  # the oracle itself is not timed here
+    stub = {"ms": 123.0, "cores": 1, "iterations": 3, "relres": 1e-9, "assembly_s": 0.1, "setup_s": 0.1,
+            "full_solve_s": 0.1, "krylov_rest_s": 0.0, "apply_s_mean": 0.01, "spmv_s_mean": 0.01,
+            "sample_wall_s": 0.1}
+    bench.oracle_reference = lambda p, steps, warmup: stub  # the oracle itself is not timed here
 
     class Args:
         m, warmup, steps, gpus = 8, 0, 2, world

@@ -169,6 +169,54 @@ def test_mixed_precision_solve(lib, name, prec):
     ctx.close()
 
 
+def _emulated_iterations(P, S, b, levels_prec, tol):
+    """The oracle's FGMRES iteration count with each level's local-solve inputs and outputs
+    rounded to the given precision (the oracle's mixed-precision emulation)."""
+    from oracle import fgmres, gdsw as og
+    for lev, pr in zip(P.levels, levels_prec):
+        lev.rounding = og.ROUNDING[pr]
+    try:
+        _, info = fgmres.fgmres(lambda v: S["A"] @ v, b, P.apply, tol=tol)
+    finally:
+        for lev in P.levels:
+            lev.rounding = None
+    return info["iterations"]
+
+
+@pytest.mark.parametrize("name", ["channel16_obstacles", "die_rcb_4lvl", "box_4lvl", "box_3lvl"])
+def test_mixed_iterations_match_emulation(lib, name):
+    """Mixed path at the benchmark's tolerance 1e-8: the FP32 path's FGMRES iteration count is
+    within +-1 of the oracle's with FP32-rounded local-solve inputs and outputs."""
+    from oracle import fem
+    p, S, P = oracle_for(name)
+    b = fem.lifted_rhs(S) if p.rhs_seed is None else I.random_rhs(S["A"].shape[0], p.rhs_seed)
+    its_o = _emulated_iterations(P, S, b, FP32[0], 1e-8)
+    ctx = lib.Context(p, precision=FP32[0], phi_precision=FP32[1], tol=1e-8)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.gdsw_solve(dev(b), x)
+    assert info.status == 0 and info.relres <= 1e-8
+    assert abs(info.iterations - its_o) <= 1, (info.iterations, its_o)
+    ctx.close()
+
+
+def test_bf16_die_128_row_tiles(lib):
+    """BF16 local factors with the 128-row forward tiles the autotuner picks on the die
+    workload (forced here, per-step launches and the persistent launch): forward error
+    <= 1e-8 against the FP64 oracle solved to 1e-13."""
+    from oracle import fem, fgmres
+    p, S, P = oracle_for("die_rcb_4lvl")
+    b = fem.lifted_rhs(S)
+    xo, _ = fgmres.fgmres(lambda v: S["A"] @ v, b, P.apply, tol=1e-13)
+    ctx = lib.Context(p, precision=BF16[0], phi_precision=BF16[1], tol=1e-12)
+    for persistent in (False, True):
+        ctx.gdsw_set_local_sweep(persistent, 0, 128)
+        x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+        info = ctx.gdsw_solve(dev(b), x)
+        assert info.status == 0
+        assert rel(host(x), xo) <= 1e-8, (persistent, rel(host(x), xo))
+    ctx.close()
+
+
 def test_poiseuille_exact_on_gpu(lib):
     """Section 2 closed form: the GPU solve reproduces the analytic Poiseuille flow."""
     from oracle import fem

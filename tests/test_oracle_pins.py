@@ -370,10 +370,176 @@ def test_rotation_modes_pin():
     assert np.linalg.norm(S["A"] @ r) <= 1e-10 * np.linalg.norm(r)          # in the kernel of A
     rot, _ = og.build_level1(S, p, rotations=True)
     plain, _ = og.build_level1(S, p)
-    base = og.build_level1(S, p, rotations=False)[0]
-    assert (plain.Phi != base.Phi).nnz == 0 and rot.n0 > plain.n0
+    # the default space: per entity three translations if it holds a free velocity node and
+    # one pressure constant if it holds a Q1 node, all as 0/1 indicators
+    expect = sum(3 * int((m.vindex[nodes] >= 0).any()) + int((m.pindex[nodes] >= 0).any())
+                 for _, nodes in plain.entities)
+    assert plain.n0 == expect and np.all(plain.PhiGamma.data == 1.0)
+    assert rot.n0 > plain.n0
     for lev, ok in ((rot, True), (plain, False)):
         Phi = lev.Phi.toarray()
         c = np.linalg.lstsq(Phi, r, rcond=None)[0]
         res = np.linalg.norm(Phi @ c - r) / np.linalg.norm(r)
         assert (res <= 1e-10) if ok else (res >= 1e-3), (ok, res)
+
+
+# --------------------------------------------------------------------------- overlap depth
+def _box_overlap_dofs(p, parts):
+    """Free dofs of every overlapping subdomain of a box partition of an uncarved box,
+    counted axis by axis: the part's element range [lo, hi) grows by one element layer to
+    [max(lo-1, 0), min(hi+1, m)); a Q2 node index i along that axis is kept when it lies
+    strictly inside the grown range (2 lo' < i < 2 hi'), or on the physical boundary
+    (i = 0 or i = 2m) that the grown range reaches.  Dof numbering as documented for the
+    inputs: free velocity nodes (tags other than wall/inflow) in node order, three
+    components each, then the Q1 (all-even index) nodes in node order."""
+    dims = (p.nx, p.ny, p.nz)
+    nxn, nyn = 2 * p.nx + 1, 2 * p.ny + 1
+    free_v = np.nonzero((p.tags != I.TAG_WALL) & (p.tags != I.TAG_INFLOW))[0]
+    vnum = -np.ones(p.n_nodes, dtype=np.int64)
+    vnum[free_v] = np.arange(free_v.size)
+    nid = np.arange(p.n_nodes)
+    ijk = np.stack([nid % nxn, (nid // nxn) % nyn, nid // (nxn * nyn)], axis=1)
+    q1 = np.nonzero((ijk % 2 == 0).all(axis=1))[0]
+    pnum = -np.ones(p.n_nodes, dtype=np.int64)
+    pnum[q1] = np.arange(q1.size)
+    nu = 3 * free_v.size
+    out = []
+    for bz in range(parts[2]):
+        for by in range(parts[1]):
+            for bx in range(parts[0]):
+                keep = []
+                for b, q, m in zip((bx, by, bz), parts, dims):
+                    lo, hi = b * m // q, (b + 1) * m // q
+                    lo2, hi2 = max(lo - 1, 0), min(hi + 1, m)
+                    idx = [i for i in range(2 * m + 1)
+                           if 2 * lo2 < i < 2 * hi2 or (i == 0 and lo2 == 0) or (i == 2 * m and hi2 == m)]
+                    keep.append(np.array(idx))
+                k3, j3, i3 = np.meshgrid(keep[2], keep[1], keep[0], indexing="ij")
+                nodes = np.sort((i3 + nxn * (j3 + nyn * k3)).ravel())
+                v = vnum[nodes]
+                v = v[v >= 0]
+                pp = pnum[nodes]
+                out.append(np.sort(np.concatenate([(3 * v[:, None] + np.arange(3)).ravel(), nu + pp[pp >= 0]])))
+    return out
+
+
+@pytest.mark.parametrize("m,parts", [(8, (4, 4, 4)), (6, (2, 3, 1)), (4, (2, 2, 2))])
+def test_overlap_one_element_layer(m, parts):
+    """Section 3 'one layer of overlap' with Section 2.1's homogeneous Dirichlet data on the
+    artificial boundary: for box partitions of an uncarved cube (corner, edge, face and
+    interior parts) the oracle's overlapping dof sets equal the box-geometric count of one
+    element layer with the rim of the grown box dropped -- and differ from zero or two
+    layers."""
+    p = I.unit_cube(m, parts=parts)
+    S = fem.assemble(p)
+    got = gdsw.overlapping_dofs(S, p)
+    lev, _ = gdsw.build_level1(S, p)
+    expect = _box_overlap_dofs(p, parts)
+    assert len(got) == len(expect) == parts[0] * parts[1] * parts[2]
+    for a, b, c in zip(got, expect, lev.dofs):
+        assert np.array_equal(a, b) and np.array_equal(c, b)
+    for k in (0, 2):
+        other = gdsw.overlapping_dofs(S, p, overlap=k)
+        assert any(not np.array_equal(a, b) for a, b in zip(other, expect))
+
+
+def test_coarse_overlap_chain_by_hand():
+    """Section 2.2 coarse levels with one layer of overlap, written out by hand on a chain:
+    eight one-element parts along x (faces F1..F7 between parts k-1 and k, each one entity
+    with ux, uy, uz, p), grouped in pairs {0,1}, {2,3}, {4,5}, {6,7}.  Face F_k lies in the
+    closure of group J when one of its parts belongs to J; coarse nodes couple when their
+    sharing sets meet (F_k with F_k-1 and F_k+1), so with one graph layer
+    Omega_0' = F1..F3, Omega_1' = F1..F5, Omega_2' = F3..F7, Omega_3' = F5..F7."""
+    p = I.box_problem(8, 1, 1, (8, 1, 1), groups=((2, 1, 1),), levels=3)
+    S = fem.assemble(p)
+    P = gdsw.GDSW(S, p)
+    lev1, lev2 = P.levels
+    assert [tuple(s) for s, nodes in lev1.entities] == [(k - 1, k) for k in range(1, 8)]
+    assert lev1.n0 == 28
+    F = lambda a, b: np.arange(4 * (a - 1), 4 * b)        # dofs of faces F_a .. F_b
+    expect = [F(1, 3), F(1, 5), F(3, 7), F(5, 7)]
+    assert len(lev2.dofs) == 4
+    for got, exp in zip(lev2.dofs, expect):
+        assert np.array_equal(got, exp), (got, exp)
+    # level-2 interface: the faces shared by two groups, F2, F4, F6
+    assert [tuple(s) for s, nodes in lev2.entities] == [(0, 1), (1, 2), (2, 3)]
+    assert [list(nodes) for s, nodes in lev2.entities] == [[1], [3], [5]]
+
+
+def test_fgmres_restart_cycles():
+    """Restarted FGMRES (Section 3): with restart 5 on a case that needs more than 15
+    iterations, (a) the residual estimates never increase, (b) the run reaches the dense
+    solution, (c) a restart continues from the cycle's iterate exactly as a fresh run started
+    there, and (d) the second cycle's update is the least-squares minimiser of the residual
+    of that iterate over span(A Z) of the cycle."""
+    p = I.box_problem(4, 4, 4, (2, 2, 2), levels=2, form="symmetric", uk_seed=3, lam=1.0, n=0.5, nu_inf=1e-3)
+    S = fem.assemble(p)
+    A = S["A"]
+    P = gdsw.GDSW(S, p)
+    b = I.random_rhs(A.shape[0], 8)
+    mv = lambda v: A @ v
+    x, info = fgmres.fgmres(mv, b, P.apply, tol=1e-12, restart=5, max_it=400)
+    assert info["converged"] and info["iterations"] > 15
+    h = np.array(info["history"])
+    assert np.all(h[1:] <= h[:-1] * (1 + 1e-12))
+    xd = np.linalg.solve(A.toarray(), b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    x5, _ = fgmres.fgmres(mv, b, P.apply, tol=0.0, restart=5, max_it=5)
+    x10, i10 = fgmres.fgmres(mv, b, P.apply, tol=0.0, restart=5, max_it=10, keep_basis=True)
+    y10, _ = fgmres.fgmres(mv, b, P.apply, tol=0.0, restart=5, max_it=5, x0=x5)
+    assert np.linalg.norm(x10 - y10) <= 1e-13 * np.linalg.norm(x10)
+    AZ = np.column_stack([A @ z for z in i10["Z"]])
+    y, *_ = np.linalg.lstsq(AZ, b - A @ x5, rcond=None)
+    assert np.linalg.norm(x10 - (x5 + i10["Z"].T @ y)) <= 1e-10 * np.linalg.norm(x10)
+
+
+# --------------------------------------------------------------------------- mixed emulation
+def test_rounding_functions():
+    """The two roundings of the mixed-precision emulation against hand-worked ties and the
+    conversions of two libraries: binary32 (Python's struct packing, a C float cast) and
+    bfloat16 (PyTorch's float32 -> bfloat16 conversion, round to nearest even)."""
+    import struct
+    one = 1.0
+    # binary32: 24-bit significand, ties to even
+    assert gdsw.round_fp32(one + 2.0 ** -24) == one
+    assert gdsw.round_fp32(one + 3 * 2.0 ** -24) == one + 2.0 ** -22
+    x = np.random.default_rng(0).standard_normal(2000) * np.exp(np.random.default_rng(1).uniform(-30, 30, 2000))
+    ref = np.array([struct.unpack("f", struct.pack("f", v))[0] for v in x])
+    assert np.array_equal(gdsw.round_fp32(x), ref)
+    # bfloat16: 8-bit significand, ties to even
+    assert gdsw.round_bf16(one + 2.0 ** -8) == one
+    assert gdsw.round_bf16(one + 3 * 2.0 ** -8) == one + 2.0 ** -6
+    assert gdsw.round_bf16(one + 2.0 ** -8 + 2.0 ** -20) == one + 2.0 ** -7
+    assert gdsw.round_bf16(-(one + 2.0 ** -8)) == -one and gdsw.round_bf16(0.0) == 0.0
+    assert gdsw.round_bf16(255.5) == 256.0 and gdsw.round_bf16(3.0) == 3.0
+    torch = pytest.importorskip("torch")
+    x32 = gdsw.round_fp32(x)
+    ref = torch.from_numpy(x32.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(gdsw.round_bf16(x32), ref)
+
+
+def test_mixed_emulation_effect():
+    """The emulation perturbs the preconditioner by the unit roundoff of its precision
+    (FP32 ~ 1e-7, BF16 ~ 4e-3, relative) and the FP64 flexible GMRES still reaches the
+    FP64 solution, with iteration counts close to the FP64 preconditioner's."""
+    p = I.box_problem(4, 4, 4, (2, 2, 2), groups=((2, 2, 1),), levels=3, form="symmetric", uk_seed=3,
+                      lam=1.0, n=0.5, nu_inf=1e-3)
+    S = fem.assemble(p)
+    A = S["A"]
+    P64 = gdsw.GDSW(S, p)
+    P32 = gdsw.GDSW(S, p, local_precision=("fp32", "fp32"))
+    P16 = gdsw.GDSW(S, p, local_precision=("bf16", "fp32"))
+    r = np.random.default_rng(3).standard_normal(A.shape[0])
+    z64 = P64.apply(r)
+    e32 = np.linalg.norm(P32.apply(r) - z64) / np.linalg.norm(z64)
+    e16 = np.linalg.norm(P16.apply(r) - z64) / np.linalg.norm(z64)
+    assert 1e-10 < e32 < 1e-5 and 1e-5 < e16 < 1e-1 and e32 < e16, (e32, e16)
+    b = fem.lifted_rhs(S)
+    xd = spla.spsolve(A.tocsc(), b)
+    its = {}
+    for name, P in (("fp64", P64), ("fp32", P32), ("bf16", P16)):
+        x, info = fgmres.fgmres(lambda v: A @ v, b, P.apply, tol=1e-11)
+        assert info["converged"]
+        assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+        its[name] = info["iterations"]
+    assert abs(its["fp32"] - its["fp64"]) <= 1 and its["bf16"] >= its["fp64"], its
