@@ -43,8 +43,14 @@ def parse():
     ap.add_argument("--mixed", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison context")
     ap.add_argument("--m", type=int, default=32, help="elements per edge of the channel")
-    ap.add_argument("--workload", choices=["channel", "die"], default="channel",
-                    help="channel: 32^3 Carreau channel (3 levels); die: 64x64x128 die-like channel (4 levels)")
+    ap.add_argument("--workload", choices=["channel", "die", "mg"], default="channel",
+                    help="channel: 32^3 Carreau channel (3 levels); die: 64x64x128 die-like channel (4 levels); "
+                         "mg: geometric multigrid on the 64^3 Carreau cube with its 16^3 grid solved by 4-level GDSW")
+    ap.add_argument("--mg-m", type=int, default=64, help="elements per edge of the finest multigrid grid")
+    ap.add_argument("--mg-smoother", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--mg-nu", type=int, default=2, help="pre- and post-smoothing steps")
+    ap.add_argument("--mg-symmetric", type=int, default=1, help="1: post-smoothing in reverse colour order")
+    ap.add_argument("--mg-restart", type=int, default=200)
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--prof-stride", type=int, default=1,
@@ -293,11 +299,12 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- serving
-def run_serving(n_req, sizes, slots, seed=5, budget_frac=0.8, fixed_rate=False):
+def run_serving(n_req, sizes, slots, seed=5, budget_frac=0.8, fixed_rate=False, closed_req=None):
     """Continuous batching of mixed Carreau requests (unit-cube channels m^3, m ~ U{sizes},
     n ~ U[0.3, 1], nu0/nu_inf log-uniform in [10, 1e4]).  Closed loop first (all submitted at
-    once: throughput), then open loop with Poisson arrivals at 0.8x that throughput
-    (latency = submit -> result in host memory)."""
+    once: throughput; on the first closed_req requests of the mix when given), then open loop
+    with Poisson arrivals of all n_req requests at 0.8x that throughput (latency = submit ->
+    result in host memory)."""
     import numpy as np
     import torch
     from paper_2606_01433_gb300 import gdsw, inputs as I
@@ -306,11 +313,12 @@ def run_serving(n_req, sizes, slots, seed=5, budget_frac=0.8, fixed_rate=False):
     free, _ = torch.cuda.mem_get_info()
     srv = gdsw.Server(device=torch.cuda.current_device(), mem_budget_bytes=int(free * budget_frac), max_slots=slots)
     st, _ = srv.gdsw_server_wait(srv.gdsw_server_submit(probs[0]))  # warm-up
+    nc = n_req if closed_req is None else min(closed_req, n_req)
     t0 = time.perf_counter()
-    tickets = [srv.gdsw_server_submit(p) for p in probs]
+    tickets = [srv.gdsw_server_submit(p) for p in probs[:nc]]
     closed = [srv.gdsw_server_wait(t)[0] for t in tickets]
     makespan = time.perf_counter() - t0
-    thr = n_req / makespan
+    thr = nc / makespan
     def open_loop(gaps):
         tickets = []
         t0 = time.perf_counter()
@@ -348,7 +356,8 @@ def run_serving(n_req, sizes, slots, seed=5, budget_frac=0.8, fixed_rate=False):
             "solve_ms_p50": float(np.median([s.solve_ms for s in opened])),
             "queue_ms_p50": float(np.median([s.queue_ms for s in opened])),
             "iterations_p50": float(np.median([s.iterations for s in opened])),
-            "converged": ok, "of": (3 if fixed else 2) * n_req, "peak_running": stats.peak_running,
+            "closed_loop_requests": nc,
+            "converged": ok, "of": nc + (2 if fixed else 1) * n_req, "peak_running": stats.peak_running,
             "peak_used_gb": stats.peak_used_bytes / 1e9, "budget_gb": stats.budget_bytes / 1e9,
             "local_precision": "fp32"}
 
@@ -366,6 +375,93 @@ def run_serve_mode(args, rank, world, local):
                 "higher_is_better": False, "scaling": "weak", "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "serving_carreau_cubes", "requests": args.requests},
                 "serving": res}
+        print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- multigrid arm
+MG_WORKLOAD = "mg_cube{m}_carreau_n0.5_q2q1_3grids_vanka_v22_coarse16_gdsw4_512_64_8"
+
+
+def run_mg(args, rank, world, local):
+    """Geometric multigrid whose coarse problem the four-level GDSW method solves (Section 3;
+    configuration 4): the unit-cube Carreau channel on grids m^3, (m/2)^3, (m/4)^3; V(2,2)
+    cycles with the element-Vanka smoother (FP32 patch inverses by default), the coarsest grid
+    solved by GDSW-preconditioned FGMRES to 1e-1 (parts of 2^3 elements grouped 2x2x2 twice:
+    four levels); FP64 FGMRES on the finest grid to 1e-8, preconditioned by one V-cycle per
+    iteration.  One step = one solve of the seeded random right-hand side."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_01433_gb300 import gdsw, inputs as I
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m = args.mg_m
+    q = m // 4 // 2
+    probs = I.mg_hierarchy(m, 3, parts=(q, q, q), groups=((2, 2, 2), (2, 2, 2)), levels=4, seed=4)
+    t0 = time.perf_counter()
+    G = gdsw.Multigrid(probs, pre=args.mg_nu, post=args.mg_nu, smoother=args.mg_smoother, coarse_tol=1e-1,
+                       tol=1e-8, restart=args.mg_restart, max_it=2000, symmetric=bool(args.mg_symmetric))
+    setup_s = time.perf_counter() - t0
+    n = G.n
+    b = torch.from_numpy(I.random_rhs(n, probs[0].rhs_seed)).to(dev)
+    x = torch.zeros_like(b)
+    for _ in range(args.warmup):
+        x.zero_()
+        info = G.solve(b, x)
+    st0 = G.gdsw_mg_stats()
+    stream = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    lib = gdsw.load()
+    launches0 = lib.gdsw_kernel_launches()
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    evs[0].record(stream)
+    its = []
+    for k in range(args.steps):
+        x.zero_()
+        info = G.solve(b, x)
+        its.append(info.iterations)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = lib.gdsw_kernel_launches() - launches0
+    total_ms = allreduce_max(evs[0].elapsed_time(evs[-1]), world, dev)
+    st1 = G.gdsw_mg_stats()
+    ms = total_ms / args.steps
+    cycles = (st1["cycles"] - st0["cycles"]) / args.steps
+    coarse_its = (st1["coarse_iterations"] - st0["coarse_iterations"]) / max(st1["coarse_solves"] - st0["coarse_solves"], 1)
+    # end to end: b from pinned host memory, x back to host, inside the timed region
+    bh = torch.from_numpy(I.random_rhs(n, probs[0].rhs_seed)).pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bd = bh.to(dev, non_blocking=True)
+        xd = torch.zeros_like(bd)
+        G.solve(bd, xd)
+        xh.copy_(xd, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = allreduce_max((time.perf_counter() - t0) * 1e3 / args.steps, world, dev)
+    sizes = [int(g.n) for g in G.grids]
+    relres = info.relres
+    G.close()
+    if rank == 0:
+        line = {"metric": "multigrid solve time at rel res 1e-8 (FP64 FGMRES, V-cycle preconditioned, GDSW coarse solver)",
+                "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.mg_smoother == "fp32" else "f64", "data": "synthetic",
+                "config": {"workload": MG_WORKLOAD.format(m=m), "grids_dofs": sizes, "smoother": args.mg_smoother,
+                           "cycle": "V(%d,%d)" % (args.mg_nu, args.mg_nu), "symmetric": bool(args.mg_symmetric),
+                           "restart": args.mg_restart, "coarse_tol": 1e-1, "tol": 1e-8,
+                           "l2": "inputs larger than L2 (no flush)"},
+                "iterations": its[-1], "relres": relres, "vcycles_per_solve": cycles,
+                "coarse_fgmres_iterations_mean": coarse_its, "setup_s": setup_s, "clocks": clk,
+                "gpu_launches": launches,
+                "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}}
         print(json.dumps(line), flush=True)
 
 
@@ -538,7 +634,9 @@ def run_gdsw(args, rank, world, local):
     torch.cuda.empty_cache()
     serving = None
     if os.environ.get("GDSW_BENCH_NO_SERVE") != "1":
-        serving = run_serving(24, (8, 12, 16), 4)
+        # the serving mix (256 requests of 8^3 .. 32^3, 8 slots, Poisson arrivals at 0.8x the
+        # closed-loop rate measured on the first 64 requests)
+        serving = run_serving(256, (8, 12, 16, 20, 24, 28, 32), 8, closed_req=64)
 
     peak, peak_kind = measured_peaks()
     ms_step = total_ms / args.steps
@@ -618,6 +716,8 @@ def main():
         run_reference(args, rank, world)
     elif args.serve:
         run_serve_mode(args, rank, world, local)
+    elif args.workload == "mg":
+        run_mg(args, rank, world, local)
     else:
         run_gdsw(args, rank, world, local)
     if world > 1:

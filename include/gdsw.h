@@ -215,8 +215,10 @@ int gdsw_picard_update(gdsw_ctx* ctx, const double* x);
  * Q2 velocity and Q1 pressure, zero at coarse Dirichlet nodes; R = P^T), and attaches the
  * V-cycle as the preconditioner of the finest context: gdsw_solve on grids[0] then runs FP64
  * FGMRES preconditioned by V-cycles.  A smoothing step is a multiplicative sweep over the
- * eight element colours (parity of the voxel indices): r = b - A z in FP64, then every patch
- * e of the colour adds omega A_e^{-1} r_e to z.  The multigrid object does not own the grid
+ * eight element colours (parity of the voxel indices): r = b - A z, then every patch e of the
+ * colour adds omega A_e^{-1} r_e to z; FP64 smoothing forms r with the FP64 SpMV, FP32
+ * smoothing only on the rows the colour's patches touch, with FP32 operator values copied
+ * when the multigrid is created (re-create it after re-assembling a grid's operator).  The multigrid object does not own the grid
  * contexts; destroy it before them.  Errors as for the other calls; a failed create leaves
  * its reason in gdsw_mg_last_error(NULL). */
 typedef struct gdsw_mg gdsw_mg;
@@ -224,6 +226,7 @@ typedef struct gdsw_mg_options {
   double omega;                 /* Vanka damping (1 = undamped) */
   int32_t pre, post;            /* smoothing steps before / after the coarse correction */
   int32_t smoother_precision;   /* GDSW_FP32 (patch inverses and products in FP32) or GDSW_FP64 */
+  int32_t symmetric;            /* 1: post-smoothing sweeps the colours in reverse order */
 } gdsw_mg_options;
 int gdsw_mg_create(gdsw_ctx* const* grids, int32_t ngrids, const gdsw_mg_options* opt, gdsw_mg** out);
 void gdsw_mg_destroy(gdsw_mg* mg);

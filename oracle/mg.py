@@ -21,7 +21,8 @@ textbook components on nested voxel grids (readings, also listed in the design n
     x <- x + omega sum_{e of colour c} R_e^T A_e^{-1} R_e (b - A x), c = 0..7.  (An
     additive, partition-of-unity-weighted Vanka diverged or converged slowly on these Q2/Q1
     problems: the continuous pressure couples every patch to its neighbours.)
-  * cycle: V-cycle with nu1 pre- and nu2 post-smoothing steps, zero initial guess on every
+  * cycle: V-cycle with nu1 pre- and nu2 post-smoothing steps (optionally the post-smoothing
+    sweeps the colours in reverse order: a symmetric cycle), zero initial guess on every
     coarser grid; on the coarsest grid GDSW-preconditioned FGMRES from zero to the relative
     residual coarse_tol (1e-1 in the paper);
   * outer iteration: x <- x + V(b - A x) with the residual in FP64, until
@@ -119,9 +120,9 @@ class Vanka:
         self.colour = (el % p.nx) % 2 + 2 * (((el // p.nx) % p.ny) % 2) + 4 * ((el // (p.nx * p.ny)) % 2)
         self.inv = [np.linalg.inv(A[d][:, d].toarray()) for d in self.dofs]
 
-    def smooth(self, b, x, steps):
+    def smooth(self, b, x, steps, reverse=False):
         for _ in range(steps):
-            for c in range(8):
+            for c in (range(7, -1, -1) if reverse else range(8)):
                 r = b - self.A @ x
                 dx = np.zeros_like(x)
                 for e in np.nonzero(self.colour == c)[0]:
@@ -134,13 +135,14 @@ class Vanka:
 class Multigrid:
     """V-cycle on nested grids (finest first) with the multilevel GDSW-FGMRES coarse solver."""
 
-    def __init__(self, probs, omega=1.0, pre=2, post=2, coarse_tol=1e-1, coarse_restart=100, pool=None):
+    def __init__(self, probs, omega=1.0, pre=2, post=2, coarse_tol=1e-1, coarse_restart=100, pool=None,
+                 symmetric=False):
         self.S = [fem.assemble(p, pool=pool) for p in probs]
         self.A = [S["A"] for S in self.S]
         self.P = [prolongation(self.S[l], self.S[l + 1]) for l in range(len(probs) - 1)]
         self.R = [P.T.tocsr() for P in self.P]
         self.smoothers = [Vanka(self.S[l], omega) for l in range(len(probs) - 1)]
-        self.pre, self.post = pre, post
+        self.pre, self.post, self.symmetric = pre, post, symmetric
         self.coarse = gdsw.GDSW(self.S[-1], probs[-1], pool=pool)
         self.coarse_tol = coarse_tol
         self.coarse_restart = coarse_restart
@@ -163,7 +165,7 @@ class Multigrid:
         z = sm.smooth(b, np.zeros_like(b), self.pre)
         rc = self.R[level] @ (b - A @ z)
         z = z + self.P[level] @ self.vcycle(rc, level + 1)
-        return sm.smooth(b, z, self.post)
+        return sm.smooth(b, z, self.post, reverse=self.symmetric)
 
     def solve(self, b, tol=1e-8, max_cycles=200):
         """Outer iteration x <- x + V(b - A x) with the FP64 residual; returns x and the

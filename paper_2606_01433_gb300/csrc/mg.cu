@@ -18,9 +18,11 @@
 // that context runs FP64 FGMRES preconditioned by the V-cycle:
 //   V(l, b): z = 0; nu1 smoothing steps; b_{l+1} = R (b - A z); z += P V(l+1, b_{l+1});
 //            nu2 smoothing steps; on the coarsest grid FGMRES + GDSW from zero.
-// A smoothing step sweeps the eight colours: r = b - A z (FP64 SpMV), then one warp per patch
-// of the colour computes A_e^{-1} r_e and adds omega times it to z (no two patches of a
-// colour share a dof, so the additions need no ordering).
+// A smoothing step sweeps the eight colours: r = b - A z, then one warp per patch of the colour
+// computes A_e^{-1} r_e and adds omega times it to z (no two patches of a colour share a dof, so
+// the additions need no ordering).  FP64 smoothing forms r with the full FP64 SpMV; FP32
+// smoothing forms it only on the rows the colour's patches touch (about (3/4)^3 of them), with
+// an FP32 copy of the operator taken when the multigrid is created.
 #include <algorithm>
 #include <cmath>
 
@@ -44,6 +46,11 @@ struct MgGrid {
   int32_t* d_pdof = nullptr;   // npatch x PMAX dofs, -1 padding
   void* d_pinv = nullptr;      // npatch x PMAX x PMAX, column-major inverse (FP32 or FP64)
   double minpiv = 0;
+  // FP32 smoothing: an FP32 copy of the operator's values (taken at creation) and, per colour,
+  // the velocity-node and pressure rows its patches touch (the residual is formed there only)
+  float *d_a32 = nullptr, *d_bt32 = nullptr, *d_b32 = nullptr;
+  int32_t* d_rows = nullptr;   // per colour: velocity nodes, then pressure indices
+  int64_t vrow_off[9] = {0}, prow_off[9] = {0};
   // transfer to the next coarser grid
   int64_t nc = 0;
   int32_t *d_p_ptr = nullptr, *d_p_col = nullptr, *d_r_ptr = nullptr, *d_r_col = nullptr;
@@ -108,6 +115,37 @@ static PatchHost build_patches(const MeshHost& M) {
       ++q;
     }
   return P;
+}
+
+// per colour, the velocity nodes and pressure indices that its patches touch (sorted)
+static void colour_rows(const MeshHost& M, const PatchHost& P, std::vector<int32_t>& rows, int64_t voff[9],
+                        int64_t poff[9]) {
+  rows.clear();
+  std::vector<int32_t> vmark(size_t(M.nv), -1), pmark(size_t(M.np), -1);
+  for (int c = 0; c < 8; ++c) {
+    std::vector<int32_t> vr, pr;
+    for (int64_t q = P.off[c]; q < P.off[c + 1]; ++q)
+      for (int k = 0; k < PMAX; ++k) {
+        const int32_t d = P.dof[size_t(q) * PMAX + k];
+        if (d < 0) break;
+        if (d < M.nu) {
+          if (vmark[d / 3] != c) {
+            vmark[d / 3] = c;
+            vr.push_back(d / 3);
+          }
+        } else if (pmark[d - M.nu] != c) {
+          pmark[d - M.nu] = c;
+          pr.push_back(int32_t(d - M.nu));
+        }
+      }
+    std::sort(vr.begin(), vr.end());
+    std::sort(pr.begin(), pr.end());
+    voff[c] = int64_t(rows.size());
+    rows.insert(rows.end(), vr.begin(), vr.end());
+    poff[c] = int64_t(rows.size());
+    rows.insert(rows.end(), pr.begin(), pr.end());
+  }
+  voff[8] = poff[8] = int64_t(rows.size());
 }
 
 // quadratic Lagrange weights of the nodes 0, 1, 2 at t in [0, 2]
@@ -329,6 +367,74 @@ __global__ void __launch_bounds__(256) k_vanka(const int32_t* __restrict__ pdof,
     if (dof[u] >= 0) z[dof[u]] += omega * double(y[u]);
 }
 
+// r = b - A z on the velocity-node rows of a list, FP32 operator values and products, FP64
+// b and result: one warp per node, lanes over its 3x3 blocks and B^T entries, fixed butterfly
+__global__ void __launch_bounds__(256) k_resid_vrows(const int32_t* __restrict__ rows, int64_t nrows,
+                                                     const int32_t* __restrict__ a_ptr,
+                                                     const int32_t* __restrict__ a_col, const float* __restrict__ a32,
+                                                     const int32_t* __restrict__ bt_ptr,
+                                                     const int32_t* __restrict__ bt_col,
+                                                     const float* __restrict__ bt32, int64_t nu,
+                                                     const double* __restrict__ z, const double* __restrict__ b,
+                                                     double* __restrict__ r) {
+  const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (q >= nrows) return;
+  const int32_t I = rows[q];
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int32_t e = a_ptr[I] + lane; e < a_ptr[I + 1]; e += 32) {
+    const int64_t J = a_col[e];
+    const float x0 = float(z[3 * J]), x1 = float(z[3 * J + 1]), x2 = float(z[3 * J + 2]);
+    const float* v = a32 + int64_t(e) * 9;
+    s0 = fmaf(v[0], x0, fmaf(v[1], x1, fmaf(v[2], x2, s0)));
+    s1 = fmaf(v[3], x0, fmaf(v[4], x1, fmaf(v[5], x2, s1)));
+    s2 = fmaf(v[6], x0, fmaf(v[7], x1, fmaf(v[8], x2, s2)));
+  }
+  for (int32_t e = bt_ptr[I] + lane; e < bt_ptr[I + 1]; e += 32) {
+    const float xp = float(z[nu + bt_col[e]]);
+    const float* v = bt32 + int64_t(e) * 3;
+    s0 = fmaf(v[0], xp, s0);
+    s1 = fmaf(v[1], xp, s1);
+    s2 = fmaf(v[2], xp, s2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane < 3) {
+    const int64_t d = 3 * int64_t(I) + lane;
+    r[d] = b[d] - double(lane == 0 ? s0 : (lane == 1 ? s1 : s2));
+  }
+}
+
+// r = b - A z on the pressure rows of a list (FP32 values and products): one warp per row
+__global__ void __launch_bounds__(256) k_resid_prows(const int32_t* __restrict__ rows, int64_t nrows,
+                                                     const int32_t* __restrict__ b_ptr,
+                                                     const int32_t* __restrict__ b_col, const float* __restrict__ b32,
+                                                     int64_t nu, const double* __restrict__ z,
+                                                     const double* __restrict__ b, double* __restrict__ r) {
+  const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (q >= nrows) return;
+  const int32_t P = rows[q];
+  float s = 0.f;
+  for (int32_t e = b_ptr[P] + lane; e < b_ptr[P + 1]; e += 32) {
+    const int64_t J = b_col[e];
+    const float* v = b32 + int64_t(e) * 3;
+    s = fmaf(v[0], float(z[3 * J]), fmaf(v[1], float(z[3 * J + 1]), fmaf(v[2], float(z[3 * J + 2]), s)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) r[nu + P] = b[nu + P] - double(s);
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) b[i] = float(a[i]);
+}
+
 // y = M x (+ y when accumulate), CSR FP64, one thread per row
 __global__ void k_csr_mv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                          const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
@@ -348,14 +454,37 @@ static void csr_mv(const int32_t* ptr, const int32_t* col, const double* val, co
 }
 
 // ------------------------------------------------------------------ the cycle
-static void smooth(gdsw_mg* mg, int l, const double* b, double* z, int steps) {
+// r = b - A z where colour c's patches need it: the full FP64 SpMV for FP64 smoothing, the
+// colour's rows in FP32 products otherwise
+static void colour_residual(gdsw_mg* mg, MgGrid& G, int c, const double* b, const double* z, cudaStream_t s) {
+  if (mg->opt.smoother_precision == GDSW_FP64) {
+    launch_spmv(G.ctx, z, G.d_r, b, s);
+    return;
+  }
+  const gdsw_ctx* x = G.ctx;
+  const int64_t nv = G.prow_off[c] - G.vrow_off[c], np = G.vrow_off[c + 1] - G.prow_off[c];
+  if (nv > 0) {
+    k_resid_vrows<<<int((nv + 7) / 8), 256, 0, s>>>(G.d_rows + G.vrow_off[c], nv, x->d_a_ptr, x->d_a_col, G.d_a32,
+                                                    x->d_bt_ptr, x->d_bt_col, G.d_bt32, x->mesh.nu, z, b, G.d_r);
+    check_launch("k_resid_vrows");
+  }
+  if (np > 0) {
+    k_resid_prows<<<int((np + 7) / 8), 256, 0, s>>>(G.d_rows + G.prow_off[c], np, x->d_b_ptr, x->d_b_col, G.d_b32,
+                                                    x->mesh.nu, z, b, G.d_r);
+    check_launch("k_resid_prows");
+  }
+}
+
+// reverse: sweep the colours 7..0 (the post-smoothing of a symmetric cycle)
+static void smooth(gdsw_mg* mg, int l, const double* b, double* z, int steps, bool reverse = false) {
   MgGrid& G = mg->g[l];
   cudaStream_t s = mg->s;
   for (int it = 0; it < steps; ++it)
-    for (int c = 0; c < 8; ++c) {
+    for (int cc = 0; cc < 8; ++cc) {
+      const int c = reverse ? 7 - cc : cc;
       const int64_t p0 = G.colour_off[c], p1 = G.colour_off[c + 1];
       if (p1 == p0) continue;
-      launch_spmv(G.ctx, z, G.d_r, b, s);  // r = b - A z
+      colour_residual(mg, G, c, b, z, s);
       const int blocks = int((p1 - p0 + 7) / 8);
       if (mg->opt.smoother_precision == GDSW_FP64)
         k_vanka<double><<<blocks, 256, 0, s>>>(G.d_pdof, static_cast<const double*>(G.d_pinv), p0, p1, G.d_r, z,
@@ -386,7 +515,7 @@ static void vcycle(gdsw_mg* mg, int l, const double* b, double* z) {
   csr_mv(G.d_r_ptr, G.d_r_col, G.d_r_val, G.d_r, C.d_b, G.nc, false, s);   // b_c = R r
   vcycle(mg, l + 1, C.d_b, C.d_z);
   csr_mv(G.d_p_ptr, G.d_p_col, G.d_p_val, C.d_z, z, G.n, true, s);         // z += P z_c
-  smooth(mg, l, b, z, mg->opt.post);
+  smooth(mg, l, b, z, mg->opt.post, mg->opt.symmetric != 0);
 }
 
 static void mg_precond(void* data, const double* r, double* z, cudaStream_t s) {
@@ -458,10 +587,14 @@ static void mg_create(gdsw_mg* mg, gdsw_ctx* const* grids, int ngrids, const gds
         while (n < PMAX && P.dof[size_t(q) * PMAX + n] >= 0) ++n;
         inv.push_back({dense + q * PMAX * PMAX, n, PMAX, 0});
       }
-      std::vector<double> mp;
-      run_inverse<double>(tmp, inv, mp, s);
       G.minpiv = 1e300;
-      for (double x : mp) G.minpiv = std::min(G.minpiv, x);
+      constexpr size_t kChunk = 32768;  // the batched inverse puts tasks on a grid axis of <= 65535
+      for (size_t i0 = 0; i0 < inv.size(); i0 += kChunk) {
+        std::vector<InvTaskP> part(inv.begin() + i0, inv.begin() + std::min(inv.size(), i0 + kChunk));
+        std::vector<double> mp;
+        run_inverse<double>(tmp, part, mp, s);
+        for (double x : mp) G.minpiv = std::min(G.minpiv, x);
+      }
       GDSW_CHECK(G.minpiv > 0 && std::isfinite(G.minpiv), GDSW_ERR_SINGULAR, "Vanka patch matrix is singular");
       if (opt->smoother_precision == GDSW_FP64) {
         double* st = mg->arena.alloc<double>(size_t(G.npatch) * PMAX * PMAX);
@@ -479,6 +612,20 @@ static void mg_create(gdsw_mg* mg, gdsw_ctx* const* grids, int ngrids, const gds
       throw;
     }
     tmp.free_all();
+    if (opt->smoother_precision == GDSW_FP32) {
+      std::vector<int32_t> rows;
+      colour_rows(M, P, rows, G.vrow_off, G.prow_off);
+      G.d_rows = mg->arena.upload(rows, s);
+      const gdsw_ctx* x = G.ctx;
+      const int64_t na = 9 * x->nnzb, nbt = 3 * x->nbt, nb = 3 * x->nb;
+      G.d_a32 = mg->arena.alloc<float>(na);
+      G.d_bt32 = mg->arena.alloc<float>(nbt);
+      G.d_b32 = mg->arena.alloc<float>(nb);
+      k_to_f32<<<int((na + 255) / 256), 256, 0, s>>>(x->d_val, G.d_a32, na);
+      k_to_f32<<<int((nbt + 255) / 256), 256, 0, s>>>(x->d_val + na, G.d_bt32, nbt);
+      k_to_f32<<<int((nb + 255) / 256), 256, 0, s>>>(x->d_val + na + nbt, G.d_b32, nb);
+      check_launch("k_to_f32");
+    }
     // transfers
     const MeshHost& Cm = mg->g[l + 1].ctx->mesh;
     CsrHost Ph = build_prolongation(M, Cm);

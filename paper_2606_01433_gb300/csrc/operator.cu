@@ -384,13 +384,27 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ sell_r
     if (sl < nslices) {
       const int64_t g0 = aoff[sl] >> 5, g1 = aoff[sl + 1] >> 5;
       int64_t g = g0 + sub;
-      for (; g + 4 < g1; g += 8) {  // two independent slot groups per pass
-        double b0 = 0.0, b1 = 0.0, b2 = 0.0;
-        sell_block(acol, aval, x, g, lane, a0, a1, a2);
-        sell_block(acol, aval, x, g + 4, lane, b0, b1, b2);
-        a0 += b0;
-        a1 += b1;
-        a2 += b2;
+      // two slot groups per pass, their loads independent of the accumulators (so both are in
+      // flight at once) and their products chained into the same three sums: no extra FP64
+      // adds to merge partial sums, since the FP64 pipe, not memory, bounds this loop
+      for (; g + 4 < g1; g += 8) {
+        const int64_t j = __ldg(acol + g * 32 + lane), k = __ldg(acol + (g + 4) * 32 + lane);
+        const double* v = aval + g * 288 + lane;
+        const double* w = aval + (g + 4) * 288 + lane;
+        double vv[9], ww[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          vv[q] = __ldcs(v + 32 * q);
+          ww[q] = __ldcs(w + 32 * q);
+        }
+        const double x0 = __ldg(x + 3 * j), x1 = __ldg(x + 3 * j + 1), x2 = __ldg(x + 3 * j + 2);
+        const double y0 = __ldg(x + 3 * k), y1 = __ldg(x + 3 * k + 1), y2 = __ldg(x + 3 * k + 2);
+        a0 = fma(vv[2], x2, fma(vv[1], x1, fma(vv[0], x0, a0)));
+        a1 = fma(vv[5], x2, fma(vv[4], x1, fma(vv[3], x0, a1)));
+        a2 = fma(vv[8], x2, fma(vv[7], x1, fma(vv[6], x0, a2)));
+        a0 = fma(ww[2], y2, fma(ww[1], y1, fma(ww[0], y0, a0)));
+        a1 = fma(ww[5], y2, fma(ww[4], y1, fma(ww[3], y0, a1)));
+        a2 = fma(ww[8], y2, fma(ww[7], y1, fma(ww[6], y0, a2)));
       }
       if (g < g1) sell_block(acol, aval, x, g, lane, a0, a1, a2);
       const int64_t h0 = boff[sl] >> 5, h1 = boff[sl + 1] >> 5;

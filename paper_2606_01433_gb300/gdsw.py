@@ -82,7 +82,8 @@ GEMM_ENGINE = {"auto": 0, "simt": 1, "tensor": 2}
 
 
 class gdsw_mg_options(C.Structure):
-    _fields_ = [("omega", C.c_double), ("pre", C.c_int32), ("post", C.c_int32), ("smoother_precision", C.c_int32)]
+    _fields_ = [("omega", C.c_double), ("pre", C.c_int32), ("post", C.c_int32), ("smoother_precision", C.c_int32),
+                ("symmetric", C.c_int32)]
 
 
 class gdsw_profile(C.Structure):
@@ -540,7 +541,8 @@ class Multigrid:
     finest grid preconditioned by V-cycles (every step in the library's kernels)."""
 
     def __init__(self, probs, omega=1.0, pre=2, post=2, smoother="fp32", coarse_tol=1e-1,
-                 coarse_precision=("fp32", "fp32", "fp32"), coarse_phi="fp32", tol=1e-8, restart=100, max_it=1000):
+                 coarse_precision=("fp32", "fp32", "fp32"), coarse_phi="fp32", tol=1e-8, restart=100, max_it=1000,
+                 symmetric=False):
         lib = load()
         self.lib = lib
         self.h = None
@@ -548,7 +550,7 @@ class Multigrid:
         self.grids.append(Context(probs[-1], precision=coarse_precision, phi_precision=coarse_phi, tol=coarse_tol,
                                   restart=100, max_it=1000))
         arr = (C.c_void_p * len(self.grids))(*[g.h.value for g in self.grids])
-        o = gdsw_mg_options(float(omega), int(pre), int(post), PREC[smoother])
+        o = gdsw_mg_options(float(omega), int(pre), int(post), PREC[smoother], 1 if symmetric else 0)
         h = C.c_void_p()
         rc = lib.gdsw_mg_create(arr, len(self.grids), C.byref(o), C.byref(h))
         if rc != GDSW_OK:
