@@ -48,7 +48,7 @@ def parse():
                          "mg: geometric multigrid on the 64^3 Carreau cube with its 16^3 grid solved by 4-level GDSW")
     ap.add_argument("--mg-m", type=int, default=64, help="elements per edge of the finest multigrid grid")
     ap.add_argument("--mg-smoother", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--mg-nu", type=int, default=2, help="pre- and post-smoothing steps")
+    ap.add_argument("--mg-nu", type=int, default=3, help="pre- and post-smoothing steps")
     ap.add_argument("--mg-symmetric", type=int, default=1, help="1: post-smoothing in reverse colour order")
     ap.add_argument("--mg-restart", type=int, default=200)
     ap.add_argument("--profile-region", action="store_true",
@@ -379,13 +379,14 @@ def run_serve_mode(args, rank, world, local):
 
 
 # ----------------------------------------------------------------------------- multigrid arm
-MG_WORKLOAD = "mg_cube{m}_carreau_n0.5_q2q1_3grids_vanka_v22_coarse16_gdsw4_512_64_8"
+MG_WORKLOAD = "mg_cube{m}_carreau_n0.5_q2q1_3grids_vanka_coarse_gdsw4"
 
 
 def run_mg(args, rank, world, local):
     """Geometric multigrid whose coarse problem the four-level GDSW method solves (Section 3;
-    configuration 4): the unit-cube Carreau channel on grids m^3, (m/2)^3, (m/4)^3; V(2,2)
-    cycles with the element-Vanka smoother (FP32 patch inverses by default), the coarsest grid
+    configuration 4): the unit-cube Carreau channel on grids m^3, (m/2)^3, (m/4)^3; symmetric
+    V(nu, nu) cycles (nu = 3 by default) with the element-Vanka smoother (FP32 patch inverses by
+    default), the coarsest grid
     solved by GDSW-preconditioned FGMRES to 1e-1 (parts of 2^3 elements grouped 2x2x2 twice:
     four levels); FP64 FGMRES on the finest grid to 1e-8, preconditioned by one V-cycle per
     iteration.  One step = one solve of the seeded random right-hand side."""

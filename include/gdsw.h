@@ -138,7 +138,10 @@ typedef struct {
   double tuned_ms[3];       /* the chosen configuration's local-solve time (0: not tuned) */
 } gdsw_sizes_info;
 
-/* Per-call kernel timing (CUDA events on the context stream) and algorithmic bytes. */
+/* Per-call kernel timing (CUDA events on the context stream) and algorithmic bytes.  The
+ * gather, local, scatter, restrict and prolong groups hold level-1 work only; everything on
+ * the coarser levels (their gathers, local solves, scatters and transfers, and the coarsest
+ * direct solve) is the coarse group. */
 typedef struct {
   int32_t enabled;
   int64_t calls[12];
@@ -200,6 +203,21 @@ int gdsw_reassemble(gdsw_ctx* ctx, const double* uk_host);
  * new context refactors).  Newton terms are not provided: they make A non-symmetric.
  * Asynchronous on the context stream. */
 int gdsw_picard_update(gdsw_ctx* ctx, const double* x);
+
+/* r = b - A x with the current operator (device FP64 vectors). */
+int gdsw_residual(gdsw_ctx* ctx, const double* b, const double* x, double* r);
+
+/* One Newton step of Section 3's alternating Picard-Newton iteration, from the state x (device
+ * FP64, free dofs; u_k must be its velocity, as after gdsw_picard_update(ctx, x)): evaluate
+ * nu(u_k), assemble the Picard operator A(nu(u_k)) and form the nonlinear residual
+ * R = b(nu(u_k)) - A(nu(u_k)) x, add the Newton term of the Carreau law,
+ * int 4 nu'(gamma_dot)/gamma_dot (D(u_k):D(w)) (D(u_k):D(v)) -- symmetric, since the Carreau
+ * problem minimises a convex energy, so the symmetric block-LDL^T factors of the frozen
+ * preconditioner still apply -- solve J delta = R by FGMRES from zero, then x += delta and
+ * u_{k+1} = x's velocity with the Dirichlet data.  Afterwards the context's operator is the
+ * Jacobian; gdsw_reassemble restores the Picard operator.  Needs the symmetric form and a
+ * velocity (GDSW_ERR_INVALID_ARG otherwise).  info: the linear solve's record.  Synchronous. */
+int gdsw_newton_step(gdsw_ctx* ctx, double* x, gdsw_solve_info* info);
 
 /* ---- geometric multigrid with the multilevel GDSW method as its coarse solver ----
  * Section 3 of the paper also uses the Schwarz method as the coarse-grid solver of a

@@ -136,6 +136,39 @@ def quadrature_viscosity(mesh: Mesh, tabs):
     return carreau(gd, p.nu0, p.nu_inf, p.lam, p.n_carreau)
 
 
+def carreau_dnu_over_gd(gamma_dot, nu0, nu_inf, lam, n):
+    """nu'(gamma_dot) / gamma_dot of the Carreau law (finite at gamma_dot = 0):
+    (nu0 - nu_inf) (n - 1) lambda^2 (1 + (lambda gamma_dot)^2)^((n - 3)/2)."""
+    return (nu0 - nu_inf) * (n - 1.0) * lam ** 2 * (1.0 + (lam * gamma_dot) ** 2) ** ((n - 3.0) / 2.0)
+
+
+def quadrature_strain(mesh: Mesh, tabs):
+    """D(u_k) (ne, 27, 3, 3) and the Newton weight N = 4 nu'(gamma_dot) / gamma_dot (ne, 27)
+    at the Gauss points, for the Newton linearisation of Section 3's alternating
+    Picard-Newton iteration (see newton_matrices)."""
+    p = mesh.p
+    phi, dphi, psi, w = tabs
+    u = p.uk[mesh.enodes]
+    grad = np.einsum("eac,qal->eqcl", u, dphi) * (2.0 / p.h)
+    D = 0.5 * (grad + np.swapaxes(grad, 2, 3))
+    gd = np.sqrt(2.0 * np.einsum("eqcl,eqcl->eq", D, D))
+    return D, 4.0 * carreau_dnu_over_gd(gd, p.nu0, p.nu_inf, p.lam, p.n_carreau)
+
+
+def newton_matrices(h, D, N, tabs):
+    """Element matrices (ne, 81, 81) of the Newton term of the Carreau operator.
+
+    With a(u; v) = int 2 nu(gamma_dot(u)) D(u):D(v) and gamma_dot = sqrt(2 D:D), the derivative
+    in the direction w adds int 4 nu'(gamma_dot)/gamma_dot (D(u):D(w)) (D(u):D(v)); for
+    v = phi_a e_c, w = phi_b e_d it is int N (D grad phi_a)_c (D grad phi_b)_d (symmetric: the
+    Carreau problem is the minimisation of a convex energy)."""
+    phi, dphi, psi, w = tabs
+    g = np.einsum("eqcl,qal->eqac", D, dphi) * (2.0 / h)        # (D grad phi_a)_c
+    wq = w * (h / 2.0) ** 3
+    K = np.einsum("q,eq,eqac,eqbd->eacbd", wq, N, g, g)
+    return K.reshape(-1, 81, 81)
+
+
 def element_matrices(form, h, nu_q, tabs):
     """Element velocity matrices K_e (ne, 81, 81) with row/col index 3*a + c.
 
@@ -163,7 +196,7 @@ def element_divergence(h, tabs):
     return Be.reshape(8, 81)
 
 
-def assemble(prob, chunk=2048, pool=None):
+def assemble(prob, chunk=2048, pool=None, newton=False):
     """Assemble the full saddle-point operator on free dofs plus the coupling to the
     Dirichlet velocity dofs (for lifting).
 
@@ -172,6 +205,8 @@ def assemble(prob, chunk=2048, pool=None):
       Dirichlet velocity columns), g_d (3 n_dirichlet_nodes,) Dirichlet values, nu_q.
     With a host pool (oracle/parallel.py) the element chunks and each round of their
     pairwise sums run on its threads; the chunks and the summation tree are the serial ones.
+    newton=True adds the Newton term of the Carreau law at u_k (newton_matrices): the operator
+    is then the Jacobian of the nonlinear residual (symmetric form with a Picard velocity only).
     """
     mesh = Mesh(prob)
     tabs = reference_tables()
@@ -187,9 +222,15 @@ def assemble(prob, chunk=2048, pool=None):
     node_col = np.where(vcol >= 0, vcol, dcol)            # (n_nodes,)
     nvel = nu_tot + nd
 
+    use_newton = newton and prob.form == "symmetric" and prob.uk is not None
+    if use_newton:
+        Dq, Nq = quadrature_strain(mesh, tabs)
+
     def velocity_chunk(s):
         e = slice(s, min(ne, s + chunk))
         Ke = element_matrices(prob.form, prob.h, nu_q[e], tabs)       # (c, 81, 81)
+        if use_newton:
+            Ke = Ke + newton_matrices(prob.h, Dq[e], Nq[e], tabs)
         nodes = mesh.enodes[e]                                        # (c, 27)
         dof = (node_col[nodes][:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 81)
         r = np.repeat(dof[:, :, None], 81, axis=2).ravel()
@@ -254,3 +295,44 @@ def picard(prob, steps):
         xs.append(x)
         p.uk = u
     return xs
+
+
+def newton_step(prob, x):
+    """One Newton step of Section 3's alternating Picard-Newton iteration from the state x
+    (free dofs; prob.uk must hold its velocity with the Dirichlet data): with the nonlinear
+    residual R(x) = b(nu(u)) - A(nu(u)) x, solve J(x) delta = R(x) exactly (SciPy sparse LU),
+    J the Jacobian (assemble(..., newton=True)); returns x + delta and ||R(x)|| / ||b||."""
+    import scipy.sparse.linalg as spla
+    S = assemble(prob)
+    b = lifted_rhs(S)
+    R = b - S["A"] @ x
+    J = assemble(prob, newton=True)["A"]
+    return x + spla.spsolve(J.tocsc(), R), np.linalg.norm(R) / np.linalg.norm(b)
+
+
+def picard_newton(prob, kinds):
+    """Section 3's alternating Picard-Newton iteration: kinds is a string of 'P' (Picard step:
+    solve A(nu(u_k)) x = b(nu(u_k))) and 'N' (Newton step from the previous iterate, which a
+    'P' step must precede); u_{k+1} is each new iterate's velocity with the Dirichlet data.
+    Returns the iterates x_1 .. and the nonlinear residuals ||R(x_k)|| / ||b|| before each step."""
+    import copy
+    import scipy.sparse.linalg as spla
+    p = copy.copy(prob)
+    xs, res = [], []
+    x = None
+    for kind in kinds:
+        S = assemble(p)
+        b = lifted_rhs(S)
+        if kind == "P":
+            if x is not None:
+                res.append(np.linalg.norm(b - S["A"] @ x) / np.linalg.norm(b))
+            x = spla.spsolve(S["A"].tocsc(), b)
+        else:
+            if x is None:
+                raise ValueError("a Newton step needs a previous iterate")
+            x, r = newton_step(p, x)
+            res.append(r)
+        u, _ = full_solution(S, x)
+        p.uk = u
+        xs.append(x)
+    return xs, res

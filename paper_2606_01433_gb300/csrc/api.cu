@@ -963,7 +963,8 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
   const int64_t nv = L.nvec;
   double gbytes = 0;
   {
-    ProfScope ps(c, GDSW_K_GATHER, double(nv) * (4 + 8 + (L.prec == GDSW_FP64 ? 8 : 4)), s);
+    // level-1 groups carry only level-1 work; every coarser level's work is the "coarse" group
+    ProfScope ps(c, l == 0 ? GDSW_K_GATHER : GDSW_K_COARSE, double(nv) * (4 + 8 + (L.prec == GDSW_FP64 ? 8 : 4)), s);
     if (L.prec == GDSW_FP64)
       launch_gather<double>(r, L.gdof, static_cast<double*>(L.vec), nv, s);
     else
@@ -1013,7 +1014,8 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
   for (int k = 0; k < L.bwd.nlaunch(); ++k) sweep(L.bwd, k, L.bwd_ld[k], L.bwd_bytes[k]);
   }
   {
-    ProfScope ps(c, GDSW_K_SCATTER, double(nv) * (4 + 8 + (L.prec == GDSW_FP64 ? 8 : 4)) + 8.0 * L.n, s);
+    ProfScope ps(c, l == 0 ? GDSW_K_SCATTER : GDSW_K_COARSE,
+                 double(nv) * (4 + 8 + (L.prec == GDSW_FP64 ? 8 : 4)) + 8.0 * L.n, s);
     if (L.prec == GDSW_FP64)
       launch_scatter<double>(static_cast<const double*>(L.vec) + nv, L.sc_ptr, L.sc_pos, L.sc_w, z, L.n, 0, s);
     else
@@ -1042,7 +1044,7 @@ static double apply_bytes(const gdsw_ctx* c) {
 static void restrict_level(gdsw_ctx* c, int l, const double* r, double* r0, cudaStream_t s) {
   LevelDev& L = c->ld[l];
   if (L.n0 == 0) return;
-  ProfScope ps(c, GDSW_K_RESTRICT, double(L.phi_bytes) + 16.0 * L.nidofs, s);
+  ProfScope ps(c, l == 0 ? GDSW_K_RESTRICT : GDSW_K_COARSE, double(L.phi_bytes) + 16.0 * L.nidofs, s);
   if (L.phi_prec == GDSW_FP64) {
     launch_gather<double>(r, L.idofs, static_cast<double*>(L.rI), L.nidofs, s);
     launch_gemv<double, double>(static_cast<const double*>(L.phiT), static_cast<const double*>(L.rI),
@@ -1083,7 +1085,7 @@ static void apply_level(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
     GDSW_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
   }
   if (coarse) {
-    ProfScope ps(c, GDSW_K_PROLONG, double(L.phi_bytes) + 16.0 * L.nidofs, s);
+    ProfScope ps(c, l == 0 ? GDSW_K_PROLONG : GDSW_K_COARSE, double(L.phi_bytes) + 16.0 * L.nidofs, s);
     launch_prolong(L, L.x0, z, s);
   }
 }
@@ -1578,6 +1580,40 @@ int gdsw_solve_host(gdsw_ctx* c, const double* bh, double* xh, gdsw_solve_info* 
     c->err = e.msg;
     return e.code;
   }
+}
+
+int gdsw_residual(gdsw_ctx* c, const double* b, const double* x, double* r) {
+  if (!c || c->host_only || !b || !x || !r) return GDSW_ERR_INVALID_ARG;
+  GDSW_TRY(c, launch_spmv(c, x, r, b, c->stream));
+}
+
+int gdsw_newton_step(gdsw_ctx* c, double* x, gdsw_solve_info* info) {
+  if (!c || c->host_only || !x) return GDSW_ERR_INVALID_ARG;
+  gdsw_solve_info tmp{};
+  if (!info) info = &tmp;
+  GDSW_TRY(c, {
+    GDSW_CHECK(c->form == GDSW_FORM_SYMMETRIC && c->has_uk, GDSW_ERR_INVALID_ARG,
+               "a Newton step needs the symmetric (Carreau) form and a velocity u_k");
+    cudaStream_t s = c->stream;
+    const int64_t n = c->mesh.n;
+    if (!c->d_dn) c->d_dn = c->arena.alloc<double>(7 * 27 * int64_t(c->mesh.fluid.size()));
+    if (!c->d_newton_work) c->d_newton_work = c->arena.alloc<double>(3 * n);
+    double* b = c->d_newton_work;
+    double* r = b + n;
+    double* d = r + n;
+    c->prof_gate = true;
+    launch_viscosity(c, s);          // nu(u_k), D(u_k) and the Newton weights
+    launch_assembly(c, s, false);    // Picard operator A(nu(u_k)) for the residual
+    launch_lift(c, b, s);
+    launch_spmv(c, x, r, b, s);      // R = b - A x
+    launch_assembly(c, s, true);     // Jacobian J = A + Newton term
+    GDSW_CUDA(cudaMemsetAsync(d, 0, 8 * n, s));
+    fgmres_solve(c, r, d, info);     // J delta = R with the frozen preconditioner
+    launch_axpy(x, d, n, s);         // x += delta
+    launch_picard_velocity(c, x, s); // u_{k+1}
+    GDSW_CHECK(info->status == GDSW_OK || info->status == GDSW_ERR_NOT_CONVERGED, info->status,
+               "Newton step: the linear solve failed");
+  });
 }
 
 int gdsw_picard_update(gdsw_ctx* c, const double* x) {

@@ -334,6 +334,8 @@ struct gdsw_ctx {
   // device mesh / matrix
   double* d_uk = nullptr;
   double* d_nu = nullptr;           // nu[fluid element][27]
+  double* d_dn = nullptr;           // Newton linearisation: D(u_k) and N per Gauss point (7 values), or null
+  double* d_newton_work = nullptr;  // Newton step: lifted b, residual, increment (3 n)
   uint8_t* d_mask = nullptr;
   int32_t* d_fluid = nullptr;       // fluid index -> element
   int32_t* d_felem = nullptr;

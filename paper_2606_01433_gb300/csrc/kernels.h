@@ -64,7 +64,9 @@ void convert(const void* src, int sprec, void* dst, int dprec, int64_t n, cudaSt
 // operator.cu
 void launch_viscosity(gdsw_ctx* c, cudaStream_t s);
 void launch_picard_velocity(gdsw_ctx* c, const double* x, cudaStream_t s);
-void launch_assembly(gdsw_ctx* c, cudaStream_t s);
+void launch_axpy(double* x, const double* d, int64_t n, cudaStream_t s);  // x += d
+// newton: add the Newton term from the D(u_k), N values of the last viscosity launch (d_dn)
+void launch_assembly(gdsw_ctx* c, cudaStream_t s, bool newton = false);
 void launch_lift(gdsw_ctx* c, double* b, cudaStream_t s);
 void launch_spmv(gdsw_ctx* c, const double* x, double* y, const double* b, cudaStream_t s);
 void launch_sell_fill(gdsw_ctx* c, bool with_bt, cudaStream_t s);

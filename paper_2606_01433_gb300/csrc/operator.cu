@@ -58,15 +58,21 @@ __device__ __forceinline__ int shared_range(int a, int b, int n, int& e0) {
 }
 
 // ------------------------------------------------------------------ a1: Carreau viscosity
+// dn (optional, Newton linearisation of Section 3): per Gauss point D(u_k) (xx, yy, zz, xy, xz,
+// yz) and N = 4 nu'(gamma_dot) / gamma_dot = 4 (nu0 - nu_inf)(n - 1) lambda^2
+// (1 + (lambda gamma_dot)^2)^((n - 3)/2), the weight of the Newton term
+// int N (D(u_k):D(w)) (D(u_k):D(v)) of the Carreau operator's derivative
 __global__ void k_viscosity(const int32_t* __restrict__ fluid, int64_t nfe, const double* __restrict__ uk,
                             const RefTables* __restrict__ T, Geo G, int form, int has_uk, double nu0, double nu_inf,
-                            double lam, double ncar, double* __restrict__ nu) {
+                            double lam, double ncar, double* __restrict__ nu, double* __restrict__ dn) {
   int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= nfe * 27) return;
   int64_t fe = t / 27;
   int q = int(t - fe * 27);
   if (!has_uk || form == GDSW_FORM_GRADIENT) {
     nu[t] = nu0;
+    if (dn)
+      for (int k = 0; k < 7; ++k) dn[t * 7 + k] = 0.0;
     return;
   }
   int e = fluid[fe];
@@ -95,6 +101,16 @@ __global__ void k_viscosity(const int32_t* __restrict__ fluid, int64_t nfe, cons
   double gdot = sqrt(2.0 * dd);
   double lg = lam * gdot;
   nu[t] = nu_inf + (nu0 - nu_inf) * pow(1.0 + lg * lg, 0.5 * (ncar - 1.0));
+  if (dn) {
+    double* o = dn + t * 7;
+    o[0] = s * gr[0][0];
+    o[1] = s * gr[1][1];
+    o[2] = s * gr[2][2];
+    o[3] = 0.5 * s * (gr[0][1] + gr[1][0]);
+    o[4] = 0.5 * s * (gr[0][2] + gr[2][0]);
+    o[5] = 0.5 * s * (gr[1][2] + gr[2][1]);
+    o[6] = 4.0 * (nu0 - nu_inf) * (ncar - 1.0) * lam * lam * pow(1.0 + lg * lg, 0.5 * (ncar - 3.0));
+  }
 }
 
 // 3x3 velocity block between nodes I and J (Section 2 gradient form / Section 3 symmetric form)
@@ -184,9 +200,10 @@ __global__ void __launch_bounds__(256) k_assemble_A(const int32_t* __restrict__ 
                                                     const uint32_t* __restrict__ asm_unit,
                                                     const int32_t* __restrict__ a_tpos,
                                                     const double* __restrict__ nu, const RefTables* __restrict__ T,
-                                                    double sc, int form, double* __restrict__ val) {
+                                                    double sc, int form, const double* __restrict__ dn,
+                                                    double* __restrict__ val) {
   __shared__ SmemTables st;
-  __shared__ double part[256][9];
+  __shared__ double part[256][10];  // per unit: the block's non-trace part, then the trace term
   {
     const double* src = &T->dphi[0][0][0];
     double* dst = &st.dphi[0][0][0];
@@ -197,9 +214,9 @@ __global__ void __launch_bounds__(256) k_assemble_A(const int32_t* __restrict__ 
   const int blk0 = asm_cta[blockIdx.x], blk1 = asm_cta[blockIdx.x + 1];
   const int u0 = asm_uoff[blk0], u1 = asm_uoff[blk1];
   const int u = u0 + int(threadIdx.x);
-  double O[9];
+  double O[9], ON[9];
 #pragma unroll
-  for (int c = 0; c < 9; ++c) O[c] = 0.0;
+  for (int c = 0; c < 9; ++c) O[c] = ON[c] = 0.0;
   if (u < u1) {
     const uint32_t w = asm_unit[u];
     const int fe = int(w >> 10), a = int((w >> 5) & 31u), b = int(w & 31u);
@@ -218,6 +235,27 @@ __global__ void __launch_bounds__(256) k_assemble_A(const int32_t* __restrict__ 
           O[c * 3 + 2] = fma(dbc, fa2, O[c * 3 + 2]);
         }
       }
+      if (dn) {  // Newton term: N (D grad phi_a)_c (D grad phi_b)_d at every Gauss point
+        for (int q = 0; q < 27; ++q) {
+          const double* g = dn + (int64_t(fe) * 27 + q) * 7;
+          const double Dm[3][3] = {{g[0], g[3], g[4]}, {g[3], g[1], g[5]}, {g[4], g[5], g[2]}};
+          const double f = g[6] * st.wsc[q];
+          const double* da = st.dphi[q][a];
+          const double* db = st.dphi[q][b];
+          double ga[3], gb[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            ga[c] = Dm[c][0] * da[0] + Dm[c][1] * da[1] + Dm[c][2] * da[2];
+            gb[c] = Dm[c][0] * db[0] + Dm[c][1] * db[1] + Dm[c][2] * db[2];
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double fc = f * ga[c];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ON[c * 3 + d] = fma(fc, gb[d], ON[c * 3 + d]);
+          }
+        }
+      }
     } else {  // only the trace is needed
       for (int q = 0; q < 27; ++q) {
         const double f = __ldg(nq + q) * st.wsc[q];
@@ -230,21 +268,22 @@ __global__ void __launch_bounds__(256) k_assemble_A(const int32_t* __restrict__ 
     }
   }
 #pragma unroll
-  for (int c = 0; c < 9; ++c) part[threadIdx.x][c] = O[c];
+  for (int c = 0; c < 9; ++c) part[threadIdx.x][c] = form == GDSW_FORM_SYMMETRIC ? O[c] + ON[c] : 0.0;
+  part[threadIdx.x][9] = O[0] + O[4] + O[8];
   __syncthreads();
   for (int blk = blk0 + int(threadIdx.x); blk < blk1; blk += blockDim.x) {
     const int v0 = asm_uoff[blk], v1 = asm_uoff[blk + 1];
     if (v1 == v0) continue;  // a lower block: written as the transpose of its upper partner
-    double S[9];
+    double S[10];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) S[c] = part[v0 - u0][c];
+    for (int c = 0; c < 10; ++c) S[c] = part[v0 - u0][c];
     for (int v = v0 + 1; v < v1; ++v)
 #pragma unroll
-      for (int c = 0; c < 9; ++c) S[c] += part[v - u0][c];
-    const double tr = S[0] + S[4] + S[8];
+      for (int c = 0; c < 10; ++c) S[c] += part[v - u0][c];
+    const double tr = S[9];
     double out[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) out[c] = form == GDSW_FORM_SYMMETRIC ? S[c] : 0.0;
+    for (int c = 0; c < 9; ++c) out[c] = S[c];
     out[0] += tr;
     out[4] += tr;
     out[8] += tr;
@@ -477,6 +516,17 @@ __global__ void k_picard_velocity(const int32_t* __restrict__ vnode, int64_t nv,
   uk[3 * int64_t(vnode[I]) + (q - 3 * I)] = x[q];
 }
 
+__global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) x[i] += d[i];
+}
+
+void launch_axpy(double* x, const double* d, int64_t n, cudaStream_t s) {
+  if (n == 0) return;
+  k_axpy<<<int((n + 255) / 256), 256, 0, s>>>(x, d, n);
+  check_launch("k_axpy");
+}
+
 void launch_picard_velocity(gdsw_ctx* c, const double* x, cudaStream_t s) {
   const int64_t nv = c->mesh.nv;
   GDSW_CUDA(cudaMemcpyAsync(c->d_uk, c->d_gdir, sizeof(double) * 3 * c->mesh.nnodes, cudaMemcpyDeviceToDevice, s));
@@ -492,11 +542,11 @@ void launch_viscosity(gdsw_ctx* c, cudaStream_t s) {
   int64_t n = nfe * 27;
   k_viscosity<<<int((n + 255) / 256), 256, 0, s>>>(c->d_fluid, nfe, c->d_uk, static_cast<RefTables*>(c->d_tables),
                                                   geo(c), c->form, c->has_uk ? 1 : 0, c->nu0, c->nu_inf, c->lam,
-                                                  c->ncar, c->d_nu);
+                                                  c->ncar, c->d_nu, c->d_dn);
   check_launch("k_viscosity");
 }
 
-void launch_assembly(gdsw_ctx* c, cudaStream_t s) {
+void launch_assembly(gdsw_ctx* c, cudaStream_t s, bool newton) {
   const auto* T = static_cast<RefTables*>(c->d_tables);
   const int64_t np = c->mesh.np;
   double* aval = c->d_val;
@@ -505,7 +555,7 @@ void launch_assembly(gdsw_ctx* c, cudaStream_t s) {
   const int ncta = int(c->mesh.asm_cta.size()) - 1;
   if (ncta > 0)
     k_assemble_A<<<ncta, 256, 0, s>>>(c->d_asm_cta, c->d_asm_uoff, c->d_asm_unit, c->d_a_tpos, c->d_nu, T,
-                                      0.5 * c->mesh.h, c->form, aval);
+                                      0.5 * c->mesh.h, c->form, newton ? c->d_dn : nullptr, aval);
   check_launch("k_assemble_A");
   if (c->b_assembled) {  // B = -(q, div u) depends on the mesh only, not on the viscosity
     launch_sell_fill(c, false, s);

@@ -115,7 +115,19 @@ __global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, co
   double acc = 0.0;
   const TP* p = phiT + m.phi + l;
   int j = 0;
-  for (; j + 8 <= m.c; j += 8) {  // eight independent loads in flight, products in column order
+  for (; j + 16 <= m.c; j += 16) {  // sixteen independent loads in flight, products in column order
+    TP v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = __ldcs(p + int64_t(j + u) * m.ld);
+#pragma unroll
+    for (int h = 0; h < 16; h += 8) {
+      X part = X(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) part = fma(X(v[h + u]), xs[j + h + u], part);
+      acc += double(part);
+    }
+  }
+  for (; j + 8 <= m.c; j += 8) {
     TP v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + int64_t(j + u) * m.ld);

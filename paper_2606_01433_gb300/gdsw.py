@@ -141,6 +141,8 @@ def load(path: str = LIB_PATH):
         "gdsw_plan_bytes": ([vp, i32, i32, i32, C.POINTER(C.c_double)], C.c_int),
         "gdsw_set_local_sweep": ([vp, i32, i32, i32], C.c_int),
         "gdsw_picard_update": ([vp, vp], C.c_int),
+        "gdsw_residual": ([vp, dp, dp, dp], C.c_int),
+        "gdsw_newton_step": ([vp, dp, C.POINTER(gdsw_solve_info)], C.c_int),
         "gdsw_sweep_wait_selftest": ([vp], C.c_int),
         "gdsw_profile_enable": ([vp, i32], C.c_int),
         "gdsw_profile_read": ([vp, C.POINTER(gdsw_profile)], C.c_int),
@@ -325,6 +327,18 @@ class Context:
         self.gdsw_rhs_lift(b)
         info = self.gdsw_solve(b, x)
         self.gdsw_picard_update(x)
+        return info
+
+    def gdsw_residual(self, b, x, r):
+        return self._check(self.lib.gdsw_residual(self.h, _ptr(b), _ptr(x), _ptr(r)))
+
+    def newton_step(self, x):
+        """One Section 3 Newton step from the state x (device FP64; u_k must be its velocity):
+        gdsw_newton_step.  Returns the linear solve's gdsw_solve_info."""
+        info = gdsw_solve_info()
+        rc = self.lib.gdsw_newton_step(self.h, _ptr(x), C.byref(info))
+        if rc not in (GDSW_OK, GDSW_ERR_NOT_CONVERGED):
+            raise GdswError(rc, self.lib.gdsw_last_error(self.h).decode())
         return info
 
     def gdsw_apply_local(self, level, r, z):
