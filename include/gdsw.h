@@ -92,8 +92,11 @@ typedef struct {
 } gdsw_partition;
 
 typedef struct {
-  int32_t levels;        /* L in {2,3,4}: L-1 Schwarz levels, direct solve of A_0^(L) */
+  int32_t levels;        /* L in {2,3,4}: L-1 Schwarz levels, direct solve of A_0^(L); 1: operator only */
   int32_t overlap;       /* element layers of overlap on level 1 (the paper uses 1) */
+  int32_t rotations;     /* 1: add the rigid rotations about each entity's centroid to the
+                            level-1 coarse space (the null-space enrichment Section 2.1 leaves
+                            out; two levels only); 0: translations and pressure constants */
 } gdsw_levels;
 
 typedef struct {

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <tuple>
 
 #include "common.h"
 #include "kernels.h"
@@ -530,6 +531,11 @@ static void upload_coarse_space(gdsw_ctx* c, int l, int phi_prec) {
   L.rr_pos = c->arena.upload(C.rr_pos, s);
   L.rg_ptr = c->arena.upload(C.rg_ptr, s);
   L.rg_dof = c->arena.upload(C.rg_dof, s);
+  L.rg_val = c->arena.upload(C.rg_val, s);
+  L.gval = c->arena.upload(C.gval, s);
+  L.gu_dof = c->arena.upload(C.gu_dof, s);
+  L.gu_ptr = c->arena.upload(C.gu_ptr, s);
+  L.ngu = int64_t(C.gu_dof.size());
   // PhiT layout: part J stores c_J rows of length pad8(n_IJ)
   std::vector<ProMeta> meta(C.nparts);
   std::vector<GemvTask> tasks;
@@ -584,6 +590,7 @@ static std::vector<int64_t> phi_offsets(const CoarseSpace& C, std::vector<int32_
 // segment lists for A0 = sum of keyed contributions, built on the host
 struct SegList {
   std::vector<int64_t> key, ptr, pos;
+  std::vector<double> w;  // per entry weight (empty: all 1)
 };
 static SegList make_segments(std::vector<std::pair<int64_t, int64_t>>& kv) {
   std::stable_sort(kv.begin(), kv.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
@@ -600,12 +607,31 @@ static SegList make_segments(std::vector<std::pair<int64_t, int64_t>>& kv) {
   return L;
 }
 
+// the same with a weight per entry: kvw = (key, source position, weight)
+static SegList make_segments_w(std::vector<std::tuple<int64_t, int64_t, double>>& kvw) {
+  std::stable_sort(kvw.begin(), kvw.end(),
+                   [](const auto& a, const auto& b) { return std::get<0>(a) < std::get<0>(b); });
+  SegList L;
+  L.ptr.push_back(0);
+  for (size_t q = 0; q < kvw.size(); ++q) {
+    if (q == 0 || std::get<0>(kvw[q]) != std::get<0>(kvw[q - 1])) {
+      if (q > 0) L.ptr.push_back(int64_t(q));
+      L.key.push_back(std::get<0>(kvw[q]));
+    }
+    L.pos.push_back(std::get<1>(kvw[q]));
+    L.w.push_back(std::get<2>(kvw[q]));
+  }
+  if (!kvw.empty()) L.ptr.push_back(int64_t(kvw.size()));
+  return L;
+}
+
 static void run_segments(gdsw_ctx* c, SegList& L, const double* src, double* dst, DevArena& tmp) {
   if (L.key.empty()) return;
   int64_t* k = tmp.upload(L.key, c->stream);
   int64_t* p = tmp.upload(L.ptr, c->stream);
   int64_t* q = tmp.upload(L.pos, c->stream);
-  segsum(k, p, q, int64_t(L.key.size()), src, dst, c->stream);
+  double* w = L.w.empty() ? nullptr : tmp.upload(L.w, c->stream);
+  segsum(k, p, q, w, int64_t(L.key.size()), src, dst, c->stream);
 }
 
 // ------------------------------------------------------------------ factor storage
@@ -727,10 +753,14 @@ static void level1_coarse(gdsw_ctx* c, double* A0, double& minpiv) {
     factor_slabs<T>(S, fac, minpiv, s);
     // right-hand sides Tneg = -A_IGamma Phi_Gamma
     CSBuild B = cs_layout(C);
-    std::vector<int32_t> gamma_col(c->mesh.n, -1), ilocal(c->mesh.n, -1);
-    for (size_t q = 0; q < C.gdofs.size(); ++q) gamma_col[C.gdofs[q]] = C.gcol[q];
+    // Phi_Gamma entries by dof: gamma_ptr[g] .. gamma_ptr[g + 1] index gcol / gval (gdofs ascending)
+    std::vector<int32_t> gamma_ptr(c->mesh.n + 1, 0), ilocal(c->mesh.n, -1);
+    for (int32_t g : C.gdofs) ++gamma_ptr[g + 1];
+    for (int64_t g = 0; g < c->mesh.n; ++g) gamma_ptr[g + 1] += gamma_ptr[g];
     for (int64_t p = 0; p < S.nvec; ++p) ilocal[S.gdof[p]] = int32_t(p);
-    int32_t* d_gc = tmp.upload(gamma_col, s);
+    int32_t* d_gc = tmp.upload(gamma_ptr, s);
+    int32_t* d_gcol = tmp.upload(C.gcol, s);
+    double* d_gval = tmp.upload(C.gval, s);
     int32_t* d_il = tmp.upload(ilocal, s);
     int32_t* d_cols = tmp.upload(C.cols, s);
     int64_t* d_coff = tmp.upload(C.coff, s);
@@ -738,7 +768,7 @@ static void level1_coarse(gdsw_ctx* c, double* A0, double& minpiv) {
     int32_t* d_ldt = tmp.upload(B.ldt, s);
     double* Tn = tmp.alloc<double>(B.ttot);
     GDSW_CUDA(cudaMemsetAsync(Tn, 0, B.ttot * 8, s));
-    launch_tneg(A, SV, d_gc, d_cols, d_coff, d_toff, d_ldt, Tn, err, s);
+    launch_tneg(A, SV, d_gc, d_gcol, d_gval, d_cols, d_coff, d_toff, d_ldt, Tn, err, s);
     int herr = 0;
     GDSW_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     GDSW_CUDA(cudaStreamSynchronize(s));
@@ -793,37 +823,34 @@ static void level1_coarse(gdsw_ctx* c, double* A0, double& minpiv) {
     {
       // interface-interface couplings: positions into the value array
       const MeshHost& M = c->mesh;
-      std::vector<std::pair<int64_t, int64_t>> kv;
+      // (Phi_G^T A_GG Phi_G)_{kl} = sum over entries (a, k, w_a) and (b, l, w_b) of w_a w_b A_ab
+      std::vector<std::tuple<int64_t, int64_t, double>> kvw;
       const int64_t bt0 = 9 * c->nnzb, b0 = bt0 + 3 * c->nbt;
       for (int k = 0; k < C.n0; ++k) {
-        std::vector<std::pair<int64_t, int64_t>> row;
+        std::vector<std::tuple<int, int64_t, double>> row;
+        auto add = [&](int64_t b, int64_t pos, double wa) {
+          for (int32_t e = gamma_ptr[b]; e < gamma_ptr[b + 1]; ++e) row.emplace_back(C.gcol[e], pos, wa * C.gval[e]);
+        };
         for (int32_t e = C.rg_ptr[k]; e < C.rg_ptr[k + 1]; ++e) {
           int64_t a = C.rg_dof[e];
+          const double wa = C.rg_val[e];
           if (a < M.nu) {
             int64_t I = a / 3;
             int cc = int(a - 3 * I);
             for (int32_t blk = M.a_ptr[I]; blk < M.a_ptr[I + 1]; ++blk)
-              for (int d = 0; d < 3; ++d) {
-                int gc = gamma_col[3 * int64_t(M.a_col[blk]) + d];
-                if (gc >= 0) row.push_back({gc, int64_t(blk) * 9 + cc * 3 + d});
-              }
-            for (int32_t q = M.bt_ptr[I]; q < M.bt_ptr[I + 1]; ++q) {
-              int gc = gamma_col[M.nu + M.bt_col[q]];
-              if (gc >= 0) row.push_back({gc, bt0 + int64_t(q) * 3 + cc});
-            }
+              for (int d = 0; d < 3; ++d) add(3 * int64_t(M.a_col[blk]) + d, int64_t(blk) * 9 + cc * 3 + d, wa);
+            for (int32_t q = M.bt_ptr[I]; q < M.bt_ptr[I + 1]; ++q) add(M.nu + M.bt_col[q], bt0 + int64_t(q) * 3 + cc, wa);
           } else {
             int64_t P = a - M.nu;
             for (int32_t q = M.b_ptr[P]; q < M.b_ptr[P + 1]; ++q)
-              for (int d = 0; d < 3; ++d) {
-                int gc = gamma_col[3 * int64_t(M.b_col[q]) + d];
-                if (gc >= 0) row.push_back({gc, b0 + int64_t(q) * 3 + d});
-              }
+              for (int d = 0; d < 3; ++d) add(3 * int64_t(M.b_col[q]) + d, b0 + int64_t(q) * 3 + d, wa);
           }
         }
-        std::stable_sort(row.begin(), row.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-        for (auto& pr : row) kv.push_back({int64_t(k) * n0 + pr.first, pr.second});
+        std::stable_sort(row.begin(), row.end(),
+                         [](const auto& x, const auto& y) { return std::get<0>(x) < std::get<0>(y); });
+        for (auto& pr : row) kvw.emplace_back(int64_t(k) * n0 + std::get<0>(pr), std::get<1>(pr), std::get<2>(pr));
       }
-      SegList L = make_segments(kv);
+      SegList L = make_segments_w(kvw);
       run_segments(c, L, c->d_val, A0, tmp);
     }
     // store Phi_I^T in the storage precision
@@ -1054,7 +1081,7 @@ static void restrict_level(gdsw_ctx* c, int l, const double* r, double* r0, cuda
     launch_gemv<float, float>(static_cast<const float*>(L.phiT), static_cast<const float*>(L.rI),
                               static_cast<float*>(L.yc), nullptr, L.phi_plan, 0, L.max_ld_phi, s);
   }
-  launch_restrict_reduce(L.yc, L.phi_prec, r, L.rr_ptr, L.rr_pos, L.rg_ptr, L.rg_dof, r0, L.n0, s);
+  launch_restrict_reduce(L.yc, L.phi_prec, r, L.rr_ptr, L.rr_pos, L.rg_ptr, L.rg_dof, L.rg_val, r0, L.n0, s);
 }
 
 static void coarsest_solve(gdsw_ctx* c, const double* r0, double* x0, cudaStream_t s) {
@@ -1165,7 +1192,8 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
     // ---- host symbolic set-up (shared by gdsw_analyze, gdsw_setup and the server's admission)
     build_mesh(c->mesh, mesh);
     c->lh.assign(nlev, LevelHost());
-    if (nlev > 0) build_level1(c, part, lv->overlap, opt->slab_elems);
+    GDSW_CHECK(lv->rotations == 0 || lv->levels == 2, GDSW_ERR_INVALID_ARG, "rotation modes need two levels");
+    if (nlev > 0) build_level1(c, part, lv->overlap, opt->slab_elems, lv->rotations);
     for (int l = 1; l < nlev; ++l) {
       GDSW_CHECK(part->groups[l - 1] != nullptr, GDSW_ERR_INVALID_ARG, "null grouping array");
       build_coarse_level(c, l, part->groups[l - 1], part->group_len[l - 1]);

@@ -161,7 +161,10 @@ struct CoarseSpace {
   std::vector<int64_t> ioff;        // per part offset into idofs (nparts + 1)
   std::vector<int32_t> cols;        // concatenated coarse columns per part (ascending)
   std::vector<int64_t> coff;        // per part offset into cols (nparts + 1)
-  std::vector<int32_t> gdofs, gcol; // interface dofs (ascending) and their coarse column
+  std::vector<int32_t> gdofs, gcol; // Phi_Gamma entries: interface dof (ascending), coarse column
+  std::vector<double> gval;         //   and value (1 for translations and pressure constants)
+  std::vector<int32_t> gu_dof, gu_ptr;  // the distinct interface dofs and their entry ranges
+  std::vector<double> rg_val;       // values of the rg lists below
   // restriction reduce lists per coarse dof: positions in the concatenated per-part
   // result buffer (offset coff[J] + local column) and interface dofs
   std::vector<int32_t> rr_ptr, rr_pos, rg_ptr, rg_dof;
@@ -267,7 +270,10 @@ struct LevelDev {
   // coarse space
   int n0 = 0, phi_prec = GDSW_FP64;
   int32_t *idofs = nullptr, *cols = nullptr, *gdofs = nullptr, *gcol = nullptr;
-  int64_t nidofs = 0, ncols = 0, ngamma = 0;
+  int32_t *gu_dof = nullptr, *gu_ptr = nullptr;  // Phi_Gamma entries grouped by interface dof
+  double* gval = nullptr;                        // Phi_Gamma values
+  double* rg_val = nullptr;
+  int64_t nidofs = 0, ncols = 0, ngamma = 0, ngu = 0;
   void* phiT = nullptr;         // concatenated Phi_I^T blocks
   void* rI = nullptr;           // gathered interior residual (phi precision)
   void* yc = nullptr;           // per-part restricted values (phi precision)

@@ -9,6 +9,7 @@
 #include <thread>
 
 #include <atomic>
+#include <cmath>
 
 #include "common.h"
 
@@ -543,19 +544,34 @@ static void coarse_lists(CoarseSpace& C, const std::vector<std::vector<int>>& en
     C.rr_pos.insert(C.rr_pos.end(), rr[k].begin(), rr[k].end());
     C.rr_ptr[k + 1] = int32_t(C.rr_pos.size());
   }
-  std::vector<std::vector<int32_t>> rg(C.n0);
-  for (size_t q = 0; q < C.gdofs.size(); ++q) rg[C.gcol[q]].push_back(C.gdofs[q]);
+  if (C.gval.size() != C.gdofs.size()) C.gval.assign(C.gdofs.size(), 1.0);  // indicator entries
+  std::vector<std::vector<std::pair<int32_t, double>>> rg(C.n0);
+  for (size_t q = 0; q < C.gdofs.size(); ++q) rg[C.gcol[q]].push_back({C.gdofs[q], C.gval[q]});
   C.rg_ptr.assign(C.n0 + 1, 0);
   C.rg_dof.clear();
+  C.rg_val.clear();
   for (int k = 0; k < C.n0; ++k) {
     std::sort(rg[k].begin(), rg[k].end());
-    C.rg_dof.insert(C.rg_dof.end(), rg[k].begin(), rg[k].end());
+    for (auto& e : rg[k]) {
+      C.rg_dof.push_back(e.first);
+      C.rg_val.push_back(e.second);
+    }
     C.rg_ptr[k + 1] = int32_t(C.rg_dof.size());
   }
+  // entries grouped by interface dof (gdofs ascending): prolongation, one thread per dof
+  C.gu_dof.clear();
+  C.gu_ptr.assign(1, 0);
+  for (size_t q = 0; q < C.gdofs.size(); ++q) {
+    if (q == 0 || C.gdofs[q] != C.gdofs[q - 1]) {
+      if (q > 0) C.gu_ptr.push_back(int32_t(q));
+      C.gu_dof.push_back(C.gdofs[q]);
+    }
+  }
+  if (!C.gdofs.empty()) C.gu_ptr.push_back(int32_t(C.gdofs.size()));
 }
 
 // ------------------------------------------------------------------ level 1
-void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int slab_elems) {
+void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int slab_elems, int rotations) {
   MeshHost& M = ctx->mesh;
   LevelHost& L = ctx->lh[0];
   const int64_t ne = int64_t(M.nx) * M.ny * M.nz;
@@ -728,17 +744,54 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
   C.n_entities = int(ents.size());
   std::vector<std::vector<int>> ent_cols(ents.size());
   int n0 = 0;
-  std::vector<std::array<int, 4>> ecol(ents.size());
+  std::vector<std::array<int, 7>> ecol(ents.size());
+  // rotations: e_a x (x - x_c) about the centroid x_c of the entity's free velocity nodes, kept
+  // when it does not vanish on the entity (the one about a straight edge's own line does)
+  std::vector<std::array<double, 3>> centroid(ents.size(), {0.0, 0.0, 0.0});
+  auto node_xyz = [&](int64_t v, double x[3]) {
+    int i, j, k;
+    M.coords(v, i, j, k);
+    x[0] = M.origin[0] + 0.5 * M.h * i;
+    x[1] = M.origin[1] + 0.5 * M.h * j;
+    x[2] = M.origin[2] + 0.5 * M.h * k;
+  };
+  auto rot_value = [&](size_t e, int64_t v, int a, int comp) {  // (e_a x (x - x_c))_comp
+    double x[3];
+    node_xyz(v, x);
+    double d[3] = {x[0] - centroid[e][0], x[1] - centroid[e][1], x[2] - centroid[e][2]};
+    double ea[3] = {0, 0, 0};
+    ea[a] = 1.0;
+    double cr[3] = {ea[1] * d[2] - ea[2] * d[1], ea[2] * d[0] - ea[0] * d[2], ea[0] * d[1] - ea[1] * d[0]};
+    return cr[comp];
+  };
   C.cn_set.clear(); C.cn_dofs.clear(); C.cn_modes.clear();
   for (size_t e = 0; e < ents.size(); ++e) {
     bool hv = false, hp = false;
+    int nvel = 0;
     for (int64_t v : ents[e].nodes) {
       hv |= M.vidx[v] >= 0;
       hp |= M.pidx[v] >= 0;
+      if (M.vidx[v] >= 0) {
+        double x[3];
+        node_xyz(v, x);
+        for (int d = 0; d < 3; ++d) centroid[e][d] += x[d];
+        ++nvel;
+      }
     }
+    if (nvel > 0)
+      for (int d = 0; d < 3; ++d) centroid[e][d] /= nvel;
+    bool keep_rot[3] = {false, false, false};
+    if (rotations && nvel >= 2)
+      for (int a = 0; a < 3; ++a) {
+        double nrm = 0.0;
+        for (int64_t v : ents[e].nodes)
+          if (M.vidx[v] >= 0)
+            for (int comp = 0; comp < 3; ++comp) nrm += rot_value(e, v, a, comp) * rot_value(e, v, a, comp);
+        keep_rot[a] = std::sqrt(nrm) > 1e-8 * M.h;
+      }
     std::vector<int> dofs, modes;
-    for (int md = 0; md < 4; ++md) {
-      bool present = md < 3 ? hv : hp;
+    for (int md = 0; md < 7; ++md) {
+      bool present = md < 3 ? hv : (md == 3 ? hp : keep_rot[md - 4]);
       ecol[e][md] = present ? n0 : -1;
       if (present) {
         dofs.push_back(n0);
@@ -755,17 +808,24 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
   C.gdofs.clear();
   C.gcol.clear();
   {
-    std::vector<std::pair<int32_t, int32_t>> gl;
+    struct GE { int32_t dof, col; double val; };
+    std::vector<GE> gl;
     for (size_t e = 0; e < ents.size(); ++e)
       for (int64_t v : ents[e].nodes) {
         if (M.vidx[v] >= 0)
-          for (int c = 0; c < 3; ++c) gl.push_back({int32_t(3 * M.vidx[v] + c), ecol[e][c]});
-        if (M.pidx[v] >= 0) gl.push_back({int32_t(M.nu + M.pidx[v]), ecol[e][3]});
+          for (int c = 0; c < 3; ++c) {
+            gl.push_back({int32_t(3 * M.vidx[v] + c), ecol[e][c], 1.0});
+            for (int a = 0; a < 3; ++a)
+              if (ecol[e][4 + a] >= 0) gl.push_back({int32_t(3 * M.vidx[v] + c), ecol[e][4 + a], rot_value(e, v, a, c)});
+          }
+        if (M.pidx[v] >= 0) gl.push_back({int32_t(M.nu + M.pidx[v]), ecol[e][3], 1.0});
       }
-    std::sort(gl.begin(), gl.end());
+    std::sort(gl.begin(), gl.end(), [](const GE& a, const GE& b) { return a.dof != b.dof ? a.dof < b.dof : a.col < b.col; });
+    C.gval.clear();
     for (auto& q : gl) {
-      C.gdofs.push_back(q.first);
-      C.gcol.push_back(q.second);
+      C.gdofs.push_back(q.dof);
+      C.gcol.push_back(q.col);
+      C.gval.push_back(q.val);
     }
   }
   // interiors: nodes whose sharing set is {i}

@@ -83,9 +83,10 @@ template <typename TV>
 void launch_scatter(const TV* x, const int32_t* ptr, const int32_t* pos, const double* w, double* z, int n,
                     int accumulate, cudaStream_t s);
 void launch_restrict_reduce(const void* yc, int prec, const double* r, const int32_t* rr_ptr, const int32_t* rr_pos,
-                            const int32_t* rg_ptr, const int32_t* rg_dof, double* r0, int n0, cudaStream_t s);
+                            const int32_t* rg_ptr, const int32_t* rg_dof, const double* rg_val, double* r0, int n0,
+                            cudaStream_t s);
 void launch_prolong(const LevelDev& L, const double* x0, double* z, cudaStream_t s);
-void launch_axpy_gamma(const int32_t* gdofs, const int32_t* gcol, int64_t ng, const double* x0, double* z,
-                       cudaStream_t s);
+void launch_axpy_gamma(const int32_t* gu_dof, const int32_t* gu_ptr, const int32_t* gcol, const double* gval,
+                       int64_t ngu, const double* x0, double* z, cudaStream_t s);
 
 }  // namespace gdsw

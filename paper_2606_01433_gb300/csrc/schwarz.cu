@@ -56,28 +56,29 @@ template <typename TP>
 __global__ void k_restrict_reduce(const TP* __restrict__ yc, const double* __restrict__ r,
                                   const int32_t* __restrict__ rr_ptr, const int32_t* __restrict__ rr_pos,
                                   const int32_t* __restrict__ rg_ptr, const int32_t* __restrict__ rg_dof,
-                                  double* __restrict__ r0, int n0) {
+                                  const double* __restrict__ rg_val, double* __restrict__ r0, int n0) {
   int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (k >= n0) return;
   double acc = 0.0;
   for (int e = rr_ptr[k] + lane; e < rr_ptr[k + 1]; e += 32) acc += double(yc[rr_pos[e]]);
-  for (int e = rg_ptr[k] + lane; e < rg_ptr[k + 1]; e += 32) acc += r[rg_dof[e]];
+  for (int e = rg_ptr[k] + lane; e < rg_ptr[k + 1]; e += 32) acc = fma(rg_val[e], r[rg_dof[e]], acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) r0[k] = acc;
 }
 
 void launch_restrict_reduce(const void* yc, int prec, const double* r, const int32_t* rr_ptr, const int32_t* rr_pos,
-                            const int32_t* rg_ptr, const int32_t* rg_dof, double* r0, int n0, cudaStream_t s) {
+                            const int32_t* rg_ptr, const int32_t* rg_dof, const double* rg_val, double* r0, int n0,
+                            cudaStream_t s) {
   if (n0 == 0) return;
   int blocks = (n0 + 7) / 8;
   if (prec == GDSW_FP64)
     k_restrict_reduce<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(yc), r, rr_ptr, rr_pos, rg_ptr, rg_dof,
-                                                     r0, n0);
+                                                     rg_val, r0, n0);
   else
     k_restrict_reduce<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(yc), r, rr_ptr, rr_pos, rg_ptr, rg_dof,
-                                                    r0, n0);
+                                                    rg_val, r0, n0);
   check_launch("k_restrict_reduce");
 }
 
@@ -143,10 +144,16 @@ __global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, co
   z[g] += acc;
 }
 
-__global__ void k_axpy_gamma(const int32_t* __restrict__ gdofs, const int32_t* __restrict__ gcol, int64_t ng,
+// z[g] += sum over the Phi_Gamma entries of interface dof g of value * x0[column], one thread
+// per interface dof, entries in column order
+__global__ void k_axpy_gamma(const int32_t* __restrict__ gu_dof, const int32_t* __restrict__ gu_ptr,
+                             const int32_t* __restrict__ gcol, const double* __restrict__ gval, int64_t ngu,
                              const double* __restrict__ x0, double* __restrict__ z) {
   int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (q < ng) z[gdofs[q]] += x0[gcol[q]];
+  if (q >= ngu) return;
+  double acc = 0.0;
+  for (int32_t e = gu_ptr[q]; e < gu_ptr[q + 1]; ++e) acc = fma(gval[e], x0[gcol[e]], acc);
+  z[gu_dof[q]] += acc;
 }
 
 void launch_prolong(const LevelDev& L, const double* x0, double* z, cudaStream_t s) {
@@ -162,13 +169,13 @@ void launch_prolong(const LevelDev& L, const double* x0, double* z, cudaStream_t
                                                         L.pro_tile_col0, L.idofs, L.cols, x0, z);
     check_launch("k_prolong");
   }
-  launch_axpy_gamma(L.gdofs, L.gcol, L.ngamma, x0, z, s);
+  launch_axpy_gamma(L.gu_dof, L.gu_ptr, L.gcol, L.gval, L.ngu, x0, z, s);
 }
 
-void launch_axpy_gamma(const int32_t* gdofs, const int32_t* gcol, int64_t ng, const double* x0, double* z,
-                       cudaStream_t s) {
-  if (ng == 0) return;
-  k_axpy_gamma<<<int((ng + 255) / 256), 256, 0, s>>>(gdofs, gcol, ng, x0, z);
+void launch_axpy_gamma(const int32_t* gu_dof, const int32_t* gu_ptr, const int32_t* gcol, const double* gval,
+                       int64_t ngu, const double* x0, double* z, cudaStream_t s) {
+  if (ngu == 0) return;
+  k_axpy_gamma<<<int((ngu + 255) / 256), 256, 0, s>>>(gu_dof, gu_ptr, gcol, gval, ngu, x0, z);
   check_launch("k_axpy_gamma");
 }
 

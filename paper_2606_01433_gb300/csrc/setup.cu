@@ -107,10 +107,11 @@ __device__ __forceinline__ int find_col(const int32_t* cols, int c, int key) {
   return (lo < c && cols[lo] == key) ? lo : -1;
 }
 
-// Tneg = -A_IGamma Phi_Gamma for every interior row (one thread per row, nonzero order):
-// Phi_Gamma is the entity indicator, so each interface column adds its value to the
-// coarse column of its entity.
-__global__ void k_tneg(MatView A, SlabView S, const int32_t* __restrict__ gamma_col, const int32_t* __restrict__ cols,
+// Tneg = -A_IGamma Phi_Gamma for every interior row (one thread per row, nonzero order): each
+// interface column adds its value times its Phi_Gamma entries (gamma_ptr: entry range of every
+// dof, empty off the interface) to their coarse columns.
+__global__ void k_tneg(MatView A, SlabView S, const int32_t* __restrict__ gamma_ptr, const int32_t* __restrict__ gcol,
+                       const double* __restrict__ gval, const int32_t* __restrict__ cols,
                        const int64_t* __restrict__ coff, const int64_t* __restrict__ toff, const int32_t* __restrict__ ldt,
                        double* __restrict__ T, int* __restrict__ err) {
   int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -120,14 +121,14 @@ __global__ void k_tneg(MatView A, SlabView S, const int32_t* __restrict__ gamma_
   const int32_t* ci = cols + coff[i];
   const int c = int(coff[i + 1] - coff[i]);
   row_visit(A, S.gdof[p], [&](int64_t col, double v) {
-    int gc = gamma_col[col];
-    if (gc < 0) return;
-    int j = find_col(ci, c, gc);
-    if (j < 0) {
-      atomicExch(err, 2);
-      return;
+    for (int32_t e = gamma_ptr[col]; e < gamma_ptr[col + 1]; ++e) {
+      int j = find_col(ci, c, gcol[e]);
+      if (j < 0) {
+        atomicExch(err, 2);
+        return;
+      }
+      T[rowoff + j] -= v * gval[e];
     }
-    T[rowoff + j] -= v;
   });
 }
 
@@ -164,21 +165,24 @@ __global__ void k_yint(MatView A, SlabView S, const int32_t* __restrict__ ilocal
   }
 }
 
-// A0[key] += sum of src[pos] over a segment (deterministic list order)
+// A0[key] += sum of (w *) src[pos] over a segment (deterministic list order; w null = 1)
 __global__ void k_segsum(const int64_t* __restrict__ key, const int64_t* __restrict__ ptr,
-                         const int64_t* __restrict__ pos, int64_t nseg, const double* __restrict__ src,
-                         double* __restrict__ dst) {
+                         const int64_t* __restrict__ pos, const double* __restrict__ w, int64_t nseg,
+                         const double* __restrict__ src, double* __restrict__ dst) {
   int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (s >= nseg) return;
   double acc = 0.0;
-  for (int64_t e = ptr[s]; e < ptr[s + 1]; ++e) acc += src[pos[e]];
+  if (w)
+    for (int64_t e = ptr[s]; e < ptr[s + 1]; ++e) acc = fma(w[e], src[pos[e]], acc);
+  else
+    for (int64_t e = ptr[s]; e < ptr[s + 1]; ++e) acc += src[pos[e]];
   dst[key[s]] += acc;
 }
 
-void segsum(const int64_t* key, const int64_t* ptr, const int64_t* pos, int64_t nseg, const double* src, double* dst,
-            cudaStream_t s) {
+void segsum(const int64_t* key, const int64_t* ptr, const int64_t* pos, const double* w, int64_t nseg,
+            const double* src, double* dst, cudaStream_t s) {
   if (nseg == 0) return;
-  k_segsum<<<int((nseg + 255) / 256), 256, 0, s>>>(key, ptr, pos, nseg, src, dst);
+  k_segsum<<<int((nseg + 255) / 256), 256, 0, s>>>(key, ptr, pos, w, nseg, src, dst);
   check_launch("k_segsum");
 }
 
@@ -293,10 +297,11 @@ void dense_gamma(const int32_t* gdofs, const int32_t* gcol, int64_t ng, double* 
 }  // namespace gdsw
 
 namespace gdsw {
-void launch_tneg(const MatView& A, const SlabView& S, const int32_t* gamma_col, const int32_t* cols,
+void launch_tneg(const MatView& A, const SlabView& S, const int32_t* gamma_ptr, const int32_t* gcol,
+                 const double* gval, const int32_t* cols,
                  const int64_t* coff, const int64_t* toff, const int32_t* ldt, double* T, int* err, cudaStream_t s) {
   if (S.nvec == 0) return;
-  k_tneg<<<int((S.nvec + 127) / 128), 128, 0, s>>>(A, S, gamma_col, cols, coff, toff, ldt, T, err);
+  k_tneg<<<int((S.nvec + 127) / 128), 128, 0, s>>>(A, S, gamma_ptr, gcol, gval, cols, coff, toff, ldt, T, err);
   check_launch("k_tneg");
 }
 void launch_yint(const MatView& A, const SlabView& S, const int32_t* ilocal, const int64_t* coff, const int64_t* toff,

@@ -47,7 +47,7 @@ class gdsw_partition(C.Structure):
 
 
 class gdsw_levels(C.Structure):
-    _fields_ = [("levels", C.c_int32), ("overlap", C.c_int32)]
+    _fields_ = [("levels", C.c_int32), ("overlap", C.c_int32), ("rotations", C.c_int32)]
 
 
 class gdsw_options(C.Structure):
@@ -215,7 +215,7 @@ class Context:
 
     def __init__(self, prob, levels=None, weighting="pou", precision=("fp64", "fp64", "fp64"),
                  phi_precision="fp64", restart=100, max_it=1000, tol=1e-8, slab_elems=1, use_graph=False,
-                 overlap=1, stream=None, analyze_only=False):
+                 overlap=1, stream=None, analyze_only=False, rotations=False):
         lib = load()
         self.lib = lib
         self.prob = prob
@@ -242,7 +242,7 @@ class Context:
             self._keep.append(gr)
             pa.groups[l] = gr.ctypes.data
             pa.group_len[l] = gr.size
-        lv = gdsw_levels(L, overlap)
+        lv = gdsw_levels(L, overlap, 1 if rotations else 0)
         if stream is None and not analyze_only:
             try:
                 import torch
@@ -500,7 +500,7 @@ class Server:
             keep.append(gr)
             r.part.groups[l] = gr.ctypes.data
             r.part.group_len[l] = gr.size
-        r.levels = gdsw_levels(L, 1)
+        r.levels = gdsw_levels(L, 1, 0)
         prec = [PREC[q] for q in precision]
         r.opt = gdsw_options(WEIGHT_POU if weighting == "pou" else WEIGHT_PLAIN, (C.c_int32 * 3)(*prec),
                              PREC[phi_precision], restart, max_it, tol, slab_elems, 0, None)

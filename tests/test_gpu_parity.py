@@ -372,3 +372,52 @@ def test_picard_newton_iterates_match_oracle(lib):
     rn = float(torch.linalg.norm(r) / torch.linalg.norm(b))
     assert rn <= 10 * res[-1] ** 2 + 1e-11, (rn, res)
     ctx.close()
+
+
+ROT_PROBLEMS = {
+    "box_carreau": lambda: I.box_problem(4, 4, 4, (2, 2, 2), levels=2, form="symmetric", uk_seed=3, lam=1.0, n=0.5,
+                                         nu_inf=1e-3),
+    "channel12_obstacles": lambda: I.channel(12, parts=(2, 2, 2), groups=(), levels=2),
+}
+
+
+@pytest.mark.parametrize("name", list(ROT_PROBLEMS))
+def test_rotation_coarse_space(lib, name):
+    """Rotations in the coarse velocity null space (the variant Section 2.1 leaves out; two
+    levels): the GPU's weighted interface basis gives the oracle's coarse dimension, Phi^T r,
+    Phi x and Galerkin A_0 (<= 1e-12), apply (<= 1e-11) and FP64 solve (<= 1e-10, iterations
+    +-1); the mixed path reaches the FP64 solution to 1e-8."""
+    from oracle import fem, fgmres, gdsw as og
+    p = ROT_PROBLEMS[name]()
+    S = fem.assemble(p)
+    P = og.GDSW(S, p, rotations=True)
+    lev = P.levels[0]
+    ctx = lib.Context(p, tol=1e-10, rotations=True)
+    assert int(ctx.sizes.n_coarse[0]) == lev.n0 > og.GDSW(S, p).levels[0].n0
+    rng = np.random.default_rng(21)
+    r = rng.standard_normal(lev.n)
+    r0 = torch.zeros(lev.n0, dtype=torch.float64, device="cuda")
+    ctx.gdsw_restrict(0, dev(r), r0)
+    assert rel(host(r0), lev.Phi.T @ r) <= 1e-12
+    x0 = rng.standard_normal(lev.n0)
+    z = torch.zeros(lev.n, dtype=torch.float64, device="cuda")
+    ctx.gdsw_prolong(0, dev(x0), z)
+    assert rel(host(z), lev.Phi @ x0) <= 1e-12
+    assert rel(ctx.gdsw_coarse_matrix(0), P.A0[1]) <= 1e-12
+    ctx.gdsw_apply(dev(r), z)
+    assert rel(host(z), P.apply(r)) <= 1e-11
+    b = fem.lifted_rhs(S)
+    xo, io = fgmres.fgmres(lambda v: S["A"] @ v, b, P.apply, tol=1e-10)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.gdsw_solve(dev(b), x)
+    assert info.status == 0 and abs(info.iterations - io["iterations"]) <= 1
+    assert rel(host(x), xo) <= 1e-10
+    ctx.close()
+    x13, _ = fgmres.fgmres(lambda v: S["A"] @ v, b, P.apply, tol=1e-13)
+    cm = lib.Context(p, precision=FP32[0], phi_precision=FP32[1], tol=1e-12, rotations=True)
+    x = torch.zeros(cm.n, dtype=torch.float64, device="cuda")
+    info = cm.gdsw_solve(dev(b), x)
+    assert info.status == 0 and rel(host(x), x13) <= 1e-8
+    cm.close()
+    with pytest.raises(lib.GdswError):
+        lib.Context(I.box_problem(4, 4, 2, (4, 4, 2), groups=((2, 2, 1),), levels=3), rotations=True)
