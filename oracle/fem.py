@@ -13,7 +13,9 @@ Paper passages followed:
     traction-free outflow sigma n = 0.  We use nu = nu_inf + (nu0 - nu_inf)(...) which is
     the paper's law for nu_inf = 0.
 The paper uses Q2 / P1-discontinuous elements; the workloads here use Q2 / Q1
-(Taylor-Hood) with 3x3x3 Gauss quadrature on axis-aligned cubes of edge h.
+(Taylor-Hood) with 3x3x3 Gauss quadrature on axis-aligned cubes of edge h; prob.pressure =
+"p1disc" selects the paper's pair (pressure 1, xi, eta, zeta per element in reference
+coordinates; four dofs per fluid element after the velocity dofs, element order).
 
 Dof order (identical to the library's): free velocity nodes in increasing node index,
 three interleaved components each, then the Q1 (even-index) nodes of the fluid region in
@@ -107,9 +109,13 @@ class Mesh:
         self.dindex = -np.ones(prob.n_nodes, dtype=np.int64)
         self.dindex[self.dnodes] = np.arange(self.dnodes.size)
         self.pindex = -np.ones(prob.n_nodes, dtype=np.int64)
-        self.pindex[self.pnodes] = np.arange(self.pnodes.size)
+        self.pdisc = getattr(prob, "pressure", "q1") == "p1disc"
+        if self.pdisc:      # no nodal pressure: four dofs per fluid element, element order
+            self.pnodes = np.zeros(0, dtype=np.int64)
+        else:
+            self.pindex[self.pnodes] = np.arange(self.pnodes.size)
         self.nu = 3 * self.vnodes.size
-        self.np_ = self.pnodes.size
+        self.np_ = 4 * self.elems.size if self.pdisc else self.pnodes.size
         self.n = self.nu + self.np_
 
 
@@ -188,6 +194,22 @@ def element_matrices(form, h, nu_q, tabs):
     return np.einsum("eq,qij->eij", nu_q, M)
 
 
+def p1disc_values(tabs):
+    """The discontinuous P1 pressure basis at the 27 Gauss points: 1, xi, eta, zeta (reference
+    coordinates of the element, [-1, 1]^3): (27q, 4)."""
+    q = np.arange(27)
+    xi = np.stack([GAUSS_X[q % 3], GAUSS_X[(q // 3) % 3], GAUSS_X[q // 9]], axis=1)
+    return np.concatenate([np.ones((27, 1)), xi], axis=1)
+
+
+def element_divergence_p1disc(h, tabs):
+    """B_e (4, 81): -int psi_k d_d phi_b for the P1-disc pressure basis (p1disc_values)."""
+    phi, dphi, psi, w = tabs
+    scale = (h / 2.0) ** 3 * (2.0 / h)
+    Be = -np.einsum("q,qk,qbd->kbd", w * scale, p1disc_values(tabs), dphi)
+    return Be.reshape(4, 81)
+
+
 def element_divergence(h, tabs):
     """B_e (8, 81): -int psi_P d_d phi_b, det J (h/2)^3 and gradient scale 2/h."""
     phi, dphi, psi, w = tabs
@@ -243,11 +265,16 @@ def assemble(prob, chunk=2048, pool=None, newton=False):
         parts = list(run(lambda ab: ab[0] + ab[1] if len(ab) == 2 else ab[0], pairs))
     K = parts[0]
     # divergence rows (pressure) x velocity columns
-    prow = mesh.pindex[mesh.epnodes]                                   # (ne, 8)
     vdof = (node_col[mesh.enodes][:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 81)
+    if mesh.pdisc:    # Section 2's Q2 / P1-disc pair: four element-local pressure rows
+        Be = element_divergence_p1disc(prob.h, tabs)
+        prow = 4 * np.arange(ne)[:, None] + np.arange(4)[None, :]      # (ne, 4)
+    else:
+        prow = mesh.pindex[mesh.epnodes]                               # (ne, 8)
+    npe = prow.shape[1]
     r = np.repeat(prow[:, :, None], 81, axis=2).ravel()
-    c = np.repeat(vdof[:, None, :], 8, axis=1).ravel()
-    v = np.broadcast_to(Be[None], (ne, 8, 81)).ravel()
+    c = np.repeat(vdof[:, None, :], npe, axis=1).ravel()
+    v = np.broadcast_to(Be[None], (ne, npe, 81)).ravel()
     B = sp.csr_matrix((v, (r, c)), shape=(mesh.np_, nvel))
     A_ff = K[:nu_tot, :nu_tot]
     A_fd = K[:nu_tot, nu_tot:]
@@ -274,6 +301,8 @@ def full_solution(sys_, x):
     u = np.zeros((p.n_nodes, 3))
     u[mesh.vnodes] = x[:mesh.nu].reshape(-1, 3)
     u[mesh.dnodes] = p.g[mesh.dnodes]
+    if mesh.pdisc:   # P1-disc: per fluid element (constant, d/dxi, d/deta, d/dzeta) coefficients
+        return u, x[mesh.nu:].reshape(-1, 4).copy()
     pr = np.zeros(p.n_nodes)
     pr[mesh.pnodes] = x[mesh.nu:]
     return u, pr

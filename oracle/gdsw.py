@@ -34,6 +34,15 @@ Readings where the paper is silent (the same list is in the design notes):
 Optional variant (two levels only): rotation modes per entity (rigid rotations about the
 entity's centroid), the null-space enrichment the paper leaves out.
 
+Optional variant (two levels only): the paper's Q2 / P1-disc pair (prob.pressure =
+"p1disc"; four pressure dofs per element).  Readings: R_i keeps the pressure dofs of the
+elements of Omega_i' none of whose 27 nodes lies on the artificial rim (with Dirichlet
+velocity there, the constant pressure on all of Omega_i' would be a kernel of A_i); the
+interface carries no pressure dof, so the coarse space gets one pressure column per
+subdomain -- the constant on the subdomain's own elements, prescribed through the element
+constants, which join Gamma -- while the linear pressure dofs of a subdomain's elements are
+interior and extended; with one subdomain the coarse space is empty.
+
 Optional mixed-precision emulation (`local_precision`): the inputs and outputs of every
 local solve of a level are rounded to FP32 or BF16 while the solve itself stays exact, so
 that iteration counts of the GPU's mixed path (FP32/BF16 local solves recovered by the FP64
@@ -41,7 +50,9 @@ FGMRES) have an oracle counterpart.
 
 Parity status: pinned (partition of unity, constant reproduction, extension property,
 brute-force dense preconditioner, one-subdomain reduction, level collapse, symmetry; the
-rotation variant by rigid rotations lying in the range of Phi).
+rotation variant by rigid rotations lying in the range of Phi; the P1-disc variant by the
+Poiseuille closed form, the box-geometric count of its local pressure sets, its pressure
+columns on the cavity, the extension property and a brute-force dense two-level operator).
 """
 from __future__ import annotations
 
@@ -159,6 +170,17 @@ def _coarse_columns(entity_modes):
     return col, c, nodes
 
 
+def _p1disc_kept(mesh, NE, nodes):
+    """P1-disc pressure dofs of the overlapping subdomain whose kept nodes are `nodes`: the four
+    dofs of every fluid element all of whose 27 nodes are kept (so no element touching the
+    artificial boundary carries pressure; with Dirichlet velocity there the subdomain's constant
+    pressure would otherwise be a kernel of A_i)."""
+    mark = np.zeros(NE.shape[0])
+    mark[nodes] = 1.0
+    els = np.nonzero(np.asarray(NE.T @ mark).ravel() == 27)[0]
+    return (mesh.nu + 4 * els[:, None] + np.arange(4)[None, :]).ravel()
+
+
 def overlapping_dofs(sys_, prob, overlap=1):
     """Free dofs of every overlapping subdomain Omega_i' (Section 2.1; overlap reading in the
     module header): index sets only, no factorisation."""
@@ -185,6 +207,8 @@ def overlapping_dofs(sys_, prob, overlap=1):
         v = vnode_dof[nodes]
         v = v[v >= 0]
         pp = pnode_dof[nodes]
+        if mesh.pdisc:
+            pp = _p1disc_kept(mesh, NE, nodes)
         out.append(np.sort(np.concatenate([(v[:, None] + np.arange(3)[None, :]).ravel(), pp[pp >= 0]])))
     return out
 
@@ -245,7 +269,10 @@ def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False, pool
     for i in range(N):
         col = cntc[:, i]
         nodes = col.indices[col.data == deg[col.indices]]
-        lev.dofs.append(node_dofs(nodes))
+        d = node_dofs(nodes)
+        if mesh.pdisc:
+            d = np.sort(np.concatenate([d, _p1disc_kept(mesh, NE, nodes)]))
+        lev.dofs.append(d)
     lev.solvers = []
     if pool is not None and not dense_local:
         pool.share_csr("A", A)
@@ -315,6 +342,15 @@ def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False, pool
                 for c in range(3):
                     g_rows.append(v + c); g_cols.append(np.full(v.size, col[(e, 4 + a)]))
                     g_vals.append(ent_rot[e][:, a, c])
+    if mesh.pdisc and N >= 2:
+        # P1-disc: no pressure dof lies on the interface, so the pressure null space enters as
+        # one column per subdomain -- the constant pressure on the subdomain's own elements --
+        # prescribed like an interface trace (the element constants join Gamma; the linear
+        # pressure dofs stay interior and are extended).  With one subdomain there is no
+        # interface and the coarse space stays empty.
+        el_const = mesh.nu + 4 * np.arange(ne)
+        g_rows.append(el_const); g_cols.append(n0 + sub); g_vals.append(np.ones(ne))
+        n0 += N
     g_rows = np.concatenate(g_rows) if g_rows else np.zeros(0, int)
     g_cols = np.concatenate(g_cols) if g_cols else np.zeros(0, int)
     g_vals = np.concatenate(g_vals) if g_vals else np.zeros(0)
@@ -331,6 +367,10 @@ def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False, pool
     blocks = []                      # (interior dofs, coupled columns, -A_IGamma Phi_Gamma)
     for i in range(N):
         I = node_dofs(inter_nodes[owner == i])
+        if mesh.pdisc:   # the pressure dofs of the subdomain's own elements that are not in Gamma
+            els = np.nonzero(sub == i)[0]
+            k = np.arange(1, 4) if N >= 2 else np.arange(4)
+            I = np.sort(np.concatenate([I, (mesh.nu + 4 * els[:, None] + k[None, :]).ravel()]))
         lev.interior.append(I)
         if I.size == 0 or n0 == 0:
             continue
@@ -453,6 +493,8 @@ class GDSW:
         L = prob.levels if levels is None else levels
         if rotations and L > 2:
             raise ValueError("rotation modes are defined for two-level GDSW only")
+        if sys_["mesh"].pdisc and L > 2:
+            raise ValueError("the P1-disc coarse space is defined for two-level GDSW only")
         self.L = L
         self.weighting = weighting
         self.levels = []

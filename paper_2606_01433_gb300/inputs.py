@@ -51,6 +51,8 @@ class Problem:
     groups: list = dataclasses.field(default_factory=list)  # level l>=2 grouping arrays (int32)
     levels: int = 2
     rhs_seed: int | None = None     # random right-hand side on free dofs (seeded), else lifted inflow
+    pressure: str = "q1"            # "q1": continuous Q1 (Taylor-Hood); "p1disc": discontinuous P1
+                                    # per element (constant and three linear dofs, element order)
 
     @property
     def n_nodes(self) -> int:
@@ -329,7 +331,7 @@ def _groups_from_boxes(parts, groups, used, levels):
     return out
 
 
-def poiseuille(m=4, G=1.0, parts=(1, 1, 1), groups=None, levels=2):
+def poiseuille(m=4, G=1.0, parts=(1, 1, 1), groups=None, levels=2, pressure="q1"):
     """Analytic Poiseuille pin: nu = 1, gradient form on the unit cube,
     u = (G/2) y (1-y) e_x and p = G (1-x); Dirichlet u = exact on x=0 and the y, z faces,
     do-nothing outflow at x=1."""
@@ -338,7 +340,7 @@ def poiseuille(m=4, G=1.0, parts=(1, 1, 1), groups=None, levels=2):
     tags = boundary_tags(m, m, m, h, (0, 0, 0), mask, inflow=(0, 0), outflow=(0, 1), extent=None)
     tags = np.where(tags == TAG_WALL, TAG_INFLOW, tags).astype(np.uint8)
     p = Problem("poiseuille_%d" % m, m, m, m, h, (0.0, 0.0, 0.0), mask, tags,
-                np.zeros(((2 * m + 1) ** 3, 3)), "gradient", nu0=1.0, levels=levels)
+                np.zeros(((2 * m + 1) ** 3, 3)), "gradient", nu0=1.0, levels=levels, pressure=pressure)
     x = p.node_coords()
     p.g[:, 0] = 0.5 * G * x[:, 1] * (1 - x[:, 1])
     p.g[tags == TAG_OUTFLOW] = 0.0
@@ -451,7 +453,7 @@ def carreau_cube(m, n, nu_inf, seed, lam=1.0):
 
 
 def box_problem(nx, ny, nz, parts, groups=None, levels=2, form="gradient", bc="channel",
-                seed=1, uk_seed=None, nu0=1.0, nu_inf=0.0, lam=0.0, n=1.0):
+                seed=1, uk_seed=None, nu0=1.0, nu_inf=0.0, lam=0.0, n=1.0, pressure="q1"):
     """Small box problems for tests.  bc: "channel" (inflow x=0 with a parabolic profile,
     outflow x=1, walls elsewhere), "neumann" (every boundary node natural) or "cavity"
     (every boundary node a no-slip wall)."""
@@ -466,7 +468,7 @@ def box_problem(nx, ny, nz, parts, groups=None, levels=2, form="gradient", bc="c
     nn = (2 * nx + 1) * (2 * ny + 1) * (2 * nz + 1)
     p = Problem("box_%dx%dx%d_%s" % (nx, ny, nz, bc), nx, ny, nz, h, (0.0, 0.0, 0.0), mask, tags,
                 np.zeros((nn, 3)), form, nu0=nu0, nu_inf=nu_inf, lam=lam, n_carreau=n,
-                rhs_seed=seed, levels=levels)
+                rhs_seed=seed, levels=levels, pressure=pressure)
     x = p.node_coords()
     inl = tags == TAG_INFLOW
     ly, lz = ny * h, nz * h
