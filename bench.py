@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--workload", choices=["channel", "die", "mg"], default="channel",
                     help="channel: 32^3 Carreau channel (3 levels); die: 64x64x128 die-like channel (4 levels); "
                          "mg: geometric multigrid on the 64^3 Carreau cube with its 16^3 grid solved by 4-level GDSW")
+    ap.add_argument("--pressure", choices=["q1", "p1disc"], default="q1",
+                    help="channel workload: Q2/Q1 (default) or the Q2/P1-disc pair (two levels)")
+    ap.add_argument("--levels", type=int, default=0, help="channel workload: 2 = two-level GDSW (0 = the default 3)")
     ap.add_argument("--mg-m", type=int, default=64, help="elements per edge of the finest multigrid grid")
     ap.add_argument("--mg-smoother", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--mg-nu", type=int, default=3, help="pre- and post-smoothing steps")
@@ -481,9 +484,15 @@ def run_gdsw(args, rank, world, local):
         mixed = (args.mixed, "fp32", "fp32")
         wname = DIE_WORKLOAD
     else:
-        p = I.channel(args.m)
+        two = args.levels == 2 or args.pressure == "p1disc"
+        p = I.channel(args.m, groups=(), levels=2) if two else I.channel(args.m)
+        p.pressure = args.pressure
         mixed = (args.mixed, args.mixed, args.mixed)
         wname = WORKLOAD if args.m == 32 else WORKLOAD.replace("channel32", "channel%d" % args.m)
+        if two:
+            wname = wname.replace("_grouped2x2x2_3level", "_2level")
+        if args.pressure == "p1disc":
+            wname = wname.replace("q2q1", "q2p1disc")
     t0 = time.perf_counter()
     ctx = gdsw.Context(p, precision=mixed, phi_precision="fp32", tol=1e-8, restart=100, max_it=1000,
                        use_graph=bool(args.graph))
@@ -641,7 +650,8 @@ def run_gdsw(args, rank, world, local):
 
     peak, peak_kind = measured_peaks()
     ms_step = total_ms / args.steps
-    ratio = gemv_traffic_ratio(persistent) if (args.workload == "channel" and args.m == 32 and args.mixed == "fp32") else None
+    headline = args.workload == "channel" and args.m == 32 and args.pressure == "q1" and args.levels in (0, 3)
+    ratio = gemv_traffic_ratio(persistent) if (headline and args.mixed == "fp32") else None
     line = {
         "metric": METRIC,
         "value": ms_step,
@@ -701,7 +711,7 @@ def run_gdsw(args, rank, world, local):
         "serving": serving,
     }
     if rank == 0:
-        if world == 1 and os.environ.get("GDSW_BENCH_NO_CPU") != "1" and args.workload == "channel" and args.m == 32:
+        if world == 1 and os.environ.get("GDSW_BENCH_NO_CPU") != "1" and headline:
             ms, sample, cores = oracle_sample(p)
             line["cpu_baseline"] = {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
         else:

@@ -61,6 +61,11 @@ enum gdsw_precision { GDSW_FP64 = 0, GDSW_FP32 = 1, GDSW_BF16 = 2 };
  * the 3xTF32 split (AUTO, the default, for tasks of at least 96 x 96 outputs), or SIMT FMA. */
 enum gdsw_gemm_engine { GDSW_GEMM_AUTO = 0, GDSW_GEMM_SIMT = 1, GDSW_GEMM_TENSOR = 2 };
 enum gdsw_weighting { GDSW_WEIGHT_POU = 0, GDSW_WEIGHT_PLAIN = 1 };
+/* Pressure element: continuous Q1 (Taylor-Hood, one dof per even-index node) or the paper's
+ * discontinuous P1 (Section 2: four dofs per fluid element -- the coefficients of 1, xi, eta,
+ * zeta in the element's reference coordinates [-1, 1]^3 -- numbered 4 f + k after the velocity
+ * dofs, f the fluid element's rank in element order). */
+enum gdsw_pressure { GDSW_PRESSURE_Q1 = 0, GDSW_PRESSURE_P1DISC = 1 };
 
 typedef struct gdsw_ctx gdsw_ctx;
 
@@ -72,6 +77,10 @@ typedef struct {
   const uint8_t* mask;   /* host, nx*ny*nz; 1 = fluid element */
   const uint8_t* tags;   /* host, (2nx+1)(2ny+1)(2nz+1) node tags (enum gdsw_tag) */
   const double* g;       /* host, 3 per node: Dirichlet datum (read where tag is WALL/INFLOW) */
+  int32_t pressure;      /* a gdsw_pressure value; 0, the zero-initialised default, is Q1.
+                            P1-disc contexts take two levels (per-subdomain pressure coarse
+                            columns) and no multigrid hierarchy; anything else is
+                            GDSW_ERR_INVALID_ARG. */
 } gdsw_mesh;
 
 /* Viscosity (Section 2: constant mu; Section 3: Carreau law

@@ -198,6 +198,7 @@ struct MeshHost {
   std::vector<int32_t> vnode, pnode;// index -> node
   std::vector<uint8_t> active;
   int64_t nv = 0, np = 0, n = 0, nu = 0;
+  bool pdisc = false;                    // P1-disc pressure: rows 4 f + k per fluid element f
   // patterns
   std::vector<int32_t> a_ptr, a_col;     // velocity node rows x velocity node cols
   std::vector<int32_t> bt_ptr, bt_col;   // velocity node rows x pressure cols

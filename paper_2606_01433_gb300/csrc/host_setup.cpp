@@ -175,6 +175,86 @@ static void build_sell(MeshHost& M) {
   });
 }
 
+// The 27 Q2 nodes of element e, in local order a = x + 3 y + 9 z.
+static void element_nodes(const MeshHost& M, int64_t e, int64_t out[27]) {
+  const int ex = int(e % M.nx), ey = int((e / M.nx) % M.ny), ez = int(e / (int64_t(M.nx) * M.ny));
+  for (int c = 0; c < 3; ++c)
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a)
+        out[a + 3 * b + 9 * c] = (2 * ex + a) + int64_t(M.NX) * ((2 * ey + b) + int64_t(M.NY) * (2 * ez + c));
+}
+
+// P1-disc patterns (Section 2 element pair): pressure row 4 f + k couples to the free velocity
+// nodes of fluid element f (and, for the lifting, to its Dirichlet nodes with a nonzero datum);
+// velocity node I couples to the four pressure dofs of every fluid element holding it.  All
+// lists ascending (node order equals velocity-index order; fluid rank order equals element order).
+static void build_p1disc_patterns(MeshHost& M) {
+  const int64_t nf = int64_t(M.fluid.size());
+  std::vector<int32_t> rv(nf * 27), rn(nf * 27), dv(nf * 27), dn(nf * 27);
+  parallel_for(nf, [&](int64_t f) {
+    int64_t nd[27];
+    element_nodes(M, M.fluid[f], nd);
+    std::sort(nd, nd + 27);
+    int a = 0, b = 0;
+    for (int q = 0; q < 27; ++q) {
+      const int64_t v = nd[q];
+      if (M.vidx[v] >= 0) rv[f * 27 + a++] = M.vidx[v];
+      const uint8_t t = M.tags[v];
+      const bool nz = M.g[3 * v] != 0.0 || M.g[3 * v + 1] != 0.0 || M.g[3 * v + 2] != 0.0;
+      if ((t == GDSW_TAG_WALL || t == GDSW_TAG_INFLOW) && nz) dv[f * 27 + b++] = int32_t(v);
+    }
+    rn[f] = a;
+    dn[f] = b;
+  });
+  M.b_ptr.assign(4 * nf + 1, 0);
+  M.bd_ptr.assign(4 * nf + 1, 0);
+  for (int64_t f = 0; f < nf; ++f)
+    for (int k = 0; k < 4; ++k) {
+      M.b_ptr[4 * f + k + 1] = M.b_ptr[4 * f + k] + rn[f];
+      M.bd_ptr[4 * f + k + 1] = M.bd_ptr[4 * f + k] + dn[f];
+    }
+  M.b_col.resize(M.b_ptr[4 * nf]);
+  M.bd_col.resize(M.bd_ptr[4 * nf]);
+  parallel_for(nf, [&](int64_t f) {
+    for (int k = 0; k < 4; ++k) {
+      std::copy(rv.begin() + f * 27, rv.begin() + f * 27 + rn[f], M.b_col.begin() + M.b_ptr[4 * f + k]);
+      std::copy(dv.begin() + f * 27, dv.begin() + f * 27 + dn[f], M.bd_col.begin() + M.bd_ptr[4 * f + k]);
+    }
+  });
+  // velocity rows: the fluid elements holding the node, ascending
+  M.bt_ptr.assign(M.nv + 1, 0);
+  std::vector<int32_t> ecount(M.nv, 0);
+  parallel_for(M.nv, [&](int64_t I) {
+    int i, j, k, ei[2], ej[2], ek[2];
+    M.coords(M.vnode[I], i, j, k);
+    const int ni = elem_range(i, M.nx, ei), nj = elem_range(j, M.ny, ej), nk = elem_range(k, M.nz, ek);
+    int c = 0;
+    for (int z = 0; z < nk; ++z)
+      for (int y = 0; y < nj; ++y)
+        for (int x = 0; x < ni; ++x) c += M.felem[ei[x] + int64_t(M.nx) * (ej[y] + int64_t(M.ny) * ek[z])] >= 0;
+    ecount[I] = c;
+  });
+  for (int64_t I = 0; I < M.nv; ++I) M.bt_ptr[I + 1] = M.bt_ptr[I] + 4 * ecount[I];
+  M.bt_col.resize(M.bt_ptr[M.nv]);
+  parallel_for(M.nv, [&](int64_t I) {
+    int i, j, k, ei[2], ej[2], ek[2];
+    M.coords(M.vnode[I], i, j, k);
+    const int ni = elem_range(i, M.nx, ei), nj = elem_range(j, M.ny, ej), nk = elem_range(k, M.nz, ek);
+    int32_t fl[8];
+    int c = 0;
+    for (int z = 0; z < nk; ++z)
+      for (int y = 0; y < nj; ++y)
+        for (int x = 0; x < ni; ++x) {
+          const int32_t f = M.felem[ei[x] + int64_t(M.nx) * (ej[y] + int64_t(M.ny) * ek[z])];
+          if (f >= 0) fl[c++] = f;
+        }
+    std::sort(fl, fl + c);
+    int32_t* out = M.bt_col.data() + M.bt_ptr[I];
+    for (int q = 0; q < c; ++q)
+      for (int kk = 0; kk < 4; ++kk) out[4 * q + kk] = 4 * fl[q] + kk;
+  });
+}
+
 void build_mesh(MeshHost& M, const gdsw_mesh* m) {
   M.nx = m->nx; M.ny = m->ny; M.nz = m->nz;
   M.h = m->h;
@@ -201,6 +281,9 @@ void build_mesh(MeshHost& M, const gdsw_mesh* m) {
         for (int a = 0; a < 3; ++a)
           M.active[(2 * ex + a) + int64_t(M.NX) * ((2 * ey + b) + int64_t(M.NY) * (2 * ez + c))] = 1;
   }
+  GDSW_CHECK(m->pressure == GDSW_PRESSURE_Q1 || m->pressure == GDSW_PRESSURE_P1DISC, GDSW_ERR_INVALID_ARG,
+             "unknown pressure element");
+  M.pdisc = m->pressure == GDSW_PRESSURE_P1DISC;
   M.vidx.assign(M.nnodes, -1);
   M.pidx.assign(M.nnodes, -1);
   M.vnode.clear();
@@ -214,13 +297,13 @@ void build_mesh(MeshHost& M, const gdsw_mesh* m) {
     }
     int i, j, k;
     M.coords(v, i, j, k);
-    if (i % 2 == 0 && j % 2 == 0 && k % 2 == 0) {
+    if (!M.pdisc && i % 2 == 0 && j % 2 == 0 && k % 2 == 0) {
       M.pidx[v] = int32_t(M.pnode.size());
       M.pnode.push_back(int32_t(v));
     }
   }
   M.nv = int64_t(M.vnode.size());
-  M.np = int64_t(M.pnode.size());
+  M.np = M.pdisc ? 4 * int64_t(M.fluid.size()) : int64_t(M.pnode.size());
   M.nu = 3 * M.nv;
   M.n = M.nu + M.np;
   GDSW_CHECK(M.n < (int64_t(1) << 31), GDSW_ERR_INVALID_ARG, "problem too large for int32 dof indices");
@@ -263,6 +346,15 @@ void build_mesh(MeshHost& M, const gdsw_mesh* m) {
     std::vector<int32_t>* pp[3] = {&M.b_ptr, nullptr, &M.bd_ptr};
     std::vector<int32_t>* pc[3] = {&M.b_col, nullptr, &M.bd_col};
     build(M.pnode, pp, pc);
+  }
+  if (M.pdisc) {
+    // an element's pressure dofs travel with its centre node in the local orderings
+    for (int32_t e : M.fluid) {
+      int64_t nd[27];
+      element_nodes(M, e, nd);
+      GDSW_CHECK(M.vidx[nd[13]] >= 0, GDSW_ERR_INVALID_ARG, "P1-disc: an element centre node has no free velocity");
+    }
+    build_p1disc_patterns(M);
   }
   // symmetric velocity pattern: diagonal block of each row and the transpose of each block
   M.a_diag.assign(M.nv, -1);
@@ -385,10 +477,25 @@ void SlabSet::layout() {
   nvec = voff[nsub];
 }
 
+// P1-disc pressure dofs that an element adds to a dof set (they belong to no node).  high:
+// the dofs join the slab of the element's last node plane across the slab axis, else the slab
+// of its centre.  A set of whole elements (an overlapping subdomain, whose element constants
+// are free) needs `high`: a leading block of the block-tridiagonal factorisation then holds an
+// element's constant only together with every one of its velocity nodes, so the constant
+// pressure on the elements of the leading slabs is never a kernel of the leading block.  The
+// linear dofs of an interior set are controlled by the element's centre (bubble) node alone.
+struct ElemDofs {
+  int64_t e;
+  int n;
+  int32_t d[4];
+  bool high;
+};
+
 // Order the free dofs of a node set for a block-tridiagonal factorisation: slabs of
 // `t` element layers across the longest axis of the set (t = 0: one slab); inside each
 // slab the dofs of nodes coupled to the previous slab come first.  Appends to `S`.
-static void slab_order(const MeshHost& M, std::vector<int64_t> nodes, int t, SlabSet& S) {
+static void slab_order(const MeshHost& M, std::vector<int64_t> nodes, int t, SlabSet& S,
+                       const std::vector<ElemDofs>* edofs = nullptr) {
   std::sort(nodes.begin(), nodes.end());
   if (nodes.empty()) {
     S.K.push_back(0);
@@ -451,6 +558,34 @@ static void slab_order(const MeshHost& M, std::vector<int64_t> nodes, int t, Sla
     if (M.vidx[v] >= 0)
       for (int c = 0; c < 3; ++c) dst.push_back(int32_t(3 * M.vidx[v] + c));
     if (M.pidx[v] >= 0) dst.push_back(int32_t(M.nu + M.pidx[v]));
+  }
+  if (edofs) {
+    auto member = [&](int i, int j, int k) -> int32_t {
+      if (i < lo[0] || i > hi[0] || j < lo[1] || j > hi[1] || k < lo[2] || k > hi[2]) return -1;
+      return box[bidx(i, j, k)];
+    };
+    auto slab_of_raw = [&](int r) {
+      auto it = std::lower_bound(uniq.begin(), uniq.end(), r);
+      return (it != uniq.end() && *it == r) ? int(it - uniq.begin()) : -1;
+    };
+    for (const ElemDofs& x : *edofs) {
+      const int ec[3] = {int(x.e % M.nx), int((x.e / M.nx) % M.ny), int(x.e / (int64_t(M.nx) * M.ny))};
+      const int centre = 2 * ec[ax] + 1;
+      const int rc = t > 0 ? (centre - c0) / (2 * t) : 0;
+      int sl = -1;
+      if (x.high) sl = slab_of_raw(t > 0 ? (centre + 1 - c0) / (2 * t) : 0);
+      if (sl < 0) sl = slab_of_raw(rc);
+      GDSW_CHECK(sl >= 0, GDSW_ERR_INVALID_ARG, "element pressure dofs without their element's nodes");
+      bool bk = false;
+      for (int z = 0; z < 3 && !bk; ++z)
+        for (int y = 0; y < 3 && !bk; ++y)
+          for (int w = 0; w < 3 && !bk; ++w) {
+            const int32_t q = member(2 * ec[0] + w, 2 * ec[1] + y, 2 * ec[2] + z);
+            if (q >= 0 && slab[q] == sl - 1) bk = true;
+          }
+      auto& dst = bk ? A[sl] : B[sl];
+      for (int c = 0; c < x.n; ++c) dst.push_back(x.d[c]);
+    }
   }
   std::vector<int> s, m;
   for (int k = 0; k < K; ++k) {
@@ -623,6 +758,7 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
 
   // ---- overlapping subdomains (Section 2.1: k layers of elements) ----
   std::vector<std::vector<int64_t>> onodes(N);
+  std::vector<std::vector<int32_t>> oelems(N);   // P1-disc: fluid ranks whose pressure is kept
   parallel_tasks(N, [&](int64_t i) {
     int lo[3], hi[3], nn[3] = {M.nx, M.ny, M.nz};
     for (int d = 0; d < 3; ++d) {
@@ -658,13 +794,15 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
             if (any) em[lel(a, b, c)] = 1;
           }
     }
-    // nodes whose every fluid element lies in the overlapping subdomain
+    // nodes whose every fluid element lies in the overlapping subdomain (kn: also the nodes
+    // without a free dof, for the P1-disc rule on whole elements)
+    std::vector<uint8_t> kn(M.pdisc ? nm.size() : 0, 0);
     for (int c = 0; c < V[2]; ++c)
       for (int b = 0; b < V[1]; ++b)
         for (int a = 0; a < V[0]; ++a) {
           int gi = 2 * lo[0] + a, gj = 2 * lo[1] + b, gk = 2 * lo[2] + c;
           int64_t v = gi + int64_t(M.NX) * (gj + int64_t(M.NY) * gk);
-          if (!M.active[v] || !has_free(v)) continue;
+          if (!M.active[v] || (!M.pdisc && !has_free(v))) continue;
           int ei[2], ej[2], ek[2];
           int ni = elem_range(gi, M.nx, ei), nj = elem_range(gj, M.ny, ej), nk = elem_range(gk, M.nz, ek);
           bool all = true;
@@ -677,12 +815,36 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
                 if (la < 0 || lb < 0 || lc < 0 || la >= E[0] || lb >= E[1] || lc >= E[2] || !em[lel(la, lb, lc)])
                   all = false;
               }
-          if (all) onodes[i].push_back(v);
+          if (all && M.pdisc) kn[lnd(a, b, c)] = 1;
+          if (all && has_free(v)) onodes[i].push_back(v);
         }
+    // P1-disc: the pressure dofs of the elements of Omega_i' none of whose nodes lies on its
+    // artificial rim (with Dirichlet velocity there the constant pressure on all of Omega_i'
+    // would be a kernel of A_i)
+    if (M.pdisc)
+      for (int c = 0; c < E[2]; ++c)
+        for (int b = 0; b < E[1]; ++b)
+          for (int a = 0; a < E[0]; ++a) {
+            const int64_t e = gel(a, b, c);
+            if (!em[lel(a, b, c)] || !M.mask[e]) continue;
+            bool all = true;
+            for (int z = 0; z < 3 && all; ++z)
+              for (int y = 0; y < 3 && all; ++y)
+                for (int x = 0; x < 3 && all; ++x) all = kn[lnd(2 * a + x, 2 * b + y, 2 * c + z)] != 0;
+            if (all) oelems[i].push_back(M.felem[e]);
+          }
   });
   {
     std::vector<SlabSet> parts(N);
-    parallel_tasks(N, [&](int64_t i) { slab_order(M, onodes[i], slab_elems, parts[i]); });
+    parallel_tasks(N, [&](int64_t i) {
+      std::vector<ElemDofs> ed;
+      for (int32_t f : oelems[i]) {
+        ElemDofs x{M.fluid[f], 4, {}, true};
+        for (int k = 0; k < 4; ++k) x.d[k] = int32_t(M.nu + 4 * int64_t(f) + k);
+        ed.push_back(x);
+      }
+      slab_order(M, onodes[i], slab_elems, parts[i], M.pdisc ? &ed : nullptr);
+    });
     SlabSet& S = L.loc;
     S = SlabSet();
     for (int i = 0; i < N; ++i) {
@@ -804,6 +966,18 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
     C.cn_dofs.push_back(dofs);
     C.cn_modes.push_back(modes);
   }
+  // P1-disc: no pressure dof lies on the interface, so the pressure null space enters as one
+  // column per subdomain, the constant pressure on the subdomain's own elements (prescribed
+  // through the element constants, which join Gamma); none with a single subdomain
+  const int n_ent_cols = n0;
+  const bool pcols = M.pdisc && N >= 2;
+  if (pcols)
+    for (int i = 0; i < N; ++i) {
+      C.cn_set.push_back({i});
+      C.cn_dofs.push_back({n0});
+      C.cn_modes.push_back({3});
+      ++n0;
+    }
   C.n0 = n0;
   C.gdofs.clear();
   C.gcol.clear();
@@ -820,6 +994,9 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
           }
         if (M.pidx[v] >= 0) gl.push_back({int32_t(M.nu + M.pidx[v]), ecol[e][3], 1.0});
       }
+    if (pcols)
+      for (int64_t f = 0; f < int64_t(M.fluid.size()); ++f)
+        gl.push_back({int32_t(M.nu + 4 * f), int32_t(n_ent_cols + ep[M.fluid[f]]), 1.0});
     std::sort(gl.begin(), gl.end(), [](const GE& a, const GE& b) { return a.dof != b.dof ? a.dof < b.dof : a.col < b.col; });
     C.gval.clear();
     for (auto& q : gl) {
@@ -834,7 +1011,16 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
     if (M.active[v] && nsh[v] == 1 && has_free(v)) inodes[sh[v][0]].push_back(v);
   {
     std::vector<SlabSet> parts(N);
-    parallel_tasks(N, [&](int64_t i) { slab_order(M, inodes[i], slab_elems, parts[i]); });
+    // P1-disc: the pressure dofs of each subdomain's own elements that are not in Gamma (the
+    // linear ones; all four with a single subdomain)
+    std::vector<std::vector<ElemDofs>> ied(N);
+    if (M.pdisc)
+      for (int64_t f = 0; f < int64_t(M.fluid.size()); ++f) {
+        ElemDofs x{M.fluid[f], 0, {}, false};
+        for (int k = pcols ? 1 : 0; k < 4; ++k) x.d[x.n++] = int32_t(M.nu + 4 * f + k);
+        ied[ep[M.fluid[f]]].push_back(x);
+      }
+    parallel_tasks(N, [&](int64_t i) { slab_order(M, inodes[i], slab_elems, parts[i], M.pdisc ? &ied[i] : nullptr); });
     SlabSet& S = L.inter;
     S = SlabSet();
     for (int i = 0; i < N; ++i) {
@@ -847,8 +1033,10 @@ void build_level1(gdsw_ctx* ctx, const gdsw_partition* part, int overlap, int sl
     C.idofs = S.gdof;
     C.ioff = S.voff;
   }
-  std::vector<std::vector<int>> eset(ents.size());
-  for (size_t e = 0; e < ents.size(); ++e) eset[e] = C.cn_set[e];
+  std::vector<std::vector<int>> eset(C.cn_set.size());
+  for (size_t e = 0; e < C.cn_set.size(); ++e) eset[e] = C.cn_set[e];
+  ent_cols.resize(C.cn_set.size());
+  for (size_t e = ents.size(); e < C.cn_set.size(); ++e) ent_cols[e] = C.cn_dofs[e];
   coarse_lists(C, eset, ent_cols);
 }
 

@@ -24,6 +24,7 @@ struct InvTaskP {
 struct RefTables {
   double dphi[27][27][3];   // [q][a][l]
   double psi[27][8];        // [q][P]
+  double p1[27][4];         // [q][k]: P1-disc basis 1, xi, eta, zeta
   double w[27];
 };
 void host_tables(RefTables& T);

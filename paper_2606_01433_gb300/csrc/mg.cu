@@ -540,6 +540,7 @@ static void mg_create(gdsw_mg* mg, gdsw_ctx* const* grids, int ngrids, const gds
     GDSW_CHECK((l + 1 == ngrids) == (c->L >= 2), GDSW_ERR_INVALID_ARG,
                "fine grids must be operator-only contexts (levels = 1), the coarsest a GDSW context");
     GDSW_CHECK(!c->ext_precond, GDSW_ERR_INVALID_ARG, "grid context already has a multigrid attached");
+    GDSW_CHECK(!c->mesh.pdisc, GDSW_ERR_INVALID_ARG, "the multigrid transfers are defined for Q1 pressure");
   }
   cudaStream_t s = mg->s;
   mg->arena.stream = s;

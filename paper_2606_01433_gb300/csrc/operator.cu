@@ -23,6 +23,10 @@ void host_tables(RefTables& T) {
         int q = qx + 3 * qy + 9 * qz;
         double x = gx[qx], y = gx[qy], z = gx[qz];
         T.w[q] = gw[qx] * gw[qy] * gw[qz];
+        T.p1[q][0] = 1.0;
+        T.p1[q][1] = x;
+        T.p1[q][2] = y;
+        T.p1[q][3] = z;
         for (int az = 0; az < 3; ++az)
           for (int ay = 0; ay < 3; ++ay)
             for (int ax = 0; ax < 3; ++ax) {
@@ -180,6 +184,27 @@ __device__ void divergence_entry(int64_t P, int64_t J, const Geo& G, const uint8
       }
 }
 
+// The same entry for the P1-disc pressure (Section 2's element pair): row P = 4 f + k is the
+// k-th basis function (1, xi, eta, zeta) of fluid element f, which alone carries it.
+__device__ void divergence_entry_p1(int64_t P, int64_t J, const Geo& G, const int32_t* fluid, const RefTables* T,
+                                    double out[3]) {
+  const int64_t e = fluid[P >> 2];
+  const int k = int(P & 3);
+  const int ex = int(e % G.nx), ey = int((e / G.nx) % G.ny), ez = int(e / (int64_t(G.nx) * G.ny));
+  int ji, jj, jk;
+  node_ijk(J, G, ji, jj, jk);
+  const int b = (ji - 2 * ex) + 3 * (jj - 2 * ey) + 9 * (jk - 2 * ez);
+  const double sc = 0.25 * G.h * G.h;
+  out[0] = out[1] = out[2] = 0.0;
+  for (int q = 0; q < 27; ++q) {
+    const double f = -T->w[q] * sc * T->p1[q][k];
+    const double* db = T->dphi[q][b];
+    out[0] = fma(f, db[0], out[0]);
+    out[1] = fma(f, db[1], out[1]);
+    out[2] = fma(f, db[2], out[2]);
+  }
+}
+
 // ------------------------------------------------------------------ a2: assembly
 // On GB300 a warp-wide FP64 instruction holds the FP64 pipe for the same time whether 1 or 32
 // lanes are active, so the assembly is organised for uniform lanes: one thread per work unit
@@ -301,15 +326,20 @@ __global__ void __launch_bounds__(256) k_assemble_A(const int32_t* __restrict__ 
   }
 }
 
+// pfluid != nullptr: P1-disc rows (fluid element list), else Q1 rows (pressure node list)
 __global__ void k_assemble_B(const int32_t* __restrict__ b_ptr, const int32_t* __restrict__ b_col,
-                             const int32_t* __restrict__ pnode, const int32_t* __restrict__ vnode, int64_t np, Geo G,
-                             const uint8_t* mask, const RefTables* T, double* __restrict__ bval) {
+                             const int32_t* __restrict__ pnode, const int32_t* __restrict__ pfluid,
+                             const int32_t* __restrict__ vnode, int64_t np, Geo G, const uint8_t* mask,
+                             const RefTables* T, double* __restrict__ bval) {
   int64_t P = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (P >= np) return;
   for (int e = b_ptr[P] + lane; e < b_ptr[P + 1]; e += 32) {
     double out[3];
-    divergence_entry(pnode[P], vnode[b_col[e]], G, mask, T, out);
+    if (pfluid)
+      divergence_entry_p1(P, vnode[b_col[e]], G, pfluid, T, out);
+    else
+      divergence_entry(pnode[P], vnode[b_col[e]], G, mask, T, out);
     bval[int64_t(e) * 3 + 0] = out[0];
     bval[int64_t(e) * 3 + 1] = out[1];
     bval[int64_t(e) * 3 + 2] = out[2];
@@ -332,9 +362,9 @@ __global__ void k_copy_bt(const int32_t* __restrict__ bt2b, int64_t nbt, const d
 __global__ void __launch_bounds__(256) k_lift(const int32_t* __restrict__ rows, int64_t nrows,
                                               const int32_t* ad_ptr, const int32_t* ad_col, const int32_t* vnode,
                                               int64_t nv, const int32_t* bd_ptr, const int32_t* bd_col,
-                                              const int32_t* pnode, Geo G, const uint8_t* mask,
-                                              const int32_t* felem, const double* nu, const RefTables* T, int form,
-                                              const double* g, double* b) {
+                                              const int32_t* pnode, const int32_t* pfluid, Geo G,
+                                              const uint8_t* mask, const int32_t* felem, const double* nu,
+                                              const RefTables* T, int form, const double* g, double* b) {
   const int64_t w = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (w >= nrows) return;
@@ -361,7 +391,10 @@ __global__ void __launch_bounds__(256) k_lift(const int32_t* __restrict__ rows, 
     for (int e = bd_ptr[P] + lane; e < bd_ptr[P + 1]; e += 32) {
       int64_t J = bd_col[e];
       double v[3];
-      divergence_entry(pnode[P], J, G, mask, T, v);
+      if (pfluid)
+        divergence_entry_p1(P, J, G, pfluid, T, v);
+      else
+        divergence_entry(pnode[P], J, G, mask, T, v);
       acc = fma(v[0], g[3 * J], fma(v[1], g[3 * J + 1], fma(v[2], g[3 * J + 2], acc)));
     }
 #pragma unroll
@@ -561,7 +594,8 @@ void launch_assembly(gdsw_ctx* c, cudaStream_t s, bool newton) {
     launch_sell_fill(c, false, s);
     return;
   }
-  k_assemble_B<<<int((np + 7) / 8), 256, 0, s>>>(c->d_b_ptr, c->d_b_col, c->d_pnode, c->d_vnode, np, geo(c),
+  k_assemble_B<<<int((np + 7) / 8), 256, 0, s>>>(c->d_b_ptr, c->d_b_col, c->d_pnode,
+                                                 c->mesh.pdisc ? c->d_fluid : nullptr, c->d_vnode, np, geo(c),
                                                  c->d_mask, T, bval);
   check_launch("k_assemble_B");
   if (c->nbt > 0) {
@@ -578,7 +612,8 @@ void launch_lift(gdsw_ctx* c, double* b, cudaStream_t s) {
   GDSW_CUDA(cudaMemsetAsync(b, 0, size_t(3 * nv + np) * sizeof(double), s));
   if (c->n_lift_rows == 0) return;
   k_lift<<<int((c->n_lift_rows + 7) / 8), 256, 0, s>>>(c->d_lift_rows, c->n_lift_rows, c->d_ad_ptr, c->d_ad_col,
-                                                       c->d_vnode, nv, c->d_bd_ptr, c->d_bd_col, c->d_pnode, geo(c),
+                                                       c->d_vnode, nv, c->d_bd_ptr, c->d_bd_col, c->d_pnode,
+                                                       c->mesh.pdisc ? c->d_fluid : nullptr, geo(c),
                                                        c->d_mask, c->d_felem, c->d_nu,
                                                        static_cast<RefTables*>(c->d_tables), c->form, c->d_gdir, b);
   check_launch("k_lift");

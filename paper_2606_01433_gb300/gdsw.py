@@ -33,7 +33,11 @@ class GdswError(RuntimeError):
 
 class gdsw_mesh(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double),
-                ("origin", C.c_double * 3), ("mask", C.c_void_p), ("tags", C.c_void_p), ("g", C.c_void_p)]
+                ("origin", C.c_double * 3), ("mask", C.c_void_p), ("tags", C.c_void_p), ("g", C.c_void_p),
+                ("pressure", C.c_int32)]
+
+
+PRESSURE = {"q1": 0, "p1disc": 1}
 
 
 class gdsw_viscosity(C.Structure):
@@ -227,7 +231,7 @@ class Context:
         part = _np(prob.part, np.int32)
         self._keep += [mask, tags, g, part]
         m = gdsw_mesh(prob.nx, prob.ny, prob.nz, prob.h, (C.c_double * 3)(*prob.origin),
-                      mask.ctypes.data, tags.ctypes.data, g.ctypes.data)
+                      mask.ctypes.data, tags.ctypes.data, g.ctypes.data, PRESSURE[prob.pressure])
         uk = None
         if prob.uk is not None:
             uk = _np(prob.uk, np.float64)
@@ -486,7 +490,7 @@ class Server:
                 np.ascontiguousarray(prob.g, np.float64), np.ascontiguousarray(prob.part, np.int32)]
         r = gdsw_request()
         r.mesh = gdsw_mesh(prob.nx, prob.ny, prob.nz, prob.h, (C.c_double * 3)(*prob.origin),
-                           keep[0].ctypes.data, keep[1].ctypes.data, keep[2].ctypes.data)
+                           keep[0].ctypes.data, keep[1].ctypes.data, keep[2].ctypes.data, PRESSURE[prob.pressure])
         uk = None
         if prob.uk is not None:
             uk = np.ascontiguousarray(prob.uk, np.float64)

@@ -24,12 +24,21 @@ def test_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def _p1disc(p):
+    p.pressure = "p1disc"
+    return p
+
+
 CASES = [
     ("cube8_2x2x2", lambda: I.unit_cube(8)),
     ("box_3lvl", lambda: I.box_problem(4, 4, 4, (2, 2, 2), groups=((2, 2, 1),), levels=3)),
     ("box_4lvl", lambda: I.box_problem(4, 4, 2, (4, 4, 2), groups=((2, 2, 1), (2, 1, 1)), levels=4)),
     ("channel16_obstacles", lambda: I.channel(16, parts=(4, 4, 4), groups=((2, 2, 2),), levels=3)),
     ("die_rcb", lambda: I.die(16, 16, 32, nparts=16, per_group=4, levels=3)),
+    # Q2 / P1-disc (two levels): element pressure sets and per-subdomain pressure columns
+    ("cube6_p1disc", lambda: _p1disc(I.unit_cube(6, parts=(2, 2, 2)))),
+    ("channel12_p1disc", lambda: _p1disc(I.channel(12, parts=(3, 3, 3), groups=(), levels=2))),
+    ("die_rcb_p1disc", lambda: _p1disc(I.die(16, 16, 32, nparts=16, per_group=4, levels=2))),
 ]
 
 
