@@ -537,40 +537,43 @@ static void upload_coarse_space(gdsw_ctx* c, int l, int phi_prec) {
   L.gu_ptr = c->arena.upload(C.gu_ptr, s);
   L.ngu = int64_t(C.gu_dof.size());
   // PhiT layout: part J stores c_J rows of length pad8(n_IJ)
+  // 256-dof tiles of every part's interior, shared by the prolongation and the restriction
   std::vector<ProMeta> meta(C.nparts);
-  std::vector<GemvTask> tasks;
-  std::vector<GemvTile> tiles;
-  std::vector<int32_t> tp, tc;
+  std::vector<int32_t> tp, tc, tr, pnt(C.nparts, 0), qcnt(C.cols.size(), 0);
+  std::vector<int64_t> poff(C.nparts + 1, 0), qst(C.cols.size(), 0);
   int64_t off = 0;
   L.max_c = 1;
-  L.max_ld_phi = 8;
   for (int J = 0; J < C.nparts; ++J) {
     int cJ = int(C.coff[J + 1] - C.coff[J]);
     int nI = int(C.ioff[J + 1] - C.ioff[J]);
     int ld = int(pad8(std::max(nI, 1)));
     meta[J] = {off, C.ioff[J], C.coff[J], ld, nI, cJ, 0};
-    if (cJ > 0 && nI > 0) {
-      add_task(tasks, tiles, GemvTask{off, C.ioff[J], C.coff[J], -1, cJ, nI, ld, 1.0f}, L.phi_plan.rows_per_tile);
+    if (cJ > 0 && nI > 0)
       for (int col0 = 0; col0 < nI; col0 += 256) {
         tp.push_back(J);
         tc.push_back(col0);
+        tr.push_back(pnt[J]++);
       }
-      L.max_ld_phi = std::max(L.max_ld_phi, ld);
+    poff[J + 1] = poff[J] + int64_t(cJ) * pnt[J];
+    for (int j = 0; j < cJ; ++j) {
+      qst[C.coff[J] + j] = poff[J] + int64_t(j) * pnt[J];
+      qcnt[C.coff[J] + j] = pnt[J];
     }
     L.max_c = std::max(L.max_c, cJ);
     off += int64_t(cJ) * ld;
   }
-  L.phi_plan.launch_task_off = {0, int(tasks.size())};
-  L.phi_plan.launch_tile_off = {0, int(tiles.size())};
-  finish_plan(c->arena, L.phi_plan, tasks, tiles, s);
   L.pro_meta = reinterpret_cast<int64_t*>(c->arena.upload(meta, s));
   L.pro_tile_part = c->arena.upload(tp, s);
   L.pro_tile_col0 = c->arena.upload(tc, s);
+  L.pro_tile_rank = c->arena.upload(tr, s);
   L.n_pro_tiles = int(tp.size());
+  L.part_poff = c->arena.upload(poff, s);
+  L.part_ntiles = c->arena.upload(pnt, s);
+  L.q_start = c->arena.upload(qst, s);
+  L.q_count = c->arena.upload(qcnt, s);
+  L.partial = c->arena.alloc<double>(size_t(std::max<int64_t>(poff[C.nparts], 1)));
   L.phiT = c->arena.alloc<char>(size_t(std::max<int64_t>(off, 1)) * elem_size(phi_prec));
   GDSW_CUDA(cudaMemsetAsync(L.phiT, 0, size_t(std::max<int64_t>(off, 1)) * elem_size(phi_prec), s));
-  L.rI = c->arena.alloc<char>(size_t(std::max<int64_t>(L.nidofs, 1)) * elem_size(phi_prec));
-  L.yc = c->arena.alloc<char>(size_t(std::max<int64_t>(L.ncols, 1)) * elem_size(phi_prec));
   L.r0 = c->arena.alloc<double>(C.n0);
   L.x0 = c->arena.alloc<double>(C.n0);
 }
@@ -1072,16 +1075,7 @@ static void restrict_level(gdsw_ctx* c, int l, const double* r, double* r0, cuda
   LevelDev& L = c->ld[l];
   if (L.n0 == 0) return;
   ProfScope ps(c, l == 0 ? GDSW_K_RESTRICT : GDSW_K_COARSE, double(L.phi_bytes) + 16.0 * L.nidofs, s);
-  if (L.phi_prec == GDSW_FP64) {
-    launch_gather<double>(r, L.idofs, static_cast<double*>(L.rI), L.nidofs, s);
-    launch_gemv<double, double>(static_cast<const double*>(L.phiT), static_cast<const double*>(L.rI),
-                                static_cast<double*>(L.yc), nullptr, L.phi_plan, 0, L.max_ld_phi, s);
-  } else {
-    launch_gather<float>(r, L.idofs, static_cast<float*>(L.rI), L.nidofs, s);
-    launch_gemv<float, float>(static_cast<const float*>(L.phiT), static_cast<const float*>(L.rI),
-                              static_cast<float*>(L.yc), nullptr, L.phi_plan, 0, L.max_ld_phi, s);
-  }
-  launch_restrict_reduce(L.yc, L.phi_prec, r, L.rr_ptr, L.rr_pos, L.rg_ptr, L.rg_dof, L.rg_val, r0, L.n0, s);
+  launch_restrict(L, r, r0, s);
 }
 
 static void coarsest_solve(gdsw_ctx* c, const double* r0, double* x0, cudaStream_t s) {
@@ -1112,8 +1106,14 @@ static void apply_level(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
     GDSW_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
   }
   if (coarse) {
-    ProfScope ps(c, l == 0 ? GDSW_K_PROLONG : GDSW_K_COARSE, double(L.phi_bytes) + 16.0 * L.nidofs, s);
-    launch_prolong(L, L.x0, z, s);
+    {  // interior part z_I += Phi_I x0 (k_prolong): the basis once plus the read-modify-write of z_I
+      ProfScope ps(c, l == 0 ? GDSW_K_PROLONG : GDSW_K_COARSE, double(L.phi_bytes) + 16.0 * L.nidofs, s);
+      launch_prolong(L, L.x0, z, s);
+    }
+    {  // interface part z_G += Phi_G x0: per entry column and value, per dof its index and z
+      ProfScope ps(c, l == 0 ? GDSW_K_OTHER : GDSW_K_COARSE, 12.0 * L.ngamma + 24.0 * L.ngu, s);
+      launch_axpy_gamma(L.gu_dof, L.gu_ptr, L.gcol, L.gval, L.ngu, L.x0, z, s);
+    }
   }
 }
 
@@ -1682,7 +1682,11 @@ int gdsw_restrict(gdsw_ctx* c, int32_t level, const double* r, double* r0) {
 
 int gdsw_prolong(gdsw_ctx* c, int32_t level, const double* x0, double* z) {
   if (!c || c->host_only || level < 0 || level >= int(c->ld.size()) || !x0 || !z) return GDSW_ERR_INVALID_ARG;
-  GDSW_TRY(c, launch_prolong(c->ld[level], x0, z, c->stream));
+  GDSW_TRY(c, {
+    const LevelDev& L = c->ld[level];
+    launch_prolong(L, x0, z, c->stream);
+    if (L.n0 > 0) launch_axpy_gamma(L.gu_dof, L.gu_ptr, L.gcol, L.gval, L.ngu, x0, z, c->stream);
+  });
 }
 
 int gdsw_coarse_matrix(gdsw_ctx* c, int32_t l, double* host) {

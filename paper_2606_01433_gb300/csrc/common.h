@@ -276,14 +276,16 @@ struct LevelDev {
   double* rg_val = nullptr;
   int64_t nidofs = 0, ncols = 0, ngamma = 0, ngu = 0;
   void* phiT = nullptr;         // concatenated Phi_I^T blocks
-  void* rI = nullptr;           // gathered interior residual (phi precision)
-  void* yc = nullptr;           // per-part restricted values (phi precision)
-  GemvPlan phi_plan;            // y_J = PhiT_J rI_J
+  // restriction partials: per (part J, row j) the nt_J tile partials at part_poff[J] + j nt_J + t;
+  // per cols entry q (row j of part J) the start and count of its partials
+  double* partial = nullptr;
+  int64_t *part_poff = nullptr, *q_start = nullptr;
+  int32_t *part_ntiles = nullptr, *q_count = nullptr, *pro_tile_rank = nullptr;
   int32_t *pro_part = nullptr;  // per prolongation tile: part
   int64_t* pro_meta = nullptr;  // per part: phiT offset, ld, idofs offset, n_I, cols offset, c
   int n_pro_tiles = 0;
   int max_c = 0;
-  int max_ld_fwd = 0, max_ld_phi = 0;
+  int max_ld_fwd = 0;
   std::vector<int> fwd_ld, bwd_ld;  // largest input length per launch
   int32_t *pro_tile_part = nullptr, *pro_tile_col0 = nullptr;
   int32_t *rr_ptr = nullptr, *rr_pos = nullptr, *rg_ptr = nullptr, *rg_dof = nullptr;

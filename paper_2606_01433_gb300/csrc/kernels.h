@@ -83,9 +83,7 @@ void launch_gather(const double* r, const int32_t* idx, TV* out, int64_t n, cuda
 template <typename TV>
 void launch_scatter(const TV* x, const int32_t* ptr, const int32_t* pos, const double* w, double* z, int n,
                     int accumulate, cudaStream_t s);
-void launch_restrict_reduce(const void* yc, int prec, const double* r, const int32_t* rr_ptr, const int32_t* rr_pos,
-                            const int32_t* rg_ptr, const int32_t* rg_dof, const double* rg_val, double* r0, int n0,
-                            cudaStream_t s);
+void launch_restrict(const LevelDev& L, const double* r, double* r0, cudaStream_t s);
 void launch_prolong(const LevelDev& L, const double* x0, double* z, cudaStream_t s);
 void launch_axpy_gamma(const int32_t* gu_dof, const int32_t* gu_ptr, const int32_t* gcol, const double* gval,
                        int64_t ngu, const double* x0, double* z, cudaStream_t s);

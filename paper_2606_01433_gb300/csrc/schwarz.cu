@@ -49,11 +49,80 @@ template void launch_scatter<double>(const double*, const int32_t*, const int32_
 template void launch_scatter<float>(const float*, const int32_t*, const int32_t*, const double*, double*, int, int,
                                     cudaStream_t);
 
-// r0[k] = sum over parts of (Phi_I,J^T r_I,J)[k] + sum of r over the interface dofs of
-// column k (Phi_Gamma is the entity indicator).  One warp per coarse dof; lane-strided
-// partial sums and a fixed butterfly make the order deterministic.
+// Restriction r0 = Phi^T r in two deterministic passes over the stored Phi_I^T blocks.
+// Pass 1 (k_restrict_tiles): one CTA per 256-dof tile of a part's interior (the prolongation's
+// tiles); the tile's residual entries are gathered once into shared memory (in the basis
+// precision), and each warp takes rows j = warp, warp + 8, ... of PhiT_J, every lane streaming
+// eight coalesced entries of a row segment, so the basis is read exactly once with sixteen
+// loads in flight per lane.  A lane's eight products are summed in the basis precision, the
+// warp's 32 lane sums in FP64 by a fixed butterfly; the tile's partial of row j is stored.
+// Pass 2 (k_restrict_reduce): one warp per coarse column k adds, for each (part, row) that
+// carries k, that row's tile partials in tile order, then the Phi_Gamma entries of k.
 template <typename TP>
-__global__ void k_restrict_reduce(const TP* __restrict__ yc, const double* __restrict__ r,
+struct ProAcc {
+  using X = double;
+};
+template <>
+struct ProAcc<float> {
+  using X = float;
+};
+
+template <typename TP>
+__global__ void __launch_bounds__(256) k_restrict_tiles(const TP* __restrict__ phiT, const ProMeta* __restrict__ meta,
+                                                        const int32_t* __restrict__ tile_part,
+                                                        const int32_t* __restrict__ tile_col0,
+                                                        const int32_t* __restrict__ tile_rank,
+                                                        const int64_t* __restrict__ part_poff,
+                                                        const int32_t* __restrict__ part_ntiles,
+                                                        const int32_t* __restrict__ idofs,
+                                                        const double* __restrict__ r, double* __restrict__ partial) {
+  using X = typename ProAcc<TP>::X;
+  __shared__ X rs[256];
+  const int J = tile_part[blockIdx.x];
+  const ProMeta m = meta[J];
+  const int col0 = tile_col0[blockIdx.x];
+  const int l = col0 + int(threadIdx.x);
+  rs[threadIdx.x] = l < m.nI ? X(r[idofs[m.ioff + l]]) : X(0);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int span = min(256, m.ld - col0);   // stored row length left in this tile (pad entries are zero)
+  const int64_t pbase = part_poff[J] + tile_rank[blockIdx.x];
+  const int nt = part_ntiles[J];
+  for (int j = warp; j < m.c; j += 16) {
+    const int j2 = j + 8;
+    const TP* a = phiT + m.phi + int64_t(j) * m.ld + col0;
+    const TP* b = phiT + m.phi + int64_t(j2) * m.ld + col0;
+    TP va[8], vb[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = lane + 32 * u;
+      va[u] = t < span ? __ldcs(a + t) : TP(0);
+      vb[u] = (t < span && j2 < m.c) ? __ldcs(b + t) : TP(0);
+    }
+    X sa = X(0), sb = X(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      sa = fma(X(va[u]), rs[lane + 32 * u], sa);
+      sb = fma(X(vb[u]), rs[lane + 32 * u], sb);
+    }
+    double da = double(sa), db = double(sb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      da += __shfl_xor_sync(0xffffffffu, da, o);
+      db += __shfl_xor_sync(0xffffffffu, db, o);
+    }
+    if (lane == 0) {
+      partial[pbase + int64_t(j) * nt] = da;
+      if (j2 < m.c) partial[pbase + int64_t(j2) * nt] = db;
+    }
+  }
+}
+
+// r0[k] = sum over the (part, row) entries q of column k of the row's tile partials
+// (partial[q_start[q] .. + q_count[q]], in tile order) + sum of the Phi_Gamma entries of k
+// times r.  One warp per coarse dof; lane-strided partial sums and a fixed butterfly.
+__global__ void k_restrict_reduce(const double* __restrict__ partial, const int64_t* __restrict__ q_start,
+                                  const int32_t* __restrict__ q_count, const double* __restrict__ r,
                                   const int32_t* __restrict__ rr_ptr, const int32_t* __restrict__ rr_pos,
                                   const int32_t* __restrict__ rg_ptr, const int32_t* __restrict__ rg_dof,
                                   const double* __restrict__ rg_val, double* __restrict__ r0, int n0) {
@@ -61,24 +130,35 @@ __global__ void k_restrict_reduce(const TP* __restrict__ yc, const double* __res
   int lane = threadIdx.x & 31;
   if (k >= n0) return;
   double acc = 0.0;
-  for (int e = rr_ptr[k] + lane; e < rr_ptr[k + 1]; e += 32) acc += double(yc[rr_pos[e]]);
+  for (int e = rr_ptr[k] + lane; e < rr_ptr[k + 1]; e += 32) {
+    const int q = rr_pos[e];
+    const double* p = partial + q_start[q];
+    double t = 0.0;
+    for (int i = 0; i < q_count[q]; ++i) t += p[i];
+    acc += t;
+  }
   for (int e = rg_ptr[k] + lane; e < rg_ptr[k + 1]; e += 32) acc = fma(rg_val[e], r[rg_dof[e]], acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) r0[k] = acc;
 }
 
-void launch_restrict_reduce(const void* yc, int prec, const double* r, const int32_t* rr_ptr, const int32_t* rr_pos,
-                            const int32_t* rg_ptr, const int32_t* rg_dof, const double* rg_val, double* r0, int n0,
-                            cudaStream_t s) {
-  if (n0 == 0) return;
-  int blocks = (n0 + 7) / 8;
-  if (prec == GDSW_FP64)
-    k_restrict_reduce<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(yc), r, rr_ptr, rr_pos, rg_ptr, rg_dof,
-                                                     rg_val, r0, n0);
-  else
-    k_restrict_reduce<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(yc), r, rr_ptr, rr_pos, rg_ptr, rg_dof,
-                                                    rg_val, r0, n0);
+void launch_restrict(const LevelDev& L, const double* r, double* r0, cudaStream_t s) {
+  if (L.n0 == 0) return;
+  const ProMeta* meta = reinterpret_cast<const ProMeta*>(L.pro_meta);
+  if (L.n_pro_tiles > 0) {
+    if (L.phi_prec == GDSW_FP64)
+      k_restrict_tiles<double><<<L.n_pro_tiles, 256, 0, s>>>(static_cast<const double*>(L.phiT), meta,
+                                                             L.pro_tile_part, L.pro_tile_col0, L.pro_tile_rank,
+                                                             L.part_poff, L.part_ntiles, L.idofs, r, L.partial);
+    else
+      k_restrict_tiles<float><<<L.n_pro_tiles, 256, 0, s>>>(static_cast<const float*>(L.phiT), meta,
+                                                            L.pro_tile_part, L.pro_tile_col0, L.pro_tile_rank,
+                                                            L.part_poff, L.part_ntiles, L.idofs, r, L.partial);
+    check_launch("k_restrict_tiles");
+  }
+  k_restrict_reduce<<<(L.n0 + 7) / 8, 256, 0, s>>>(L.partial, L.q_start, L.q_count, r, L.rr_ptr, L.rr_pos,
+                                                   L.rg_ptr, L.rg_dof, L.rg_val, r0, L.n0);
   check_launch("k_restrict_reduce");
 }
 
@@ -89,15 +169,6 @@ void launch_restrict_reduce(const void* yc, int prec, const double* r, const int
 // precision the basis itself carries) and adds the run totals in FP64, so the kernel issues
 // one FP64 add per eight columns instead of one FP64 FMA per column -- GB300's FP64 pipe
 // would otherwise bound it, far below the memory rate.
-template <typename TP>
-struct ProAcc {
-  using X = double;
-};
-template <>
-struct ProAcc<float> {
-  using X = float;
-};
-
 template <typename TP>
 __global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, const ProMeta* __restrict__ meta,
                                                  const int32_t* __restrict__ tile_part,
@@ -169,7 +240,6 @@ void launch_prolong(const LevelDev& L, const double* x0, double* z, cudaStream_t
                                                         L.pro_tile_col0, L.idofs, L.cols, x0, z);
     check_launch("k_prolong");
   }
-  launch_axpy_gamma(L.gu_dof, L.gu_ptr, L.gcol, L.gval, L.ngu, x0, z, s);
 }
 
 void launch_axpy_gamma(const int32_t* gu_dof, const int32_t* gu_ptr, const int32_t* gcol, const double* gval,
