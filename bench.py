@@ -479,6 +479,8 @@ def run_gdsw(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if os.environ.get("GDSW_LAUNCH_OVERLAP") == "0":
+        gdsw.set_launch_overlap(False)
     if args.workload == "die":
         p = I.die()
         mixed = (args.mixed, "fp32", "fp32")

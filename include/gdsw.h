@@ -340,6 +340,13 @@ int gdsw_gemm_f32(const gdsw_gemm_task* tasks, int32_t ntasks, int32_t engine);
 /* Default engine of the FP32 set-up GEMMs for contexts set up afterwards (process-wide). */
 int gdsw_set_gemm_engine(int32_t engine);
 
+/* Overlapped launch chain of the batched GEMV sweeps (process-wide, default on): each launch
+ * of a local solve is made with programmatic dependent launch, so that its CTAs can become
+ * resident and prefetch their factor rows while the previous launch drains; they wait for the
+ * previous launch's completion before reading any vector, so results are bitwise the same with
+ * the chain on (1) or off (0).  Returns GDSW_OK, or GDSW_ERR_INVALID_ARG for another value. */
+int gdsw_set_launch_overlap(int32_t on);
+
 /* FMA throughput of the current device in TFLOP/s (precision GDSW_FP64 or GDSW_FP32): one
  * launch of independent fused multiply-add chains (8 per thread, 8 CTAs of 256 threads per
  * SM), timed with CUDA events after a warm-up launch.  It is the arithmetic roofline of the

@@ -572,6 +572,8 @@ static void upload_coarse_space(gdsw_ctx* c, int l, int phi_prec) {
   L.q_start = c->arena.upload(qst, s);
   L.q_count = c->arena.upload(qcnt, s);
   L.partial = c->arena.alloc<double>(size_t(std::max<int64_t>(poff[C.nparts], 1)));
+  GDSW_CHECK(8 * (256 + 33 * int64_t(L.max_c)) <= 200 * 1024, GDSW_ERR_INVALID_ARG,
+             "a part has too many coarse columns for the restriction tile");
   L.phiT = c->arena.alloc<char>(size_t(std::max<int64_t>(off, 1)) * elem_size(phi_prec));
   GDSW_CUDA(cudaMemsetAsync(L.phiT, 0, size_t(std::max<int64_t>(off, 1)) * elem_size(phi_prec), s));
   L.r0 = c->arena.alloc<double>(C.n0);

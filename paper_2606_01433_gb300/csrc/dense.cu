@@ -52,6 +52,39 @@ __device__ __forceinline__ void load16s(const __nv_bfloat16* p, float* v) {
   }
 }
 
+// ------------------------------------------------------------------ overlapped launch chain
+// The local sweeps are chains of launches: each slab step reads the vectors the previous one
+// wrote.  With programmatic dependent launch a CTA of the next launch may become resident while
+// the previous launch drains its last wave: it prefetches the start of its factor rows into L2
+// (the factors do not depend on the previous launch), then waits (griddepcontrol.wait) until
+// the previous grid has completed and its writes are visible, and only then reads a vector.
+// Every CTA releases its dependents as it starts (griddepcontrol.launch_dependents).  Both
+// instructions do nothing in a launch made without the attribute.
+bool g_launch_overlap = true;
+__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+template <typename... KArgs, typename... Args>
+static void launch_chained(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                           Args... args) {
+  if (!g_launch_overlap) {
+    kernel<<<grid, block, smem, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, KArgs(args)...);
+}
+
 // raw 16-byte streaming load, unpacked only at the multiply (keeps BF16 tiles at half the
 // registers of unpacked floats)
 __device__ __forceinline__ uint4 ldraw(const void* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
@@ -237,6 +270,24 @@ __global__ void __launch_bounds__(256) k_gemv(const TM* __restrict__ M, const TV
   TV* xs = reinterpret_cast<TV*>(smem_raw);
   const GemvTile tl = tiles[blockIdx.x];
   const GemvTask t = tasks[tl.task];
+  dep_release();
+  {  // factor prefetch before the dependency wait: the first 2 KB of the warp's first rows, or
+     // the first eight rows of the warp's part of a symmetric tile
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (t.kind == 1) {
+      constexpr int T = 32 * Vec16<TM>::N, RW = T / 8;
+      const int I = tl.row0 >> 16, J = tl.row0 & 0xffff;
+      const int64_t tidx = int64_t(I) * t.ld - int64_t(I) * (I - 1) / 2 + (J - I);
+      prefetch_l2(M + t.mat + tidx * T * T + int64_t(warp * RW + (lane >> 2)) * T + (lane & 3) * (128 / sizeof(TM)));
+    } else {
+      for (int q = lane >> 4; q < RPW; q += 2) {
+        const int r = tl.row0 + warp * RPW + q;
+        const int off = (lane & 15) * int(128 / sizeof(TM));
+        if (r < t.rows && off < t.ld) prefetch_l2(M + t.mat + int64_t(r) * t.ld + off);
+      }
+    }
+  }
+  dep_wait();
   if (t.kind == 1)  // packed symmetric tile; partial sums go to ybase + t.part
     sym_tile<TM, TV>(M, xbase, ybase, t, tl.row0 >> 16, tl.row0 & 0xffff, xs);
   else
@@ -312,6 +363,12 @@ __global__ void __launch_bounds__(256) k_gemvt(const TM* __restrict__ M, const T
   __shared__ TV part[(256 / LW) * (C + 1)];
   const GemvTile tl = tiles[blockIdx.x];
   const GemvTask t = tasks[tl.task];
+  dep_release();
+  {  // factor prefetch before the dependency wait: the tile's first 128 rows (two lines each)
+    const int r = threadIdx.x >> 1, off = tl.row0 + (threadIdx.x & 1) * int(128 / sizeof(TM));
+    if (r < t.rows && off < t.ld) prefetch_l2(M + t.mat + int64_t(r) * t.ld + off);
+  }
+  dep_wait();
   cols_tile<TM, TV>(M, xbase, ybase, bbase, t, tl.row0, reinterpret_cast<TV*>(smem_raw), part);
 }
 
@@ -321,17 +378,18 @@ void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P
   int t0 = P.launch_tile_off[launch], t1 = P.launch_tile_off[launch + 1];
   if (t1 <= t0) return;
   size_t smem = size_t(max_ld) * sizeof(TV);
+  const unsigned nb = unsigned(t1 - t0);
+  const GemvTile* tl = P.d_tiles + t0;
   if (P.transposed) {
-    k_gemvt<TM, TV><<<t1 - t0, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+    launch_chained(k_gemvt<TM, TV>, nb, 256, smem, s, M, x, y, b, P.d_tasks, tl);
     check_launch("k_gemvt");
   } else {
-    const int nb = t1 - t0;
     if (P.rows_per_tile == 128)
-      k_gemv<TM, TV, 4, 4><<<nb, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+      launch_chained(k_gemv<TM, TV, 4, 4>, nb, 256, smem, s, M, x, y, b, P.d_tasks, tl);
     else if (P.rows_per_tile == 64)
-      k_gemv<TM, TV, 4, 2><<<nb, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+      launch_chained(k_gemv<TM, TV, 4, 2>, nb, 256, smem, s, M, x, y, b, P.d_tasks, tl);
     else
-      k_gemv<TM, TV, 4, 1><<<nb, 256, smem, s>>>(M, x, y, b, P.d_tasks, P.d_tiles + t0);
+      launch_chained(k_gemv<TM, TV, 4, 1>, nb, 256, smem, s, M, x, y, b, P.d_tasks, tl);
     check_launch("k_gemv");
   }
 }
@@ -354,6 +412,8 @@ __global__ void k_sym_reduce(const TV* __restrict__ vec, TV* ybase, const GemvTa
                              const GemvTile* __restrict__ tiles, int T) {
   const GemvTile tl = tiles[blockIdx.x];
   const GemvTask t = tasks[tl.task];
+  dep_release();
+  dep_wait();
   reduce_tile<TV>(vec, ybase, t, tl.row0, T);
 }
 
@@ -361,7 +421,7 @@ template <typename TV>
 void launch_sym_reduce(const TV* vec, TV* y, const GemvPlan& P, int T, cudaStream_t s) {
   int t0 = P.launch_tile_off[0], t1 = P.launch_tile_off[1];
   if (t1 <= t0) return;
-  k_sym_reduce<TV><<<t1 - t0, 256, 0, s>>>(vec, y, P.d_tasks, P.d_tiles + t0, T);
+  launch_chained(k_sym_reduce<TV>, unsigned(t1 - t0), 256, 0, s, vec, y, P.d_tasks, P.d_tiles + t0, T);
   check_launch("k_sym_reduce");
 }
 template void launch_sym_reduce<double>(const double*, double*, const GemvPlan&, int, cudaStream_t);

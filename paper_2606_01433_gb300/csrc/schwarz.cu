@@ -52,10 +52,11 @@ template void launch_scatter<float>(const float*, const int32_t*, const int32_t*
 // Restriction r0 = Phi^T r in two deterministic passes over the stored Phi_I^T blocks.
 // Pass 1 (k_restrict_tiles): one CTA per 256-dof tile of a part's interior (the prolongation's
 // tiles); the tile's residual entries are gathered once into shared memory (in the basis
-// precision), and each warp takes rows j = warp, warp + 8, ... of PhiT_J, every lane streaming
-// eight coalesced entries of a row segment, so the basis is read exactly once with sixteen
-// loads in flight per lane.  A lane's eight products are summed in the basis precision, the
-// warp's 32 lane sums in FP64 by a fixed butterfly; the tile's partial of row j is stored.
+// precision).  Warp w takes rows j = w + 8 i of PhiT_J, four rows per step, each lane reading
+// one 16-byte vector per row per 32 V columns, so a step has eight (FP32) or sixteen (FP64)
+// 16-byte loads in flight per lane and the basis is read exactly once.  Lane sums (basis
+// precision) go to shared memory, [row][lane] with rows padded to 33; after the tile, one
+// thread per row adds its 32 lane sums in FP64 in lane order and stores the tile's partial.
 // Pass 2 (k_restrict_reduce): one warp per coarse column k adds, for each (part, row) that
 // carries k, that row's tile partials in tile order, then the Phi_Gamma entries of k.
 template <typename TP>
@@ -77,44 +78,60 @@ __global__ void __launch_bounds__(256) k_restrict_tiles(const TP* __restrict__ p
                                                         const int32_t* __restrict__ idofs,
                                                         const double* __restrict__ r, double* __restrict__ partial) {
   using X = typename ProAcc<TP>::X;
-  __shared__ X rs[256];
+  constexpr int V = 16 / sizeof(TP), NC = 256 / (32 * V);  // elements per 16-byte load; loads per lane per row
+  extern __shared__ __align__(16) unsigned char rt_smem[];
+  X* rs = reinterpret_cast<X*>(rt_smem);                      // 256 residual entries
+  X* lsum = rs + 256;                                          // [row][lane] lane sums, rows of 33
   const int J = tile_part[blockIdx.x];
   const ProMeta m = meta[J];
   const int col0 = tile_col0[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int span = min(256, m.ld - col0);   // stored row length left in this tile (a multiple of 8)
+  // rows j0, j0 + 8, j0 + 16, j0 + 24 of the tile, one 16-byte vector per lane and 32 V columns
+  auto load_step = [&](int j0, uint4 (&v)[4][NC]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + 8 * q;
+      const TP* row = phiT + m.phi + int64_t(j) * m.ld + col0;
+#pragma unroll
+      for (int u = 0; u < NC; ++u) {
+        const int t = (lane + 32 * u) * V;
+        v[q][u] = (j < m.c && t < span) ? __ldcs(reinterpret_cast<const uint4*>(row + t)) : make_uint4(0, 0, 0, 0);
+      }
+    }
+  };
+  auto use_step = [&](int j0, const uint4 (&v)[4][NC]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + 8 * q;
+      X acc = X(0);
+#pragma unroll
+      for (int u = 0; u < NC; ++u) {
+        const TP* e = reinterpret_cast<const TP*>(&v[q][u]);
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc = fma(X(e[k]), rs[(lane + 32 * u) * V + k], acc);
+      }
+      if (j < m.c) lsum[j * 33 + lane] = acc;
+    }
+  };
+  // the first step's basis loads go out before the residual gather and its barrier
+  uint4 va[4][NC];
+  load_step(warp, va);
   const int l = col0 + int(threadIdx.x);
   rs[threadIdx.x] = l < m.nI ? X(r[idofs[m.ioff + l]]) : X(0);
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int span = min(256, m.ld - col0);   // stored row length left in this tile (pad entries are zero)
+  for (int j0 = warp; j0 < m.c; j0 += 32) {
+    if (j0 > warp) load_step(j0, va);
+    use_step(j0, va);
+  }
+  __syncthreads();
   const int64_t pbase = part_poff[J] + tile_rank[blockIdx.x];
   const int nt = part_ntiles[J];
-  for (int j = warp; j < m.c; j += 16) {
-    const int j2 = j + 8;
-    const TP* a = phiT + m.phi + int64_t(j) * m.ld + col0;
-    const TP* b = phiT + m.phi + int64_t(j2) * m.ld + col0;
-    TP va[8], vb[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = lane + 32 * u;
-      va[u] = t < span ? __ldcs(a + t) : TP(0);
-      vb[u] = (t < span && j2 < m.c) ? __ldcs(b + t) : TP(0);
-    }
-    X sa = X(0), sb = X(0);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      sa = fma(X(va[u]), rs[lane + 32 * u], sa);
-      sb = fma(X(vb[u]), rs[lane + 32 * u], sb);
-    }
-    double da = double(sa), db = double(sb);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      da += __shfl_xor_sync(0xffffffffu, da, o);
-      db += __shfl_xor_sync(0xffffffffu, db, o);
-    }
-    if (lane == 0) {
-      partial[pbase + int64_t(j) * nt] = da;
-      if (j2 < m.c) partial[pbase + int64_t(j2) * nt] = db;
-    }
+  for (int j = threadIdx.x; j < m.c; j += blockDim.x) {
+    double s = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) s += double(lsum[j * 33 + q]);
+    partial[pbase + int64_t(j) * nt] = s;
   }
 }
 
@@ -147,14 +164,16 @@ void launch_restrict(const LevelDev& L, const double* r, double* r0, cudaStream_
   if (L.n0 == 0) return;
   const ProMeta* meta = reinterpret_cast<const ProMeta*>(L.pro_meta);
   if (L.n_pro_tiles > 0) {
+    const size_t es = L.phi_prec == GDSW_FP64 ? 8 : 4;
+    const size_t smem = es * (256 + 33 * size_t(L.max_c));
     if (L.phi_prec == GDSW_FP64)
-      k_restrict_tiles<double><<<L.n_pro_tiles, 256, 0, s>>>(static_cast<const double*>(L.phiT), meta,
-                                                             L.pro_tile_part, L.pro_tile_col0, L.pro_tile_rank,
-                                                             L.part_poff, L.part_ntiles, L.idofs, r, L.partial);
+      k_restrict_tiles<double><<<L.n_pro_tiles, 256, smem, s>>>(static_cast<const double*>(L.phiT), meta,
+                                                                L.pro_tile_part, L.pro_tile_col0, L.pro_tile_rank,
+                                                                L.part_poff, L.part_ntiles, L.idofs, r, L.partial);
     else
-      k_restrict_tiles<float><<<L.n_pro_tiles, 256, 0, s>>>(static_cast<const float*>(L.phiT), meta,
-                                                            L.pro_tile_part, L.pro_tile_col0, L.pro_tile_rank,
-                                                            L.part_poff, L.part_ntiles, L.idofs, r, L.partial);
+      k_restrict_tiles<float><<<L.n_pro_tiles, 256, smem, s>>>(static_cast<const float*>(L.phiT), meta,
+                                                               L.pro_tile_part, L.pro_tile_col0, L.pro_tile_rank,
+                                                               L.part_poff, L.part_ntiles, L.idofs, r, L.partial);
     check_launch("k_restrict_tiles");
   }
   k_restrict_reduce<<<(L.n0 + 7) / 8, 256, 0, s>>>(L.partial, L.q_start, L.q_count, r, L.rr_ptr, L.rr_pos,
@@ -180,13 +199,28 @@ __global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, co
   X* xs = reinterpret_cast<X*>(xs_raw);
   const int J = tile_part[blockIdx.x];
   const ProMeta m = meta[J];
+  const int l = tile_col0[blockIdx.x] + threadIdx.x;
+  const TP* p = phiT + m.phi + l;
+  TP v0[16];  // the first sixteen columns' loads go out before the staging of x0 and its barrier
+  if (l < m.nI && m.c >= 16) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v0[u] = __ldcs(p + int64_t(u) * m.ld);
+  }
   for (int j = threadIdx.x; j < m.c; j += blockDim.x) xs[j] = X(x0[cols[m.coff + j]]);
   __syncthreads();
-  const int l = tile_col0[blockIdx.x] + threadIdx.x;
   if (l >= m.nI) return;
   double acc = 0.0;
-  const TP* p = phiT + m.phi + l;
   int j = 0;
+  if (m.c >= 16) {
+#pragma unroll
+    for (int h = 0; h < 16; h += 8) {
+      X part = X(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) part = fma(X(v0[h + u]), xs[h + u], part);
+      acc += double(part);
+    }
+    j = 16;
+  }
   for (; j + 16 <= m.c; j += 16) {  // sixteen independent loads in flight, products in column order
     TP v[16];
 #pragma unroll
@@ -252,6 +286,8 @@ void launch_axpy_gamma(const int32_t* gu_dof, const int32_t* gu_ptr, const int32
 void set_prolong_smem_limits() {
   cudaFuncSetAttribute(k_prolong<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_prolong<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_restrict_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_restrict_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace gdsw

@@ -409,6 +409,16 @@ extern "C" int gdsw_gemm_f32(const gdsw_gemm_task* tasks, int32_t ntasks, int32_
   }
 }
 
+namespace gdsw {
+extern bool g_launch_overlap;
+}
+
+extern "C" int gdsw_set_launch_overlap(int32_t on) {
+  if (on != 0 && on != 1) return GDSW_ERR_INVALID_ARG;
+  gdsw::g_launch_overlap = on != 0;
+  return GDSW_OK;
+}
+
 extern "C" int gdsw_set_gemm_engine(int32_t engine) {
   if (engine < GDSW_GEMM_AUTO || engine > GDSW_GEMM_TENSOR) return GDSW_ERR_INVALID_ARG;
   gdsw::set_gemm_engine(engine);

@@ -142,6 +142,7 @@ def load(path: str = LIB_PATH):
         "gdsw_mg_restrict": ([vp, i32, dp, dp], C.c_int),
         "gdsw_mg_stats": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "gdsw_set_gemm_engine": ([i32], C.c_int),
+        "gdsw_set_launch_overlap": ([i32], C.c_int),
         "gdsw_plan_bytes": ([vp, i32, i32, i32, C.POINTER(C.c_double)], C.c_int),
         "gdsw_set_local_sweep": ([vp, i32, i32, i32], C.c_int),
         "gdsw_picard_update": ([vp, vp], C.c_int),
@@ -187,6 +188,13 @@ def gemm_f32(tasks, engine="tensor"):
     rc = lib.gdsw_gemm_f32(arr, len(tasks), GEMM_ENGINE[engine])
     if rc != GDSW_OK:
         raise GdswError(rc, "gdsw_gemm_f32 failed")
+
+
+def set_launch_overlap(on=True):
+    """Overlapped (programmatic dependent) launch chain of the local sweeps, process-wide."""
+    rc = load().gdsw_set_launch_overlap(1 if on else 0)
+    if rc != GDSW_OK:
+        raise GdswError(rc, "gdsw_set_launch_overlap failed")
 
 
 def set_gemm_engine(engine):

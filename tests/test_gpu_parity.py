@@ -288,6 +288,40 @@ def test_host_buffers_and_graph(lib):
     g.close()
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32, BF16], ids=["fp64", "fp32", "bf16"])
+def test_launch_overlap_is_bitwise_neutral(lib, prec):
+    """The overlapped launch chain of the sweeps (programmatic dependent launch with a factor
+    prefetch before the dependency wait) changes no number: applies (plain and CUDA-graph)
+    and solves are bitwise equal with the chain on and off, on a four-level die problem."""
+    p, S, P = oracle_for("die_rcb_4lvl")
+    r = np.random.default_rng(7).standard_normal(S["A"].shape[0])
+    b = I.random_rhs(S["A"].shape[0], 12)
+    out = []
+    try:
+        for on in (True, False):
+            lib.set_launch_overlap(on)
+            res = []
+            for graph in (False, True):
+                ctx = lib.Context(p, precision=prec[0], phi_precision=prec[1], tol=1e-10, use_graph=graph)
+                if not graph:   # one launch per slab step: the chained path
+                    ctx.gdsw_set_local_sweep(False)
+                z = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+                ctx.gdsw_apply(dev(r), z)
+                res.append(host(z))
+                if not graph:
+                    x = torch.zeros_like(z)
+                    info = ctx.gdsw_solve(dev(b), x)
+                    assert info.status == 0
+                    res.append((info.iterations, host(x)))
+                ctx.close()
+            out.append(res)
+    finally:
+        lib.set_launch_overlap(True)
+    (z_on, (it_on, x_on), zg_on), (z_off, (it_off, x_off), zg_off) = out
+    assert np.array_equal(z_on, z_off) and np.array_equal(zg_on, zg_off) and np.array_equal(z_on, zg_on)
+    assert it_on == it_off and np.array_equal(x_on, x_off)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_persistent_sweep_equals_step_launches(lib, prec):
     """The persistent level sweep (one launch per level; tiles claimed in dependency order,
