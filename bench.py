@@ -698,7 +698,8 @@ def run_gdsw(args, rank, world, local):
                                         "coarse_levels", "total"], [float(v) for v in sizes.setup_ms])),
         "factor_gb": sizes.factor_entries[0] * (4 if args.mixed == "fp32" else 2) / 1e9,
         "roofline": {"kernel": ("k_sweep (level-1 persistent block-LDL^T sweep, one launch per apply)" if persistent
-                                else "k_gemv/k_gemvt (level-1 block-LDL^T sweeps, one launch per slab step)"),
+                                else "k_gemv/k_sym_reduce/k_gemvt (level-1 block-LDL^T sweep: one chained launch "
+                                     "per slab step, the chain of one apply timed as one unit)"),
                      "bound": "hbm", "achieved": gemv_gbs,
                      "peak": peak, "unit": "GB/s", "frac": (gemv_gbs / peak) if gemv_gbs else None,
                      "peak_kind": peak_kind, "avg_launch_ms": gemv_avg_ms, "avg_launch_bytes": gemv_avg_bytes,

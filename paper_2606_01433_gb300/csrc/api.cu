@@ -1005,8 +1005,7 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
   // block-LDL^T sweeps: forward launches (S_k^{-1} y_k and the G_{k+1} update), then backward
   // launches (G_{k+1}^T), every one a ragged batched GEMV over all parts of the level
   const int group = l == 0 ? GDSW_K_LOCAL : GDSW_K_COARSE;
-  auto sweep = [&](const GemvPlan& P, int k, int ld, double bytes) {
-    ProfScope ps(c, group, bytes, s);
+  auto sweep = [&](const GemvPlan& P, int k, int ld) {
     if (L.prec == GDSW_FP64) {
       double* v = static_cast<double*>(L.vec);
       launch_gemv<double, double>(static_cast<const double*>(L.fac), v, v, v, P, k, ld, s);
@@ -1034,16 +1033,20 @@ static void local_solve(gdsw_ctx* c, int l, const double* r, double* z, cudaStre
       launch_sweep<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(L.fac), static_cast<float*>(L.vec),
                                          L.sweep, c->d_sweep_flag, L.sym_T, s);
   } else {
-  for (int k = 0; k < L.fwd.nlaunch(); ++k) sweep(L.fwd, k, L.fwd_ld[k], L.fwd_bytes[k]);
+  // the chained launches are timed as one unit: events between them would break the chain
+  double bytes = L.red_bytes;
+  for (double b : L.fwd_bytes) bytes += b;
+  for (double b : L.bwd_bytes) bytes += b;
+  ProfScope ps(c, group, bytes, s);
+  for (int k = 0; k < L.fwd.nlaunch(); ++k) sweep(L.fwd, k, L.fwd_ld[k]);
   if (L.red.launch_tile_off.size() == 2 && L.red.launch_tile_off[1] > 0) {
     // w_k = S_k^{-1} y_k of the packed symmetric blocks: sum of the partial products
-    ProfScope ps(c, group, L.red_bytes, s);
     if (L.prec == GDSW_FP64)
       launch_sym_reduce<double>(static_cast<const double*>(L.vec), static_cast<double*>(L.vec), L.red, L.sym_T, s);
     else
       launch_sym_reduce<float>(static_cast<const float*>(L.vec), static_cast<float*>(L.vec), L.red, L.sym_T, s);
   }
-  for (int k = 0; k < L.bwd.nlaunch(); ++k) sweep(L.bwd, k, L.bwd_ld[k], L.bwd_bytes[k]);
+  for (int k = 0; k < L.bwd.nlaunch(); ++k) sweep(L.bwd, k, L.bwd_ld[k]);
   }
   {
     ProfScope ps(c, l == 0 ? GDSW_K_SCATTER : GDSW_K_COARSE,

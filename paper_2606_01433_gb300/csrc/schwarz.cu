@@ -199,28 +199,13 @@ __global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, co
   X* xs = reinterpret_cast<X*>(xs_raw);
   const int J = tile_part[blockIdx.x];
   const ProMeta m = meta[J];
-  const int l = tile_col0[blockIdx.x] + threadIdx.x;
-  const TP* p = phiT + m.phi + l;
-  TP v0[16];  // the first sixteen columns' loads go out before the staging of x0 and its barrier
-  if (l < m.nI && m.c >= 16) {
-#pragma unroll
-    for (int u = 0; u < 16; ++u) v0[u] = __ldcs(p + int64_t(u) * m.ld);
-  }
   for (int j = threadIdx.x; j < m.c; j += blockDim.x) xs[j] = X(x0[cols[m.coff + j]]);
   __syncthreads();
+  const int l = tile_col0[blockIdx.x] + threadIdx.x;
   if (l >= m.nI) return;
   double acc = 0.0;
+  const TP* p = phiT + m.phi + l;
   int j = 0;
-  if (m.c >= 16) {
-#pragma unroll
-    for (int h = 0; h < 16; h += 8) {
-      X part = X(0);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) part = fma(X(v0[h + u]), xs[h + u], part);
-      acc += double(part);
-    }
-    j = 16;
-  }
   for (; j + 16 <= m.c; j += 16) {  // sixteen independent loads in flight, products in column order
     TP v[16];
 #pragma unroll
