@@ -41,6 +41,44 @@ inline void check_launch(const char* what) {
   if (e != cudaSuccess) throw Error{GDSW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
 }
 
+// ------------------------------------------------------------------ overlapped launch chains
+// A launch made with programmatic dependent launch may have CTAs resident while the previous
+// kernel of its stream drains.  Every kernel launched that way calls dep_release() (its own
+// dependents may start) and dep_wait() (the previous grid has completed and its writes are
+// visible) before it reads anything the previous kernels wrote or writes anything they read;
+// before the wait it may only read data that no kernel of the stream writes (factors, plans,
+// the operator), and after it it reads such data through coherent loads (no ld.global.nc).
+// A kernel that follows a wait on another stream's event is launched in plain order: the
+// dependency wait covers only the previous grid of its own stream.  Both instructions do
+// nothing in a launch made without the attribute.
+// g_launch_overlap (gdsw_set_launch_overlap) switches the attribute off process-wide.
+extern bool g_launch_overlap;
+#ifdef __CUDACC__
+__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                           Args... args) {
+  if (!g_launch_overlap) {
+    kernel<<<grid, block, smem, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, KArgs(args)...);
+}
+#endif
+
 // ------------------------------------------------------------------ device memory
 // Stream-ordered when built with a stream (cudaMallocAsync / cudaFreeAsync on that stream):
 // freeing then never waits for the whole device, so contexts that set up, solve and tear down

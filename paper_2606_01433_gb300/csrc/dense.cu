@@ -54,36 +54,11 @@ __device__ __forceinline__ void load16s(const __nv_bfloat16* p, float* v) {
 
 // ------------------------------------------------------------------ overlapped launch chain
 // The local sweeps are chains of launches: each slab step reads the vectors the previous one
-// wrote.  With programmatic dependent launch a CTA of the next launch may become resident while
-// the previous launch drains its last wave: it prefetches the start of its factor rows into L2
-// (the factors do not depend on the previous launch), then waits (griddepcontrol.wait) until
-// the previous grid has completed and its writes are visible, and only then reads a vector.
-// Every CTA releases its dependents as it starts (griddepcontrol.launch_dependents).  Both
-// instructions do nothing in a launch made without the attribute.
+// wrote.  Each launch of the chain is a programmatic dependent launch (common.h): its CTAs may
+// become resident while the previous launch drains its last wave, prefetch the start of their
+// factor rows into L2 (the factors do not depend on the previous launch), and wait for the
+// previous grid before reading a vector.
 bool g_launch_overlap = true;
-__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
-template <typename... KArgs, typename... Args>
-static void launch_chained(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
-                           Args... args) {
-  if (!g_launch_overlap) {
-    kernel<<<grid, block, smem, s>>>(args...);
-    return;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, KArgs(args)...);
-}
 
 // raw 16-byte streaming load, unpacked only at the multiply (keeps BF16 tiles at half the
 // registers of unpacked floats)
@@ -381,15 +356,15 @@ void launch_gemv(const TM* M, const TV* x, TV* y, const TV* b, const GemvPlan& P
   const unsigned nb = unsigned(t1 - t0);
   const GemvTile* tl = P.d_tiles + t0;
   if (P.transposed) {
-    launch_chained(k_gemvt<TM, TV>, nb, 256, smem, s, M, x, y, b, P.d_tasks, tl);
+    launch_chained(k_gemvt<TM, TV>, dim3(nb), dim3(256), smem, s, M, x, y, b, P.d_tasks, tl);
     check_launch("k_gemvt");
   } else {
     if (P.rows_per_tile == 128)
-      launch_chained(k_gemv<TM, TV, 4, 4>, nb, 256, smem, s, M, x, y, b, P.d_tasks, tl);
+      launch_chained(k_gemv<TM, TV, 4, 4>, dim3(nb), dim3(256), smem, s, M, x, y, b, P.d_tasks, tl);
     else if (P.rows_per_tile == 64)
-      launch_chained(k_gemv<TM, TV, 4, 2>, nb, 256, smem, s, M, x, y, b, P.d_tasks, tl);
+      launch_chained(k_gemv<TM, TV, 4, 2>, dim3(nb), dim3(256), smem, s, M, x, y, b, P.d_tasks, tl);
     else
-      launch_chained(k_gemv<TM, TV, 4, 1>, nb, 256, smem, s, M, x, y, b, P.d_tasks, tl);
+      launch_chained(k_gemv<TM, TV, 4, 1>, dim3(nb), dim3(256), smem, s, M, x, y, b, P.d_tasks, tl);
     check_launch("k_gemv");
   }
 }
@@ -421,7 +396,7 @@ template <typename TV>
 void launch_sym_reduce(const TV* vec, TV* y, const GemvPlan& P, int T, cudaStream_t s) {
   int t0 = P.launch_tile_off[0], t1 = P.launch_tile_off[1];
   if (t1 <= t0) return;
-  launch_chained(k_sym_reduce<TV>, unsigned(t1 - t0), 256, 0, s, vec, y, P.d_tasks, P.d_tiles + t0, T);
+  launch_chained(k_sym_reduce<TV>, dim3(unsigned(t1 - t0)), dim3(256), 0, s, vec, y, P.d_tasks, P.d_tiles + t0, T);
   check_launch("k_sym_reduce");
 }
 template void launch_sym_reduce<double>(const double*, double*, const GemvPlan&, int, cudaStream_t);

@@ -21,6 +21,8 @@ constexpr int DG = 8;       // basis vectors per multi-dot pass
 // part[b * ldp + t0 + q] = sum over block b's chunk of V[t0+q][e] * w[e]
 __global__ void __launch_bounds__(RT) k_dots(const double* __restrict__ V, int64_t n, int nvec,
                                              const double* __restrict__ w, double* __restrict__ part, int ldp) {
+  dep_release();
+  dep_wait();
   __shared__ double red[DG][RT];
   const int t0 = blockIdx.y * DG;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -50,6 +52,8 @@ __global__ void __launch_bounds__(RT) k_dots(const double* __restrict__ V, int64
 // fixed butterfly (deterministic)
 __global__ void k_sum_parts(const double* __restrict__ part, int nb, int nvec, int ldp, double* __restrict__ out,
                             int accumulate) {
+  dep_release();
+  dep_wait();
   const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (t >= nvec) return;
@@ -63,6 +67,8 @@ __global__ void k_sum_parts(const double* __restrict__ part, int nb, int nvec, i
 // w -= sum_t h[t] V[t]
 __global__ void k_update(const double* __restrict__ V, int64_t n, int nvec, const double* __restrict__ h,
                          double* __restrict__ w) {
+  dep_release();
+  dep_wait();
   extern __shared__ double hs[];
   for (int t = threadIdx.x; t < nvec; t += blockDim.x) hs[t] = h[t];
   __syncthreads();
@@ -76,6 +82,8 @@ __global__ void k_update(const double* __restrict__ V, int64_t n, int nvec, cons
 // x += sum_t y[t] Z[t]
 __global__ void k_xupdate(const double* __restrict__ Z, int64_t n, int nvec, const double* __restrict__ y,
                           double* __restrict__ x) {
+  dep_release();
+  dep_wait();
   extern __shared__ double ys[];
   for (int t = threadIdx.x; t < nvec; t += blockDim.x) ys[t] = y[t];
   __syncthreads();
@@ -87,6 +95,8 @@ __global__ void k_xupdate(const double* __restrict__ Z, int64_t n, int nvec, con
 }
 
 __global__ void k_norm_parts(const double* __restrict__ w, int64_t n, double* __restrict__ part) {
+  dep_release();
+  dep_wait();
   __shared__ double red[RT];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t e0 = blockIdx.x * chunk, e1 = min(n, e0 + chunk);
@@ -103,6 +113,8 @@ __global__ void k_norm_parts(const double* __restrict__ w, int64_t n, double* __
 
 // scal[slot] = sqrt(sum of parts)
 __global__ void k_norm_finish(const double* __restrict__ part, int nb, double* __restrict__ scal, int slot) {
+  dep_release();
+  dep_wait();
   if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   double s = 0.0;
   for (int b = threadIdx.x; b < nb; b += 32) s += part[b];
@@ -114,6 +126,8 @@ __global__ void k_norm_finish(const double* __restrict__ part, int nb, double* _
 // v = w / scal[slot] (0 if the norm vanished)
 __global__ void k_scale(const double* __restrict__ w, int64_t n, const double* __restrict__ scal, int slot,
                         double* __restrict__ v) {
+  dep_release();
+  dep_wait();
   int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (e >= n) return;
   double d = scal[slot];
@@ -125,6 +139,8 @@ __global__ void k_scale(const double* __restrict__ w, int64_t n, const double* _
 // |g[j+1]| (the residual estimate), mirrored to pinned host memory.
 __global__ void k_givens(double* __restrict__ H, int ldh, int j, double* __restrict__ cs, double* __restrict__ sn,
                          double* __restrict__ g, double* __restrict__ scal, double* __restrict__ hmirror) {
+  dep_release();
+  dep_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* col = H + int64_t(j) * ldh;
   col[j + 1] = scal[1];
@@ -149,6 +165,8 @@ __global__ void k_givens(double* __restrict__ H, int ldh, int j, double* __restr
 // back substitution y = R^{-1} g for the first k columns
 __global__ void k_backsolve(const double* __restrict__ H, int ldh, int k, const double* __restrict__ g,
                             double* __restrict__ y) {
+  dep_release();
+  dep_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = k - 1; i >= 0; --i) {
     double s = g[i];
@@ -160,6 +178,8 @@ __global__ void k_backsolve(const double* __restrict__ H, int ldh, int k, const 
 
 // start of a cycle: V[0] = r / beta, g = (beta, 0, ...)
 __global__ void k_cycle_start(double* __restrict__ g, int m1, const double* __restrict__ scal) {
+  dep_release();
+  dep_wait();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < m1) g[t] = t == 0 ? scal[0] : 0.0;
 }
@@ -190,20 +210,22 @@ static void cgs2(gdsw_ctx* c, int j, double* w, cudaStream_t s) {
   // four passes over the basis (two multi-dots, two multi-axpys) plus w traffic and the norm
   ProfScope ps(c, GDSW_K_ARNOLDI, 8.0 * n * (4.0 * nvec + 7.0), s);
   for (int pass = 0; pass < 2; ++pass) {
-    k_dots<<<gd, RT, 0, s>>>(c->d_V, n, nvec, w, c->d_part, ldp);
+    launch_chained(k_dots, gd, dim3(RT), 0, s, c->d_V, n, nvec, w, c->d_part, ldp);
     check_launch("k_dots");
-    k_sum_parts<<<(nvec + 3) / 4, 128, 0, s>>>(c->d_part, RB, nvec, ldp, pass == 0 ? hcol : c->d_y, 0);
+    launch_chained(k_sum_parts, dim3((nvec + 3) / 4), dim3(128), 0, s, c->d_part, RB, nvec, ldp,
+                   pass == 0 ? hcol : c->d_y, 0);
     check_launch("k_sum_parts");
-    k_update<<<ub, 256, nvec * sizeof(double), s>>>(c->d_V, n, nvec, pass == 0 ? hcol : c->d_y, w);
+    launch_chained(k_update, dim3(ub), dim3(256), nvec * sizeof(double), s, c->d_V, n, nvec,
+                   pass == 0 ? hcol : c->d_y, w);
     check_launch("k_update");
     if (pass == 1) {
-      k_sum_parts<<<(nvec + 3) / 4, 128, 0, s>>>(c->d_part, RB, nvec, ldp, hcol, 1);
+      launch_chained(k_sum_parts, dim3((nvec + 3) / 4), dim3(128), 0, s, c->d_part, RB, nvec, ldp, hcol, 1);
       check_launch("k_sum_parts");
     }
   }
-  k_norm_parts<<<RB, RT, 0, s>>>(w, n, c->d_part);
+  launch_chained(k_norm_parts, dim3(RB), dim3(RT), 0, s, w, n, c->d_part);
   check_launch("k_norm_parts");
-  k_norm_finish<<<1, 32, 0, s>>>(c->d_part, RB, c->d_scal, 1);
+  launch_chained(k_norm_finish, dim3(1), dim3(32), 0, s, c->d_part, RB, c->d_scal, 1);
   check_launch("k_norm_finish");
 }
 
@@ -278,9 +300,10 @@ void fgmres_solve(gdsw_ctx* c, const double* b, double* x, gdsw_solve_info* info
         launch_spmv(c, zj, w, nullptr, s);
       }
       cgs2(c, j, w, s);
-      k_scale<<<ub, 256, 0, s>>>(w, n, c->d_scal, 1, w);
+      launch_chained(k_scale, dim3(ub), dim3(256), 0, s, w, n, c->d_scal, 1, w);
       check_launch("k_scale");
-      k_givens<<<1, 32, 0, s>>>(c->d_H, ldh, j, c->d_cs, c->d_sn, c->d_gvec, c->d_scal, nullptr);
+      launch_chained(k_givens, dim3(1), dim3(32), 0, s, c->d_H, ldh, j, c->d_cs, c->d_sn, c->d_gvec, c->d_scal,
+                     static_cast<double*>(nullptr));
       check_launch("k_givens");
       GDSW_CUDA(cudaMemcpyAsync(c->h_scal, c->d_scal + 2, 8, cudaMemcpyDeviceToHost, s));
       GDSW_CUDA(cudaStreamSynchronize(s));

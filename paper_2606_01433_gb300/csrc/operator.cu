@@ -449,6 +449,9 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ sell_r
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nu = 3 * nv;
   const int64_t vblocks = (nslices + 1) / 2;
+  // launched in plain stream order (its x gathers use the non-coherent cache path, which a
+  // chained launch must not use for data the previous kernel wrote); it lets its successor start
+  dep_release();
   if (blockIdx.x < vblocks) {
     const int64_t sl = 2 * int64_t(blockIdx.x) + (warp >> 2);
     const int sub = warp & 3;
@@ -625,8 +628,8 @@ void launch_spmv(gdsw_ctx* c, const double* x, double* y, const double* rhs, cud
   const int64_t ns = c->n_sell_slices;
   const int64_t blocks = (ns + 1) / 2 + (np + 7) / 8;
   k_spmv<<<int(blocks), 256, 0, s>>>(c->d_sell_row, c->d_sell_aoff, c->d_sell_acol, c->d_sell_aval,
-                                              c->d_sell_boff, c->d_sell_bcol, c->d_sell_btval, ns, c->d_b_ptr,
-                                              c->d_b_col, bval, nv, np, x, y, rhs);
+                                     c->d_sell_boff, c->d_sell_bcol, c->d_sell_btval, ns, c->d_b_ptr, c->d_b_col,
+                                     bval, nv, np, x, y, rhs);
   check_launch("k_spmv");
 }
 

@@ -12,14 +12,16 @@ namespace gdsw {
 template <typename TV>
 __global__ void k_gather(const double* __restrict__ r, const int32_t* __restrict__ idx, TV* __restrict__ out,
                          int64_t n) {
+  dep_release();
+  dep_wait();
   int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (p < n) out[p] = TV(__ldg(r + __ldg(idx + p)));
+  if (p < n) out[p] = TV(r[__ldg(idx + p)]);
 }
 
 template <typename TV>
 void launch_gather(const double* r, const int32_t* idx, TV* out, int64_t n, cudaStream_t s) {
   if (n == 0) return;
-  k_gather<TV><<<int((n + 255) / 256), 256, 0, s>>>(r, idx, out, n);
+  launch_chained(k_gather<TV>, dim3(unsigned((n + 255) / 256)), dim3(256), 0, s, r, idx, out, n);
   check_launch("k_gather");
 }
 template void launch_gather<double>(const double*, const int32_t*, double*, int64_t, cudaStream_t);
@@ -30,6 +32,8 @@ template void launch_gather<float>(const double*, const int32_t*, float*, int64_
 template <typename TV>
 __global__ void k_scatter(const TV* __restrict__ x, const int32_t* __restrict__ ptr, const int32_t* __restrict__ pos,
                           const double* __restrict__ w, double* __restrict__ z, int n, int accumulate) {
+  dep_release();
+  dep_wait();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
   double acc = 0.0;
@@ -41,7 +45,7 @@ template <typename TV>
 void launch_scatter(const TV* x, const int32_t* ptr, const int32_t* pos, const double* w, double* z, int n,
                     int accumulate, cudaStream_t s) {
   if (n == 0) return;
-  k_scatter<TV><<<(n + 255) / 256, 256, 0, s>>>(x, ptr, pos, w, z, n, accumulate);
+  launch_chained(k_scatter<TV>, dim3(unsigned((n + 255) / 256)), dim3(256), 0, s, x, ptr, pos, w, z, n, accumulate);
   check_launch("k_scatter");
 }
 template void launch_scatter<double>(const double*, const int32_t*, const int32_t*, const double*, double*, int, int,
@@ -82,6 +86,7 @@ __global__ void __launch_bounds__(256) k_restrict_tiles(const TP* __restrict__ p
   extern __shared__ __align__(16) unsigned char rt_smem[];
   X* rs = reinterpret_cast<X*>(rt_smem);                      // 256 residual entries
   X* lsum = rs + 256;                                          // [row][lane] lane sums, rows of 33
+  dep_release();  // launched in plain stream order (it follows a wait on the main stream)
   const int J = tile_part[blockIdx.x];
   const ProMeta m = meta[J];
   const int col0 = tile_col0[blockIdx.x];
@@ -143,6 +148,8 @@ __global__ void k_restrict_reduce(const double* __restrict__ partial, const int6
                                   const int32_t* __restrict__ rr_ptr, const int32_t* __restrict__ rr_pos,
                                   const int32_t* __restrict__ rg_ptr, const int32_t* __restrict__ rg_dof,
                                   const double* __restrict__ rg_val, double* __restrict__ r0, int n0) {
+  dep_release();
+  dep_wait();
   int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (k >= n0) return;
@@ -176,8 +183,8 @@ void launch_restrict(const LevelDev& L, const double* r, double* r0, cudaStream_
                                                                L.part_poff, L.part_ntiles, L.idofs, r, L.partial);
     check_launch("k_restrict_tiles");
   }
-  k_restrict_reduce<<<(L.n0 + 7) / 8, 256, 0, s>>>(L.partial, L.q_start, L.q_count, r, L.rr_ptr, L.rr_pos,
-                                                   L.rg_ptr, L.rg_dof, L.rg_val, r0, L.n0);
+  launch_chained(k_restrict_reduce, dim3(unsigned((L.n0 + 7) / 8)), dim3(256), 0, s, L.partial, L.q_start,
+                 L.q_count, r, L.rr_ptr, L.rr_pos, L.rg_ptr, L.rg_dof, L.rg_val, r0, L.n0);
   check_launch("k_restrict_reduce");
 }
 
@@ -197,6 +204,7 @@ __global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, co
   using X = typename ProAcc<TP>::X;
   extern __shared__ double xs_raw[];
   X* xs = reinterpret_cast<X*>(xs_raw);
+  dep_release();  // launched in plain stream order (it follows a wait on the coarse stream)
   const int J = tile_part[blockIdx.x];
   const ProMeta m = meta[J];
   for (int j = threadIdx.x; j < m.c; j += blockDim.x) xs[j] = X(x0[cols[m.coff + j]]);
@@ -239,6 +247,8 @@ __global__ void __launch_bounds__(256) k_prolong(const TP* __restrict__ phiT, co
 __global__ void k_axpy_gamma(const int32_t* __restrict__ gu_dof, const int32_t* __restrict__ gu_ptr,
                              const int32_t* __restrict__ gcol, const double* __restrict__ gval, int64_t ngu,
                              const double* __restrict__ x0, double* __restrict__ z) {
+  dep_release();
+  dep_wait();
   int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (q >= ngu) return;
   double acc = 0.0;
@@ -264,7 +274,8 @@ void launch_prolong(const LevelDev& L, const double* x0, double* z, cudaStream_t
 void launch_axpy_gamma(const int32_t* gu_dof, const int32_t* gu_ptr, const int32_t* gcol, const double* gval,
                        int64_t ngu, const double* x0, double* z, cudaStream_t s) {
   if (ngu == 0) return;
-  k_axpy_gamma<<<int((ngu + 255) / 256), 256, 0, s>>>(gu_dof, gu_ptr, gcol, gval, ngu, x0, z);
+  launch_chained(k_axpy_gamma, dim3(unsigned((ngu + 255) / 256)), dim3(256), 0, s, gu_dof, gu_ptr, gcol, gval, ngu,
+                 x0, z);
   check_launch("k_axpy_gamma");
 }
 
