@@ -343,6 +343,10 @@ __global__ void __launch_bounds__(256) k_vanka(const int32_t* __restrict__ pdof,
                                                double* __restrict__ z, double omega) {
   const int64_t q = p0 + (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
+  dep_release();
+  if (q < p1)  // the patch inverse is set-up data: its first 4 KB go to L2 before the wait
+    prefetch_l2(reinterpret_cast<const char*>(pinv + q * PMAX * PMAX) + 128 * lane);
+  dep_wait();
   if (q >= p1) return;
   const int32_t* d = pdof + q * PMAX;
   const TM* M = pinv + q * PMAX * PMAX;
@@ -379,6 +383,8 @@ __global__ void __launch_bounds__(256) k_resid_vrows(const int32_t* __restrict__
                                                      double* __restrict__ r) {
   const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
+  dep_release();
+  dep_wait();
   if (q >= nrows) return;
   const int32_t I = rows[q];
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
@@ -417,6 +423,8 @@ __global__ void __launch_bounds__(256) k_resid_prows(const int32_t* __restrict__
                                                      const double* __restrict__ b, double* __restrict__ r) {
   const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
+  dep_release();
+  dep_wait();
   if (q >= nrows) return;
   const int32_t P = rows[q];
   float s = 0.f;
@@ -440,6 +448,8 @@ __global__ void k_csr_mv(const int32_t* __restrict__ ptr, const int32_t* __restr
                          const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
                          int64_t n, int accumulate) {
   const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  dep_release();
+  dep_wait();
   if (r >= n) return;
   double acc = accumulate ? y[r] : 0.0;
   for (int32_t q = ptr[r]; q < ptr[r + 1]; ++q) acc = fma(val[q], x[col[q]], acc);
@@ -449,7 +459,7 @@ __global__ void k_csr_mv(const int32_t* __restrict__ ptr, const int32_t* __restr
 static void csr_mv(const int32_t* ptr, const int32_t* col, const double* val, const double* x, double* y, int64_t n,
                    bool acc, cudaStream_t s) {
   if (n == 0) return;
-  k_csr_mv<<<int((n + 255) / 256), 256, 0, s>>>(ptr, col, val, x, y, n, acc ? 1 : 0);
+  launch_chained(k_csr_mv, dim3(unsigned((n + 255) / 256)), dim3(256), 0, s, ptr, col, val, x, y, n, acc ? 1 : 0);
   check_launch("k_csr_mv");
 }
 
@@ -464,13 +474,13 @@ static void colour_residual(gdsw_mg* mg, MgGrid& G, int c, const double* b, cons
   const gdsw_ctx* x = G.ctx;
   const int64_t nv = G.prow_off[c] - G.vrow_off[c], np = G.vrow_off[c + 1] - G.prow_off[c];
   if (nv > 0) {
-    k_resid_vrows<<<int((nv + 7) / 8), 256, 0, s>>>(G.d_rows + G.vrow_off[c], nv, x->d_a_ptr, x->d_a_col, G.d_a32,
-                                                    x->d_bt_ptr, x->d_bt_col, G.d_bt32, x->mesh.nu, z, b, G.d_r);
+    launch_chained(k_resid_vrows, dim3(unsigned((nv + 7) / 8)), dim3(256), 0, s, G.d_rows + G.vrow_off[c], nv,
+                   x->d_a_ptr, x->d_a_col, G.d_a32, x->d_bt_ptr, x->d_bt_col, G.d_bt32, x->mesh.nu, z, b, G.d_r);
     check_launch("k_resid_vrows");
   }
   if (np > 0) {
-    k_resid_prows<<<int((np + 7) / 8), 256, 0, s>>>(G.d_rows + G.prow_off[c], np, x->d_b_ptr, x->d_b_col, G.d_b32,
-                                                    x->mesh.nu, z, b, G.d_r);
+    launch_chained(k_resid_prows, dim3(unsigned((np + 7) / 8)), dim3(256), 0, s, G.d_rows + G.prow_off[c], np,
+                   x->d_b_ptr, x->d_b_col, G.d_b32, x->mesh.nu, z, b, G.d_r);
     check_launch("k_resid_prows");
   }
 }
@@ -487,11 +497,11 @@ static void smooth(gdsw_mg* mg, int l, const double* b, double* z, int steps, bo
       colour_residual(mg, G, c, b, z, s);
       const int blocks = int((p1 - p0 + 7) / 8);
       if (mg->opt.smoother_precision == GDSW_FP64)
-        k_vanka<double><<<blocks, 256, 0, s>>>(G.d_pdof, static_cast<const double*>(G.d_pinv), p0, p1, G.d_r, z,
-                                               mg->opt.omega);
+        launch_chained(k_vanka<double>, dim3(unsigned(blocks)), dim3(256), 0, s, G.d_pdof,
+                       static_cast<const double*>(G.d_pinv), p0, p1, G.d_r, z, mg->opt.omega);
       else
-        k_vanka<float><<<blocks, 256, 0, s>>>(G.d_pdof, static_cast<const float*>(G.d_pinv), p0, p1, G.d_r, z,
-                                              mg->opt.omega);
+        launch_chained(k_vanka<float>, dim3(unsigned(blocks)), dim3(256), 0, s, G.d_pdof,
+                       static_cast<const float*>(G.d_pinv), p0, p1, G.d_r, z, mg->opt.omega);
       check_launch("k_vanka");
     }
 }

@@ -112,3 +112,29 @@ def test_mg_rejects_bad_grids(lib):
     with pytest.raises(lib.GdswError) as e:
         lib.Multigrid([probs[0], other[1]])
     assert e.value.code == lib.GDSW_ERR_INVALID_ARG and "nested" in str(e.value)
+
+
+@pytest.mark.parametrize("smoother", ["fp32", "fp64"])
+def test_mg_launch_chain_is_bitwise_neutral(lib, smoother):
+    """The chained launches of the smoother, transfers and Krylov kernels change no number:
+    V-cycles and the preconditioned solve are bitwise equal with the chain on and off."""
+    probs = CASES["three_grid_carreau"]()
+    b = None
+    out = []
+    try:
+        for on in (True, False):
+            lib.set_launch_overlap(on)
+            G = lib.Multigrid(probs, pre=2, post=2, smoother=smoother, coarse_tol=1e-1, tol=1e-10, symmetric=True)
+            if b is None:
+                b = I.random_rhs(G.n, 6)
+            z = torch.zeros(G.n, dtype=torch.float64, device="cuda")
+            G.gdsw_mg_vcycle(dev(b), z)
+            x = torch.zeros_like(z)
+            info = G.solve(dev(b), x)
+            assert info.status == 0
+            out.append((host(z), info.iterations, host(x)))
+            G.close()
+    finally:
+        lib.set_launch_overlap(True)
+    (z1, i1, x1), (z2, i2, x2) = out
+    assert np.array_equal(z1, z2) and i1 == i2 and np.array_equal(x1, x2)
