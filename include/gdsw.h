@@ -78,9 +78,9 @@ typedef struct {
   const uint8_t* tags;   /* host, (2nx+1)(2ny+1)(2nz+1) node tags (enum gdsw_tag) */
   const double* g;       /* host, 3 per node: Dirichlet datum (read where tag is WALL/INFLOW) */
   int32_t pressure;      /* a gdsw_pressure value; 0, the zero-initialised default, is Q1.
-                            P1-disc contexts take two levels (per-subdomain pressure coarse
-                            columns) and no multigrid hierarchy; anything else is
-                            GDSW_ERR_INVALID_ARG. */
+                            P1-disc coarse spaces hold one pressure column per part on every
+                            level; P1-disc grids take no multigrid hierarchy; any other value
+                            is GDSW_ERR_INVALID_ARG. */
 } gdsw_mesh;
 
 /* Viscosity (Section 2: constant mu; Section 3: Carreau law

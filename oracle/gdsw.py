@@ -34,14 +34,17 @@ Readings where the paper is silent (the same list is in the design notes):
 Optional variant (two levels only): rotation modes per entity (rigid rotations about the
 entity's centroid), the null-space enrichment the paper leaves out.
 
-Optional variant (two levels only): the paper's Q2 / P1-disc pair (prob.pressure =
-"p1disc"; four pressure dofs per element).  Readings: R_i keeps the pressure dofs of the
+Optional variant: the paper's Q2 / P1-disc pair (prob.pressure = "p1disc"; four pressure
+dofs per element; two to four levels).  Readings: R_i keeps the pressure dofs of the
 elements of Omega_i' none of whose 27 nodes lies on the artificial rim (with Dirichlet
 velocity there, the constant pressure on all of Omega_i' would be a kernel of A_i); the
 interface carries no pressure dof, so the coarse space gets one pressure column per
 subdomain -- the constant on the subdomain's own elements, prescribed through the element
 constants, which join Gamma -- while the linear pressure dofs of a subdomain's elements are
-interior and extended; with one subdomain the coarse space is empty.
+interior and extended; with one subdomain the coarse space is empty.  On a coarse level a
+part's pressure column is a coarse node of that part alone: a local set keeps it only for its
+own part, and the level's coarse space adds one pressure column per part (the sum of its
+members' columns, prescribed through them), which is a one-part node of the next level.
 
 Optional mixed-precision emulation (`local_precision`): the inputs and outputs of every
 local solve of a level are rounded to FP32 or BF16 while the solve itself stays exact, so
@@ -52,7 +55,8 @@ Parity status: pinned (partition of unity, constant reproduction, extension prop
 brute-force dense preconditioner, one-subdomain reduction, level collapse, symmetry; the
 rotation variant by rigid rotations lying in the range of Phi; the P1-disc variant by the
 Poiseuille closed form, the box-geometric count of its local pressure sets, its pressure
-columns on the cavity, the extension property and a brute-force dense two-level operator).
+columns on the cavity, the extension property, brute-force dense two-, three- and four-level
+operators and the coarse pressure columns counted by hand).
 """
 from __future__ import annotations
 
@@ -342,6 +346,7 @@ def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False, pool
                 for c in range(3):
                     g_rows.append(v + c); g_cols.append(np.full(v.size, col[(e, 4 + a)]))
                     g_vals.append(ent_rot[e][:, a, c])
+    n_ent_cols = n0
     if mesh.pdisc and N >= 2:
         # P1-disc: no pressure dof lies on the interface, so the pressure null space enters as
         # one column per subdomain -- the constant pressure on the subdomain's own elements --
@@ -393,6 +398,8 @@ def build_level1(sys_, prob, overlap=1, dense_local=False, rotations=False, pool
     lev.gamma = gamma
     lev.n0 = n0
     lev.coarse_nodes = [(entities[e][0], cnodes[e][0], cnodes[e][1]) for e in range(len(entities))]
+    if mesh.pdisc and N >= 2:   # the subdomain pressure columns as coarse nodes of one part each
+        lev.coarse_nodes += [((i,), [n_ent_cols + i], [3]) for i in range(N)]
     lev.entities = entities
     if n0 == 0:
         A0 = np.zeros((0, 0))
@@ -408,10 +415,18 @@ def build_coarse_level(A, cnodes, group, dense_local=True):
     """A Schwarz level on a coarse operator (Section 2.2 recursion).
 
     A: dense coarse operator of the finer level; cnodes: list of (sharing set, dofs, modes)
-    per coarse node; group: maps each finer-level part to its part on this level."""
+    per coarse node; group: maps each finer-level part to its part on this level.
+
+    A coarse node whose sharing set has one part is a part's own pressure column (the P1-disc
+    variant): it carries no interface, so, as on the first level, (a) a local set keeps it only
+    if its part belongs to the set's own part (the pressure of neighbouring parts is dropped
+    with the overlap's rim), (b) this level's coarse space gets one pressure column per part,
+    the sum of its members' columns, prescribed through them (they join Gamma), and (c) those
+    columns become the next level's one-part coarse nodes."""
     n = A.shape[0]
     nn = len(cnodes)
     parts = [tuple(sorted({int(group[i]) for i in s})) for (s, d, m) in cnodes]
+    own = np.array([len(s) == 1 for (s, d, m) in cnodes], dtype=bool)   # part pressure nodes
     N = int(np.max(group)) + 1 if len(group) else 1
     # structural coupling: sharing sets intersect
     inc_r, inc_c = [], []
@@ -428,6 +443,7 @@ def build_coarse_level(A, cnodes, group, dense_local=True):
         closure = np.array([v for v in range(nn) if J in parts[v]], dtype=int)
         if closure.size:
             ext = np.unique(adj[closure].indices)
+            ext = ext[~own[ext] | np.isin(ext, closure)]
         else:
             ext = closure
         d = np.sort(np.concatenate([np.array(cnodes[v][1], dtype=int) for v in ext])) if ext.size else np.zeros(0, int)
@@ -453,6 +469,10 @@ def build_coarse_level(A, cnodes, group, dense_local=True):
                 present[mm] = True
         ent_modes.append(present)
     col, n0, cn = _coarse_columns(ent_modes)
+    n_ent_cols = n0
+    pcols = bool(own.any()) and N >= 2
+    if pcols:
+        n0 += N
     PhiG = np.zeros((n, n0))
     gamma = np.zeros(n, dtype=bool)
     for e, (s, nodes) in enumerate(entities):
@@ -460,10 +480,15 @@ def build_coarse_level(A, cnodes, group, dense_local=True):
             for dof, mm in zip(cnodes[v][1], cnodes[v][2]):
                 PhiG[dof, col[(e, mm)]] = 1.0
                 gamma[dof] = True
+    if pcols:
+        for v in np.nonzero(own)[0]:
+            for dof in cnodes[v][1]:
+                PhiG[dof, n_ent_cols + parts[v][0]] = 1.0
+                gamma[dof] = True
     Phi = PhiG.copy()
     lev.interior = []
     for J in range(N):
-        inodes = [v for v in range(nn) if parts[v] == (J,)]
+        inodes = [v for v in range(nn) if parts[v] == (J,) and not (pcols and own[v])]
         I = np.sort(np.array([dd for v in inodes for dd in cnodes[v][1]], dtype=int))
         lev.interior.append(I)
         if I.size == 0 or n0 == 0:
@@ -476,6 +501,8 @@ def build_coarse_level(A, cnodes, group, dense_local=True):
     lev.gamma = gamma
     lev.n0 = n0
     lev.coarse_nodes = [(entities[e][0], cn[e][0], cn[e][1]) for e in range(len(entities))]
+    if pcols:
+        lev.coarse_nodes += [((J,), [n_ent_cols + J], [3]) for J in range(N)]
     lev.entities = entities
     A0 = Phi.T @ A @ Phi
     return lev, A0
@@ -493,8 +520,6 @@ class GDSW:
         L = prob.levels if levels is None else levels
         if rotations and L > 2:
             raise ValueError("rotation modes are defined for two-level GDSW only")
-        if sys_["mesh"].pdisc and L > 2:
-            raise ValueError("the P1-disc coarse space is defined for two-level GDSW only")
         self.L = L
         self.weighting = weighting
         self.levels = []

@@ -1198,8 +1198,6 @@ void setup_impl(gdsw_ctx* c, const gdsw_mesh* mesh, const gdsw_viscosity* visc, 
     build_mesh(c->mesh, mesh);
     c->lh.assign(nlev, LevelHost());
     GDSW_CHECK(lv->rotations == 0 || lv->levels == 2, GDSW_ERR_INVALID_ARG, "rotation modes need two levels");
-    GDSW_CHECK(!c->mesh.pdisc || lv->levels <= 2, GDSW_ERR_INVALID_ARG,
-               "the P1-disc coarse space is defined for two levels");
     if (nlev > 0) build_level1(c, part, lv->overlap, opt->slab_elems, lv->rotations);
     for (int l = 1; l < nlev; ++l) {
       GDSW_CHECK(part->groups[l - 1] != nullptr, GDSW_ERR_INVALID_ARG, "null grouping array");

@@ -1072,6 +1072,14 @@ void build_coarse_level(gdsw_ctx* ctx, int l, const int32_t* group, int group_le
   std::vector<std::vector<int>> closure(N);
   for (int v = 0; v < nn; ++v)
     for (int J : R[v]) closure[J].push_back(v);
+  // a coarse node of one part is that part's pressure column (P1-disc): a local set keeps it
+  // only when the part is its own (the pressure of neighbouring parts is dropped with the rim)
+  std::vector<char> own(nn, 0);
+  bool any_own = false;
+  for (int v = 0; v < nn; ++v) {
+    own[v] = P.cn_set[v].size() == 1;
+    any_own = any_own || own[v];
+  }
   SlabSet& S = L.loc;
   S = SlabSet();
   std::vector<int> nb;
@@ -1080,7 +1088,8 @@ void build_coarse_level(gdsw_ctx* ctx, int l, const int32_t* group, int group_le
     for (int v : closure[J]) {
       in[v] = 1;
       neighbors(v, nb);
-      for (int w : nb) in[w] = 1;
+      for (int w : nb)
+        if (!own[w]) in[w] = 1;
     }
     std::vector<int32_t> d;
     for (int v = 0; v < nn; ++v)
@@ -1156,18 +1165,36 @@ void build_coarse_level(gdsw_ctx* ctx, int l, const int32_t* group, int group_le
     C.cn_modes.push_back(modes);
     eset[e] = ents[e].set;
   }
+  // P1-disc: one pressure column per part of this level, the sum of its members' pressure
+  // columns, prescribed through them (they join Gamma); they become the next level's one-part
+  // coarse nodes
+  const bool pcols = any_own && N >= 2;
+  if (pcols) {
+    const int n_ent_cols = n0;
+    for (int v = 0; v < nn; ++v)
+      if (own[v])
+        for (int dd : P.cn_dofs[v]) gl.push_back({dd, int32_t(n_ent_cols + R[v][0])});
+    for (int J = 0; J < N; ++J) {
+      C.cn_set.push_back({J});
+      C.cn_dofs.push_back({n0});
+      C.cn_modes.push_back({3});
+      eset.push_back({J});
+      ent_cols.push_back({n0});
+      ++n0;
+    }
+  }
   C.n0 = n0;
   std::sort(gl.begin(), gl.end());
   for (auto& q : gl) {
     C.gdofs.push_back(q.first);
     C.gcol.push_back(q.second);
   }
-  // interiors: nodes whose part set is {J}
+  // interiors: nodes whose part set is {J} (not the part pressure nodes, which are in Gamma)
   SlabSet& I = L.inter;
   I = SlabSet();
   std::vector<std::vector<int32_t>> idof(N);
   for (int v = 0; v < nn; ++v)
-    if (R[v].size() == 1)
+    if (R[v].size() == 1 && !(pcols && own[v]))
       for (int dd : P.cn_dofs[v]) idof[R[v][0]].push_back(dd);
   for (int J = 0; J < N; ++J) dense_order(idof[J], I);
   I.layout();

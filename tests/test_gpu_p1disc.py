@@ -1,11 +1,12 @@
 """GPU parity of the Q2 / P1-disc variant (the paper's element pair, Section 2) with its
-two-level GDSW coarse space, through the C ABI, against the FP64 CPU oracle.
+two- to four-level GDSW coarse spaces, through the C ABI, against the FP64 CPU oracle.
 
 The pressure is discontinuous (four dofs per fluid element); no pressure dof lies on the
 interface, so the coarse space holds the entity translations plus one pressure column per
-subdomain (the constant on the subdomain's elements).  Tolerances as in the Q2/Q1 parity
-tests: single FP64 steps <= 1e-12 (operator <= 1e-14), apply <= 1e-11, FP64 solve <= 1e-10
-with iterations +-1, mixed FP32 / BF16 local factors forward error <= 1e-8.
+subdomain (the constant on the subdomain's elements), and every coarse level one per part.
+Tolerances as in the Q2/Q1 parity tests: single FP64 steps <= 1e-12 (operator <= 1e-14),
+apply <= 1e-11, FP64 solve <= 1e-10 with iterations +-1, mixed FP32 / BF16 local factors
+forward error <= 1e-8.
 """
 import numpy as np
 import pytest
@@ -29,6 +30,8 @@ PROBLEMS = {
                                               n=0.5, nu_inf=1e-3)),
     "channel16_obstacles": lambda: _p1(I.channel(16, parts=(4, 4, 4), groups=(), levels=2)),
     "die_rcb": lambda: _p1(I.die(16, 16, 32, nparts=16, per_group=4, levels=2)),
+    "channel12_3lvl": lambda: _p1(I.channel(12, parts=(4, 4, 4), groups=((2, 2, 2),), levels=3)),
+    "die_rcb_4lvl": lambda: _p1(I.die(16, 16, 32, nparts=32, per_group=4, levels=4)),
 }
 
 _cache = {}
@@ -90,31 +93,32 @@ def test_p1disc_operator(lib, name):
 @pytest.mark.parametrize("name", list(PROBLEMS))
 @pytest.mark.parametrize("weighting", ["pou", "plain"])
 def test_p1disc_level_steps(lib, name, weighting):
-    """Section 2.1 with the P1-disc sets: local branch (the element pressure of Omega_i' kept
-    away from its rim), Phi^T r, Phi x (per-subdomain pressure columns) and A_0."""
+    """Sections 2.1 / 2.2 with the P1-disc sets on every level: local branch (the element
+    pressure of Omega_i' kept away from its rim; a coarse part's own pressure columns only),
+    Phi^T r, Phi x (per-part pressure columns) and A_0."""
     p, S, P = oracle_for(name, weighting)
-    lev = P.levels[0]
     ctx = lib.Context(p, weighting=weighting)
-    assert int(ctx.sizes.n_coarse[0]) == lev.n0
     rng = np.random.default_rng(1)
-    r = rng.standard_normal(lev.n)
-    z = torch.zeros(lev.n, dtype=torch.float64, device="cuda")
-    ctx.gdsw_apply_local(0, dev(r), z)
-    assert rel(host(z), lev.apply_local(r, weighting)) <= 1e-12
-    r0 = torch.zeros(lev.n0, dtype=torch.float64, device="cuda")
-    ctx.gdsw_restrict(0, dev(r), r0)
-    assert rel(host(r0), lev.Phi.T @ r) <= 1e-12
-    x0 = rng.standard_normal(lev.n0)
-    z2 = torch.zeros(lev.n, dtype=torch.float64, device="cuda")
-    ctx.gdsw_prolong(0, dev(x0), z2)
-    assert rel(host(z2), lev.Phi @ x0) <= 1e-12
-    assert rel(ctx.gdsw_coarse_matrix(0), P.A0[1]) <= 1e-12
+    for l, lev in enumerate(P.levels):
+        assert int(ctx.sizes.n_coarse[l]) == lev.n0
+        r = rng.standard_normal(lev.n)
+        z = torch.zeros(lev.n, dtype=torch.float64, device="cuda")
+        ctx.gdsw_apply_local(l, dev(r), z)
+        assert rel(host(z), lev.apply_local(r, weighting)) <= 1e-12, (l, "local")
+        r0 = torch.zeros(lev.n0, dtype=torch.float64, device="cuda")
+        ctx.gdsw_restrict(l, dev(r), r0)
+        assert rel(host(r0), lev.Phi.T @ r) <= 1e-12, (l, "restrict")
+        x0 = rng.standard_normal(lev.n0)
+        z2 = torch.zeros(lev.n, dtype=torch.float64, device="cuda")
+        ctx.gdsw_prolong(l, dev(x0), z2)
+        assert rel(host(z2), lev.Phi @ x0) <= 1e-12, (l, "prolong")
+        assert rel(ctx.gdsw_coarse_matrix(l), P.A0[l + 1]) <= 1e-12, (l, "A0")
     ctx.close()
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_p1disc_apply_and_solve(lib, name):
-    """Two-level apply and FP64 FGMRES: solution within 1e-10 of the oracle's, iterations
+    """Two- to four-level apply and FP64 FGMRES: solution within 1e-10 of the oracle's, iterations
     +-1; then FP32 and BF16 local factors reach the FP64 solution to 1e-8."""
     from oracle import fem, fgmres
     p, S, P = oracle_for(name)
@@ -140,8 +144,8 @@ def test_p1disc_apply_and_solve(lib, name):
 
 
 def test_p1disc_poiseuille_and_degenerate_cases(lib):
-    """Closed form on the GPU (Poiseuille's linear pressure is in P1-disc), one subdomain
-    (empty coarse space, one FGMRES step), and the two-level restriction of the variant."""
+    """Closed form on the GPU (Poiseuille's linear pressure is in P1-disc) and one subdomain
+    (empty coarse space, one FGMRES step)."""
     from oracle import fem
     p = I.poiseuille(4, parts=(2, 2, 2), pressure="p1disc")
     S = fem.assemble(p)
@@ -168,5 +172,3 @@ def test_p1disc_poiseuille_and_degenerate_cases(lib):
     info = c1.gdsw_solve(dev(r), x)
     assert info.status == 0 and info.iterations == 1
     c1.close()
-    with pytest.raises(lib.GdswError):
-        lib.Context(I.box_problem(4, 4, 2, (4, 4, 2), groups=((2, 2, 1),), levels=3, pressure="p1disc"))

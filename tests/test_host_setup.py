@@ -39,6 +39,9 @@ CASES = [
     ("cube6_p1disc", lambda: _p1disc(I.unit_cube(6, parts=(2, 2, 2)))),
     ("channel12_p1disc", lambda: _p1disc(I.channel(12, parts=(3, 3, 3), groups=(), levels=2))),
     ("die_rcb_p1disc", lambda: _p1disc(I.die(16, 16, 32, nparts=16, per_group=4, levels=2))),
+    ("box_4lvl_p1disc", lambda: _p1disc(I.box_problem(4, 4, 2, (4, 4, 2), groups=((2, 2, 1), (2, 1, 1)), levels=4))),
+    ("channel12_p1disc_3lvl", lambda: _p1disc(I.channel(12, parts=(4, 4, 4), groups=((2, 2, 2),), levels=3))),
+    ("die_rcb_p1disc_4lvl", lambda: _p1disc(I.die(16, 16, 32, nparts=32, per_group=4, levels=4))),
 ]
 
 

@@ -147,8 +147,9 @@ def test_p1disc_pressure_columns_and_translations():
     mesh = S["mesh"]
     lev, _ = gdsw.build_level1(S, p)
     N = 8
-    n_ent = sum(len(d) for (s, d, m) in lev.coarse_nodes)
+    n_ent = sum(len(d) for (s, d, m) in lev.coarse_nodes if len(s) >= 2)
     assert lev.n0 == n_ent + N
+    assert [tuple(s) for (s, d, m) in lev.coarse_nodes if len(s) == 1] == [(i,) for i in range(N)]
     sub = p.part[mesh.elems]
     for i in range(N):
         v = lev.Phi[:, n_ent + i].toarray().ravel()
@@ -220,10 +221,76 @@ def test_p1disc_brute_force_dense(weighting):
     assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
 
 
-def test_p1disc_two_levels_only():
-    """The per-subdomain pressure columns are defined for the two-level method; asking for
-    more levels is an error, not a silent reinterpretation."""
-    p = I.box_problem(4, 4, 2, (4, 4, 2), groups=((2, 2, 1),), levels=3, pressure="p1disc")
+def _brute_force(P, level=0):
+    """Section 2.2 recursion written out with dense numpy inverses (plain weighting)."""
+    lev = P.levels[level]
+    A = P.A0[level].toarray() if hasattr(P.A0[level], "toarray") else P.A0[level]
+    B = np.zeros((lev.n, lev.n))
+    for d in lev.dofs:
+        B[np.ix_(d, d)] += np.linalg.inv(A[np.ix_(d, d)])
+    if lev.n0 == 0:
+        return B
+    Phi = lev.Phi.toarray() if hasattr(lev.Phi, "toarray") else lev.Phi
+    inner = np.linalg.inv(P.A0[level + 1]) if level + 1 == len(P.levels) else _brute_force(P, level + 1)
+    return B + Phi @ inner @ Phi.T
+
+
+@pytest.mark.parametrize("L", [3, 4])
+def test_p1disc_multilevel_brute_force(L):
+    """Section 2.2 four-level equation with the P1-disc coarse spaces: on every coarse level a
+    part's pressure column is a coarse node of that part alone, so the next level adds one
+    pressure column per part; the oracle's apply equals the dense recursion built with numpy
+    inverses, the plain form is symmetric, every local and interior matrix is invertible, and
+    FGMRES reaches the dense solution."""
+    groups = ((2, 2, 1),) if L == 3 else ((2, 2, 1), (2, 1, 1))
+    p = I.box_problem(4, 4, 2, (4, 4, 2), groups=groups, levels=L, form="symmetric", uk_seed=1, lam=1.0, n=0.5,
+                      nu_inf=1e-3, pressure="p1disc")
     S = fem.assemble(p)
-    with pytest.raises(ValueError):
-        gdsw.GDSW(S, p)
+    P = gdsw.GDSW(S, p, weighting="plain")
+    n = S["A"].shape[0]
+    B = _brute_force(P)
+    for j in np.random.default_rng(4).choice(n, size=30, replace=False):
+        e = np.zeros(n); e[j] = 1.0
+        assert np.abs(P.apply(e) - B[:, j]).max() <= 1e-11 * max(1.0, np.abs(B).max())
+    assert np.abs(B - B.T).max() <= 1e-11 * np.abs(B).max()
+    for l, lev in enumerate(P.levels):
+        A = P.A0[l].toarray() if hasattr(P.A0[l], "toarray") else P.A0[l]
+        for d in list(lev.dofs) + [i for i in lev.interior if i.size]:
+            s = np.linalg.svd(A[np.ix_(d, d)], compute_uv=False)
+            assert s[-1] > 1e-10 * s[0]
+    b = I.random_rhs(n, 3)
+    x, info = fgmres.fgmres(lambda v: S["A"] @ v, b, P.apply, tol=1e-12)
+    xd = spla.spsolve(S["A"].tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+def test_p1disc_coarse_pressure_columns_by_hand():
+    """The coarse-level readings written out for a 4 x 4 x 2 box of 32 one-element subdomains
+    grouped 2 x 2 x 1 into 8 parts (all-wall cavity): (a) a level-2 local set holds the
+    pressure columns of its own part's four subdomains and no other; (b) the level-2 pressure
+    column of part J, carried down through both bases, is the constant pressure on the elements
+    of J's subdomains (zero velocity, zero slopes); (c) it is a one-part coarse node of the
+    next level."""
+    p = I.box_problem(4, 4, 2, (4, 4, 2), groups=((2, 2, 1),), levels=3, bc="cavity", pressure="p1disc")
+    S = fem.assemble(p)
+    mesh = S["mesh"]
+    P = gdsw.GDSW(S, p)
+    lev1, lev2 = P.levels
+    n_ent1 = sum(len(d) for (s, d, m) in lev1.coarse_nodes if len(s) >= 2)
+    assert lev1.n0 == n_ent1 + 32
+    group = np.asarray(p.groups[0])
+    for J in range(8):
+        pcol = n_ent1 + np.arange(32)
+        mine = np.intersect1d(lev2.dofs[J], pcol)
+        assert np.array_equal(mine, np.sort(n_ent1 + np.nonzero(group == J)[0]))
+    n_ent2 = sum(len(d) for (s, d, m) in lev2.coarse_nodes if len(s) >= 2)
+    assert lev2.n0 == n_ent2 + 8
+    assert [tuple(s) for (s, d, m) in lev2.coarse_nodes if len(s) == 1] == [(J,) for J in range(8)]
+    Phi1 = lev1.Phi.toarray()
+    sub = p.part[mesh.elems]
+    for J in range(8):
+        e2 = np.zeros(lev2.n0); e2[n_ent2 + J] = 1.0
+        v = Phi1 @ (lev2.Phi @ e2)
+        expect = np.zeros(lev1.n)
+        expect[mesh.nu + 4 * np.nonzero(np.isin(sub, np.nonzero(group == J)[0]))[0]] = 1.0
+        assert np.abs(v - expect).max() < 1e-11
