@@ -47,10 +47,10 @@ inline void check_launch(const char* what) {
 // dependents may start) and dep_wait() (the previous grid has completed and its writes are
 // visible) before it reads anything the previous kernels wrote or writes anything they read;
 // before the wait it may only read data that no kernel of the stream writes (factors, plans,
-// the operator), and after it it reads such data through coherent loads (no ld.global.nc).
-// A kernel that follows a wait on another stream's event is launched in plain order: the
-// dependency wait covers only the previous grid of its own stream.  Both instructions do
-// nothing in a launch made without the attribute.
+// the operator); the wait makes the previous grid's writes visible to this grid.  A kernel
+// that follows a wait on another stream's event is launched in plain order: the dependency
+// wait covers only the previous grid of its own stream.  Both instructions do nothing in a
+// launch made without the attribute.
 // g_launch_overlap (gdsw_set_launch_overlap) switches the attribute off process-wide.
 extern bool g_launch_overlap;
 #ifdef __CUDACC__
