@@ -425,7 +425,7 @@ __device__ __forceinline__ void sell_block(const int32_t* __restrict__ acol, con
                                            const double* __restrict__ x, int64_t g, int lane, double& a0, double& a1,
                                            double& a2) {
   const int64_t j = __ldg(acol + g * 32 + lane);
-  const double x0 = x[3 * j], x1 = x[3 * j + 1], x2 = x[3 * j + 2];
+  const double x0 = __ldg(x + 3 * j), x1 = __ldg(x + 3 * j + 1), x2 = __ldg(x + 3 * j + 2);
   const double* v = aval + g * 288 + lane;
   const double v0 = __ldcs(v), v1 = __ldcs(v + 32), v2 = __ldcs(v + 64), v3 = __ldcs(v + 96), v4 = __ldcs(v + 128),
                v5 = __ldcs(v + 160), v6 = __ldcs(v + 192), v7 = __ldcs(v + 224), v8 = __ldcs(v + 256);
@@ -449,17 +449,9 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ sell_r
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nu = 3 * nv;
   const int64_t vblocks = (nslices + 1) / 2;
-  // chained launch: the first two slot groups of each warp's values (operator data) go to L2
-  // before the dependency wait; x, which the previous kernel may have written, is read after it
+  // launched in plain stream order (its x gathers use the non-coherent cache path, which a
+  // chained launch must not use for data the previous kernel wrote); it lets its successor start
   dep_release();
-  if (blockIdx.x < vblocks) {
-    const int64_t sl = 2 * int64_t(blockIdx.x) + (warp >> 2);
-    if (sl < nslices) {
-      const int64_t g = (aoff[sl] >> 5) + (warp & 3) + (lane < 18 ? 0 : 4);
-      if (g < (aoff[sl + 1] >> 5)) prefetch_l2(aval + g * 288 + (lane < 18 ? lane : lane - 18) * 16);
-    }
-  }
-  dep_wait();
   if (blockIdx.x < vblocks) {
     const int64_t sl = 2 * int64_t(blockIdx.x) + (warp >> 2);
     const int sub = warp & 3;
@@ -480,8 +472,8 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ sell_r
           vv[q] = __ldcs(v + 32 * q);
           ww[q] = __ldcs(w + 32 * q);
         }
-        const double x0 = x[3 * j], x1 = x[3 * j + 1], x2 = x[3 * j + 2];
-        const double y0 = x[3 * k], y1 = x[3 * k + 1], y2 = x[3 * k + 2];
+        const double x0 = __ldg(x + 3 * j), x1 = __ldg(x + 3 * j + 1), x2 = __ldg(x + 3 * j + 2);
+        const double y0 = __ldg(x + 3 * k), y1 = __ldg(x + 3 * k + 1), y2 = __ldg(x + 3 * k + 2);
         a0 = fma(vv[2], x2, fma(vv[1], x1, fma(vv[0], x0, a0)));
         a1 = fma(vv[5], x2, fma(vv[4], x1, fma(vv[3], x0, a1)));
         a2 = fma(vv[8], x2, fma(vv[7], x1, fma(vv[6], x0, a2)));
@@ -492,7 +484,7 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ sell_r
       if (g < g1) sell_block(acol, aval, x, g, lane, a0, a1, a2);
       const int64_t h0 = boff[sl] >> 5, h1 = boff[sl + 1] >> 5;
       for (int64_t h = h0 + sub; h < h1; h += 4) {
-        const double xp = x[nu + __ldg(bcol + h * 32 + lane)];
+        const double xp = __ldg(x + nu + __ldg(bcol + h * 32 + lane));
         const double* v = btval + h * 96 + lane;
         a0 = fma(__ldcs(v + 0), xp, a0);
         a1 = fma(__ldcs(v + 32), xp, a1);
@@ -524,7 +516,7 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ sell_r
     for (int64_t f = f0 + lane; f < f1; f += 32) {
       const int64_t e = f / 3;
       const int d = int(f - 3 * e);
-      acc = fma(__ldcs(bval + f), x[3 * int64_t(b_col[e]) + d], acc);
+      acc = fma(__ldcs(bval + f), __ldg(x + 3 * int64_t(b_col[e]) + d), acc);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -635,9 +627,9 @@ void launch_spmv(gdsw_ctx* c, const double* x, double* y, const double* rhs, cud
   const double* bval = c->d_val + 9 * c->nnzb + 3 * c->nbt;
   const int64_t ns = c->n_sell_slices;
   const int64_t blocks = (ns + 1) / 2 + (np + 7) / 8;
-  launch_chained(k_spmv, dim3(unsigned(blocks)), dim3(256), 0, s, c->d_sell_row, c->d_sell_aoff, c->d_sell_acol,
-                 c->d_sell_aval, c->d_sell_boff, c->d_sell_bcol, c->d_sell_btval, ns, c->d_b_ptr, c->d_b_col, bval,
-                 nv, np, x, y, rhs);
+  k_spmv<<<int(blocks), 256, 0, s>>>(c->d_sell_row, c->d_sell_aoff, c->d_sell_acol, c->d_sell_aval,
+                                     c->d_sell_boff, c->d_sell_bcol, c->d_sell_btval, ns, c->d_b_ptr, c->d_b_col,
+                                     bval, nv, np, x, y, rhs);
   check_launch("k_spmv");
 }
 
