@@ -46,9 +46,8 @@ struct MgGrid {
   int32_t* d_pdof = nullptr;   // npatch x PMAX dofs, -1 padding
   void* d_pinv = nullptr;      // npatch x PMAX x PMAX, column-major inverse (FP32 or FP64)
   double minpiv = 0;
-  // FP32 smoothing: an FP32 copy of the operator's values (taken at creation; component planes:
-  // component c of block / entry e at c n + e) and, per colour, the velocity-node and pressure
-  // rows its patches touch (the residual is formed there only)
+  // FP32 smoothing: an FP32 copy of the operator's values (taken at creation) and, per colour,
+  // the velocity-node and pressure rows its patches touch (the residual is formed there only)
   float *d_a32 = nullptr, *d_bt32 = nullptr, *d_b32 = nullptr;
   int32_t* d_rows = nullptr;   // per colour: velocity nodes, then pressure indices
   int64_t vrow_off[9] = {0}, prow_off[9] = {0};
@@ -372,17 +371,16 @@ __global__ void __launch_bounds__(256) k_vanka(const int32_t* __restrict__ pdof,
     if (dof[u] >= 0) z[dof[u]] += omega * double(y[u]);
 }
 
-// r = b - A z on the velocity-node rows of a list, FP32 operator values (component planes)
-// and products, FP64 b and result: one warp per node, lanes over its 3x3 blocks and B^T
-// entries (each component one coalesced access), fixed butterfly
+// r = b - A z on the velocity-node rows of a list, FP32 operator values and products, FP64
+// b and result: one warp per node, lanes over its 3x3 blocks and B^T entries, fixed butterfly
 __global__ void __launch_bounds__(256) k_resid_vrows(const int32_t* __restrict__ rows, int64_t nrows,
                                                      const int32_t* __restrict__ a_ptr,
                                                      const int32_t* __restrict__ a_col, const float* __restrict__ a32,
                                                      const int32_t* __restrict__ bt_ptr,
                                                      const int32_t* __restrict__ bt_col,
-                                                     const float* __restrict__ bt32, int64_t sa, int64_t sbt,
-                                                     int64_t nu, const double* __restrict__ z,
-                                                     const double* __restrict__ b, double* __restrict__ r) {
+                                                     const float* __restrict__ bt32, int64_t nu,
+                                                     const double* __restrict__ z, const double* __restrict__ b,
+                                                     double* __restrict__ r) {
   const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
   dep_release();
@@ -393,17 +391,17 @@ __global__ void __launch_bounds__(256) k_resid_vrows(const int32_t* __restrict__
   for (int32_t e = a_ptr[I] + lane; e < a_ptr[I + 1]; e += 32) {
     const int64_t J = a_col[e];
     const float x0 = float(z[3 * J]), x1 = float(z[3 * J + 1]), x2 = float(z[3 * J + 2]);
-    const float* v = a32 + e;   // component m at v[m sa]
-    s0 = fmaf(v[0], x0, fmaf(v[sa], x1, fmaf(v[2 * sa], x2, s0)));
-    s1 = fmaf(v[3 * sa], x0, fmaf(v[4 * sa], x1, fmaf(v[5 * sa], x2, s1)));
-    s2 = fmaf(v[6 * sa], x0, fmaf(v[7 * sa], x1, fmaf(v[8 * sa], x2, s2)));
+    const float* v = a32 + int64_t(e) * 9;
+    s0 = fmaf(v[0], x0, fmaf(v[1], x1, fmaf(v[2], x2, s0)));
+    s1 = fmaf(v[3], x0, fmaf(v[4], x1, fmaf(v[5], x2, s1)));
+    s2 = fmaf(v[6], x0, fmaf(v[7], x1, fmaf(v[8], x2, s2)));
   }
   for (int32_t e = bt_ptr[I] + lane; e < bt_ptr[I + 1]; e += 32) {
     const float xp = float(z[nu + bt_col[e]]);
-    const float* v = bt32 + e;
+    const float* v = bt32 + int64_t(e) * 3;
     s0 = fmaf(v[0], xp, s0);
-    s1 = fmaf(v[sbt], xp, s1);
-    s2 = fmaf(v[2 * sbt], xp, s2);
+    s1 = fmaf(v[1], xp, s1);
+    s2 = fmaf(v[2], xp, s2);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -421,7 +419,7 @@ __global__ void __launch_bounds__(256) k_resid_vrows(const int32_t* __restrict__
 __global__ void __launch_bounds__(256) k_resid_prows(const int32_t* __restrict__ rows, int64_t nrows,
                                                      const int32_t* __restrict__ b_ptr,
                                                      const int32_t* __restrict__ b_col, const float* __restrict__ b32,
-                                                     int64_t sb, int64_t nu, const double* __restrict__ z,
+                                                     int64_t nu, const double* __restrict__ z,
                                                      const double* __restrict__ b, double* __restrict__ r) {
   const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
@@ -432,23 +430,17 @@ __global__ void __launch_bounds__(256) k_resid_prows(const int32_t* __restrict__
   float s = 0.f;
   for (int32_t e = b_ptr[P] + lane; e < b_ptr[P + 1]; e += 32) {
     const int64_t J = b_col[e];
-    const float* v = b32 + e;
-    s = fmaf(v[0], float(z[3 * J]), fmaf(v[sb], float(z[3 * J + 1]), fmaf(v[2 * sb], float(z[3 * J + 2]), s)));
+    const float* v = b32 + int64_t(e) * 3;
+    s = fmaf(v[0], float(z[3 * J]), fmaf(v[1], float(z[3 * J + 1]), fmaf(v[2], float(z[3 * J + 2]), s)));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) r[nu + P] = b[nu + P] - double(s);
 }
 
-// FP32 copy of m-component entries stored entry-major (entry e's components at e m .. e m + m - 1)
-// into component-major planes (component c of entry e at c n + e), so that the lanes of a warp,
-// which take consecutive entries of a row, read each component with one coalesced access
-__global__ void k_to_f32_planes(const double* __restrict__ a, float* __restrict__ b, int64_t n, int m) {
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i >= n * m) return;
-  const int64_t e = i / m;
-  const int c = int(i - e * m);
-  b[int64_t(c) * n + e] = float(a[i]);
+  if (i < n) b[i] = float(a[i]);
 }
 
 // y = M x (+ y when accumulate), CSR FP64, one thread per row
@@ -483,13 +475,12 @@ static void colour_residual(gdsw_mg* mg, MgGrid& G, int c, const double* b, cons
   const int64_t nv = G.prow_off[c] - G.vrow_off[c], np = G.vrow_off[c + 1] - G.prow_off[c];
   if (nv > 0) {
     launch_chained(k_resid_vrows, dim3(unsigned((nv + 7) / 8)), dim3(256), 0, s, G.d_rows + G.vrow_off[c], nv,
-                   x->d_a_ptr, x->d_a_col, G.d_a32, x->d_bt_ptr, x->d_bt_col, G.d_bt32, int64_t(x->nnzb),
-                   int64_t(x->nbt), x->mesh.nu, z, b, G.d_r);
+                   x->d_a_ptr, x->d_a_col, G.d_a32, x->d_bt_ptr, x->d_bt_col, G.d_bt32, x->mesh.nu, z, b, G.d_r);
     check_launch("k_resid_vrows");
   }
   if (np > 0) {
     launch_chained(k_resid_prows, dim3(unsigned((np + 7) / 8)), dim3(256), 0, s, G.d_rows + G.prow_off[c], np,
-                   x->d_b_ptr, x->d_b_col, G.d_b32, int64_t(x->nb), x->mesh.nu, z, b, G.d_r);
+                   x->d_b_ptr, x->d_b_col, G.d_b32, x->mesh.nu, z, b, G.d_r);
     check_launch("k_resid_prows");
   }
 }
@@ -641,10 +632,10 @@ static void mg_create(gdsw_mg* mg, gdsw_ctx* const* grids, int ngrids, const gds
       G.d_a32 = mg->arena.alloc<float>(na);
       G.d_bt32 = mg->arena.alloc<float>(nbt);
       G.d_b32 = mg->arena.alloc<float>(nb);
-      k_to_f32_planes<<<int((na + 255) / 256), 256, 0, s>>>(x->d_val, G.d_a32, x->nnzb, 9);
-      k_to_f32_planes<<<int((nbt + 255) / 256), 256, 0, s>>>(x->d_val + na, G.d_bt32, x->nbt, 3);
-      k_to_f32_planes<<<int((nb + 255) / 256), 256, 0, s>>>(x->d_val + na + nbt, G.d_b32, x->nb, 3);
-      check_launch("k_to_f32_planes");
+      k_to_f32<<<int((na + 255) / 256), 256, 0, s>>>(x->d_val, G.d_a32, na);
+      k_to_f32<<<int((nbt + 255) / 256), 256, 0, s>>>(x->d_val + na, G.d_bt32, nbt);
+      k_to_f32<<<int((nb + 255) / 256), 256, 0, s>>>(x->d_val + na + nbt, G.d_b32, nb);
+      check_launch("k_to_f32");
     }
     // transfers
     const MeshHost& Cm = mg->g[l + 1].ctx->mesh;

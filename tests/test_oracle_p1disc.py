@@ -1,5 +1,5 @@
 """Pins of the oracle's Q2 / P1-disc variant (the paper's own element pair, Section 2) and of
-its two-level GDSW coarse space.
+its two- to four-level GDSW coarse spaces.
 
 The pressure is discontinuous: per fluid element the coefficients of 1, xi, eta, zeta in the
 element's reference coordinates.  No pressure dof lies on the subdomain interface, so the
