@@ -75,7 +75,8 @@ inline void launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, KArgs(args)...);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, KArgs(args)...);
+  if (e != cudaSuccess) throw Error{GDSW_ERR_CUDA, std::string("chained launch: ") + cudaGetErrorString(e)};
 }
 #endif
 

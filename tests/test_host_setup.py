@@ -29,6 +29,15 @@ def _p1disc(p):
     return p
 
 
+def test_launch_overlap_switch(lib):
+    """gdsw_set_launch_overlap takes 0 or 1 (a process-wide flag; no device work) and rejects
+    anything else."""
+    L = lib.load()
+    assert L.gdsw_set_launch_overlap(5) == 1        # GDSW_ERR_INVALID_ARG
+    assert L.gdsw_set_launch_overlap(0) == 0
+    assert L.gdsw_set_launch_overlap(1) == 0
+
+
 CASES = [
     ("cube8_2x2x2", lambda: I.unit_cube(8)),
     ("box_3lvl", lambda: I.box_problem(4, 4, 4, (2, 2, 2), groups=((2, 2, 1),), levels=3)),
